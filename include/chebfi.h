@@ -1,0 +1,160 @@
+/*
+ * chebfi.h -- C ABI of the GB300 (sm_103a) Chebyshev-filtered subspace iteration for the
+ * plane-wave Kohn-Sham eigenproblem H psi = lambda S psi (Levitt & Torrent, arXiv:1406.4350,
+ * Eq. (KS) of Section 2.1; Algorithm 2 of Section 3.2; Section 4.1 for S^{-1}).
+ *
+ * Operators (Section 2.1):
+ *   H = K + V_loc + P D P^H       K diagonal |k+G|^2/2, V_loc multiplication in real space
+ *   S = I + P Q P^H               Q = 0 (NULL) is the norm-conserving case S = I
+ * with P the N_pw x N_proj projector matrix and D, Q block-diagonal (one symmetric
+ * n_a x n_a block per atom).  The paper writes D_V for D and D_S for Q.
+ *
+ * Conventions shared by every entry point
+ *  - Complex numbers are interleaved (re, im) pairs of double (complex128).
+ *  - Wavefunction blocks are column-major: band n occupies Y + 2*n*ld doubles, its
+ *    N_pw coefficients in the caller's plane-wave order (the order given to
+ *    chebfi_set_sphere).  ld >= N_pw.
+ *  - Pointers named Y, HY, X, out, evals, resid are DEVICE pointers owned by the caller;
+ *    the library never frees them.  Setup data (lattice, Miller indices, V_loc, P, D, Q)
+ *    is COPIED at the call; the caller may free its copy afterwards.
+ *  - Work is enqueued on the given CUDA stream (cudaStream_t passed as void*, NULL =
+ *    legacy default stream) and runs asynchronously, except where a function says it
+ *    synchronises.  The context is not thread-safe: one host thread at a time.
+ *  - Return value 0 = success; negative = error, with a message from chebfi_last_error.
+ *    Argument and state errors are detected before any work is enqueued.  Errors found
+ *    on the device (a Gram matrix that is not positive definite, a Jacobi sweep limit)
+ *    are reported by the functions documented to synchronise, and by chebfi_sync_status.
+ */
+#ifndef CHEBFI_H
+#define CHEBFI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chebfi_ctx chebfi_ctx;
+
+/* Arithmetic of the filter (Algorithm 2's inner loop).  Rayleigh-Ritz, Cholesky-QR,
+ * Rayleigh quotients and residuals always run in FP64. */
+typedef enum {
+  CHEBFI_F64 = 0,   /* FP64 FFT and FP64 GEMMs */
+  CHEBFI_F32 = 1,   /* FP32 FFT and FP32 GEMMs on the CUDA cores */
+  CHEBFI_MIXED = 2  /* FP32 FFT; projector GEMMs on tcgen05 tensor cores with split
+                       bf16 (hi + lo) operands and FP32 accumulation */
+} chebfi_prec;
+
+/* Upper end lambda_+ of the filtered interval (Section 4.3, "Choice of the polynomial"). */
+typedef enum {
+  CHEBFI_BOUND_PAPER = 0,    /* E_cut: the largest |k+G|^2/2 of the sphere (not a proven bound) */
+  CHEBFI_BOUND_RIGOROUS = 1  /* max(0, max K + max V + l_max(L^H D L)) / (1 + min(0, l_min(L^H Q L)))
+                                with P^H P = L L^H: a proven upper bound of the pencil */
+} chebfi_bound_mode;
+
+enum {
+  CHEBFI_OK = 0,
+  CHEBFI_ERR_ARG = -1,            /* a null pointer, a size out of range, a bad enum */
+  CHEBFI_ERR_STATE = -2,          /* a setter called out of order, or a missing setter */
+  CHEBFI_ERR_CUDA = -3,           /* a CUDA runtime call failed (message names it) */
+  CHEBFI_ERR_NOT_SPD = -4,        /* Cholesky met a non-positive pivot (Gram or S) */
+  CHEBFI_ERR_NO_CONVERGENCE = -5, /* the Jacobi eigensolver hit its sweep limit */
+  CHEBFI_ERR_FILTER_OVERFLOW = -6,/* T_degree((lambda_1-c)/r) too large for the precision */
+  CHEBFI_ERR_NOMEM = -7           /* device allocation failed */
+};
+
+typedef struct {
+  int degree;          /* Chebyshev degree n (number of S^{-1}H applications), >= 1 */
+  int sweeps;          /* repetitions of Algorithm 2, >= 1 */
+  int prec;            /* chebfi_prec of the filter */
+  int bound_mode;      /* chebfi_bound_mode, used when lambda_hi <= lambda_lo estimate */
+  double lambda_hi;    /* > 0: fixed lambda_+; <= 0: take it from bound_mode */
+} chebfi_params;
+
+/* Create a context on CUDA device `device` (made current on the calling thread).
+ * *out receives the handle; destroy it with chebfi_destroy. */
+int chebfi_create(chebfi_ctx** out, int device);
+int chebfi_destroy(chebfi_ctx* ctx);
+/* Message of the last error on this context (empty string if none); valid until the next call. */
+const char* chebfi_last_error(const chebfi_ctx* ctx);
+
+/* Section 2.1: the cell.  lattice: host, 9 doubles, rows a1, a2, a3 in bohr.
+ * grid: host, FFT sizes N1, N2, N3, each a product of 2, 3 and 5 and at most 256.
+ * kpt: host, 3 doubles, Bloch vector k in Cartesian 1/bohr.  Must precede set_sphere. */
+int chebfi_set_cell(chebfi_ctx* ctx, const double* lattice, const int* grid, const double* kpt);
+
+/* Section 2.1: the plane-wave sphere.  miller: host, npw x 3 int32 (row-major), the integer
+ * coordinates m of G = m1 b1 + m2 b2 + m3 b3 with |m_i| < N_i/2; the row order is the
+ * order of the wavefunction coefficients at this ABI.  Duplicates are an error. */
+int chebfi_set_sphere(chebfi_ctx* ctx, int64_t npw, const int32_t* miller);
+
+/* Section 2.1: the local potential V_loc(r) on the grid, N1*N2*N3 doubles, index
+ * (i1*N2 + i2)*N3 + i3 (third index fastest).  on_device: 1 if vloc is a device pointer. */
+int chebfi_set_vloc(chebfi_ctx* ctx, const double* vloc, int on_device);
+
+/* Section 2.1: projectors and their coefficients.
+ *  P: complex128 column-major npw x nproj with leading dimension ldP >= npw, host or
+ *     device (P_on_device); rows in the sphere order of set_sphere.
+ *  proj_offsets: host, natoms+1 int32, atom a owns projector columns
+ *     [proj_offsets[a], proj_offsets[a+1]); proj_offsets[0] = 0, proj_offsets[natoms] = nproj,
+ *     block sizes 1..64.
+ *  D: host, the per-atom symmetric blocks of D_V concatenated, each n_a x n_a row-major.
+ *  Q: host, same layout for D_S; NULL for S = I (norm-conserving).
+ * Precomputes G = P^H P and the Woodbury core M = Q (I + G Q)^{-1} (Section 4.1) on the
+ * device.  Synchronises; returns CHEBFI_ERR_NOT_SPD if S is not positive definite. */
+int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t ldP,
+                          int P_on_device, int natoms, const int32_t* proj_offsets,
+                          const double* D, const double* Q);
+
+/* Section 4.3: lambda_+ for the filter.  Synchronises. */
+int chebfi_upper_bound(chebfi_ctx* ctx, int mode, double* lambda_hi);
+
+/* Algorithm 1: HY = H Y for nb bands.  prec selects FP64 or FP32 arithmetic (MIXED acts
+ * as F32 here).  Y and HY must not overlap. */
+int chebfi_apply_H(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t ld,
+                   int prec, void* stream);
+/* Algorithm 1: SY = S Y = Y + P Q P^H Y (FP64). */
+int chebfi_apply_S(chebfi_ctx* ctx, const void* Y, void* SY, int64_t nb, int64_t ld, void* stream);
+/* Section 4.1 (Woodbury): out = S^{-1} X = X - P M P^H X (FP64). */
+int chebfi_apply_Sinv(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int64_t ld, void* stream);
+
+/* Algorithm 2's inner loop, in place on Y: psi^1 = (S^{-1}H psi^0 - c psi^0)/r,
+ * psi^i = 2/r (S^{-1}H psi^{i-1} - c psi^{i-1}) - psi^{i-2}, i = 2..degree, with
+ * c = (lambda_hi + lambda_lo)/2, r = (lambda_hi - lambda_lo)/2 and the projection-reuse
+ * identity of Section 4.1.  Requires lambda_hi > lambda_lo. */
+int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree,
+                       double lambda_lo, double lambda_hi, int prec, void* stream);
+
+/* S-orthonormalisation by Cholesky-QR (FP64): G_Y = Y^H S Y = L L^H, Y <- Y L^{-H}.
+ * Synchronises; CHEBFI_ERR_NOT_SPD if G_Y is not positive definite. */
+int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream);
+
+/* Algorithm 2's last three steps (FP64): columns scaled to unit S-norm, H_Psi = Y^H H Y,
+ * S_Psi = Y^H S Y, H_Psi X = S_Psi X Lambda (Cholesky reduction + Jacobi), Y <- Y X.
+ * evals: device, nb doubles, ascending.  resid: device, nb doubles ||H y - lambda S y||_2,
+ * or NULL.  Synchronises. */
+int chebfi_rayleigh_ritz(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb,
+                         int64_t ld, void* stream);
+
+/* Generalized Rayleigh quotients y^H H y / y^H S y of every band (FP64), device nb doubles
+ * (Algorithm 2's first step). */
+int chebfi_rayleigh_quotients(chebfi_ctx* ctx, const void* Y, double* rq, int64_t nb, int64_t ld,
+                              void* stream);
+
+/* Algorithm 2 repeated params->sweeps times on Y (in place): lambda_- = max Rayleigh
+ * quotient, lambda_+ from params, filter, Rayleigh-Ritz.  evals/resid as in
+ * chebfi_rayleigh_ritz.  Synchronises. */
+int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb, int64_t ld,
+                 const chebfi_params* params, void* stream);
+
+/* Synchronise the context's work and return the first device-detected error, if any. */
+int chebfi_sync_status(chebfi_ctx* ctx);
+
+/* Number of kernels the library has launched on this context (monotonic counter). */
+int64_t chebfi_kernel_launches(const chebfi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEBFI_H */

@@ -1,0 +1,210 @@
+"""Python binding of libchebfi: the same operations as the C ABI, on torch CUDA tensors.
+
+Wavefunction blocks are complex128 CUDA tensors of shape (npw, nb) in column-major
+(Fortran) layout: ``Y.stride(0) == 1`` and ``Y.stride(1) = ld >= npw``; ``fortran(x)``
+converts.  Every computation runs in libchebfi's kernels; this module only passes
+pointers, sizes and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import F64, BOUND_PAPER, Params
+
+__all__ = ["ChebFI", "ChebFIError", "fortran"]
+
+
+class ChebFIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("chebfi error %d: %s" % (code, msg))
+        self.code = code
+
+
+def fortran(x, device="cuda") -> torch.Tensor:
+    """(npw, nb) complex128 CUDA tensor in column-major layout from a numpy array or tensor."""
+    t = torch.as_tensor(np.asarray(x) if not isinstance(x, torch.Tensor) else x)
+    t = t.to(device=device, dtype=torch.complex128)
+    if t.dim() == 1:
+        t = t[:, None]
+    return t.T.contiguous().T
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _block(Y):
+    if not (isinstance(Y, torch.Tensor) and Y.is_cuda and Y.dtype == torch.complex128 and Y.dim() == 2):
+        raise TypeError("expected a 2-D complex128 CUDA tensor")
+    if Y.shape[1] > 0 and Y.stride(0) != 1:
+        raise ValueError("wavefunction block must be column-major (use fortran())")
+    ld = Y.stride(1) if Y.shape[1] > 1 else max(Y.shape[0], 1)
+    return ctypes.c_void_p(Y.data_ptr() if Y.numel() else 0), int(Y.shape[1]), int(max(ld, Y.shape[0]))
+
+
+class ChebFI:
+    """One plane-wave problem on one GPU (a libchebfi context)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _lib.load()
+        self.device = device
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            rc = self.lib.chebfi_create(ctypes.byref(h), device)
+        if rc != 0:
+            raise ChebFIError(rc, "chebfi_create failed")
+        self.h = h
+        self.npw = 0
+        self.nproj = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.chebfi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise ChebFIError(rc, self.lib.chebfi_last_error(self.h).decode())
+
+    # -- setup ---------------------------------------------------------------------
+    def set_cell(self, lattice, grid, kpt=(0.0, 0.0, 0.0)):
+        lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(9))
+        g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32).reshape(3))
+        k = np.ascontiguousarray(np.asarray(kpt, dtype=np.float64).reshape(3))
+        self._check(self.lib.chebfi_set_cell(self.h, lat.ctypes.data_as(_lib.P_double),
+                                             g.ctypes.data_as(_lib.P_int), k.ctypes.data_as(_lib.P_double)))
+
+    def set_sphere(self, miller):
+        m = np.ascontiguousarray(np.asarray(miller, dtype=np.int32).reshape(-1, 3))
+        self._check(self.lib.chebfi_set_sphere(self.h, m.shape[0], m.ctypes.data_as(_lib.P_int32)))
+        self.npw = m.shape[0]
+
+    def set_vloc(self, vloc):
+        if isinstance(vloc, torch.Tensor) and vloc.is_cuda:
+            v = vloc.to(torch.float64).contiguous()
+            self._check(self.lib.chebfi_set_vloc(self.h, ctypes.c_void_p(v.data_ptr()), 1))
+            torch.cuda.synchronize()
+        else:
+            v = np.ascontiguousarray(np.asarray(vloc, dtype=np.float64))
+            self._check(self.lib.chebfi_set_vloc(self.h, ctypes.c_void_p(v.ctypes.data), 0))
+
+    def set_projectors(self, P, proj_offsets, D, Q=None):
+        offs = np.ascontiguousarray(np.asarray(proj_offsets, dtype=np.int32))
+        Dn = np.ascontiguousarray(np.asarray(D, dtype=np.float64))
+        Qn = None if Q is None else np.ascontiguousarray(np.asarray(Q, dtype=np.float64))
+        natoms = len(offs) - 1
+        if isinstance(P, torch.Tensor) and P.is_cuda:
+            Pt = P if (P.stride(0) == 1 and P.dtype == torch.complex128) else fortran(P)
+            ptr, ld, on_dev = ctypes.c_void_p(Pt.data_ptr()), Pt.stride(1), 1
+            nproj = Pt.shape[1]
+            keep = Pt
+        else:
+            Pn = np.asfortranarray(np.asarray(P, dtype=np.complex128))
+            nproj = Pn.shape[1]
+            ptr, ld, on_dev = ctypes.c_void_p(Pn.ctypes.data), Pn.shape[0], 0
+            keep = Pn
+        self._check(self.lib.chebfi_set_projectors(
+            self.h, nproj, ptr, ld, on_dev, natoms, offs.ctypes.data_as(_lib.P_int32),
+            Dn.ctypes.data_as(_lib.P_double),
+            None if Qn is None else Qn.ctypes.data_as(_lib.P_double)))
+        del keep
+        self.nproj = nproj
+
+    @classmethod
+    def from_cell(cls, cell, device: int = 0):
+        """Context set up from a ``synth.Cell``-like object (lattice, grid, kpt, miller, vloc,
+        P, proj_offsets, D, Q)."""
+        c = cls(device)
+        c.set_cell(cell.lattice, cell.grid, cell.kpt)
+        c.set_sphere(cell.miller)
+        c.set_vloc(cell.vloc)
+        c.set_projectors(cell.P, cell.proj_offsets, cell.D, cell.Q)
+        return c
+
+    def upper_bound(self, mode: int = BOUND_PAPER) -> float:
+        out = ctypes.c_double()
+        self._check(self.lib.chebfi_upper_bound(self.h, mode, ctypes.byref(out)))
+        return out.value
+
+    # -- operators -------------------------------------------------------------------
+    def _out_like(self, Y):
+        return torch.empty((Y.shape[1], Y.shape[0]), dtype=torch.complex128, device=Y.device).T
+
+    def apply_H(self, Y, prec: int = F64, out=None):
+        out = self._out_like(Y) if out is None else out
+        y, nb, ld = _block(Y)
+        o, _, ldo = _block(out)
+        if ldo != ld:
+            raise ValueError("Y and out must share a leading dimension")
+        self._check(self.lib.chebfi_apply_H(self.h, y, o, nb, ld, prec, _stream()))
+        return out
+
+    def apply_S(self, Y, out=None):
+        out = self._out_like(Y) if out is None else out
+        y, nb, ld = _block(Y)
+        o, _, _ = _block(out)
+        self._check(self.lib.chebfi_apply_S(self.h, y, o, nb, ld, _stream()))
+        return out
+
+    def apply_Sinv(self, X, out=None):
+        out = self._out_like(X) if out is None else out
+        x, nb, ld = _block(X)
+        o, _, _ = _block(out)
+        self._check(self.lib.chebfi_apply_Sinv(self.h, x, o, nb, ld, _stream()))
+        return out
+
+    def cheb_filter(self, Y, degree: int, lambda_lo: float, lambda_hi: float, prec: int = F64):
+        """In place on Y; returns Y."""
+        y, nb, ld = _block(Y)
+        self._check(self.lib.chebfi_cheb_filter(self.h, y, nb, ld, degree, lambda_lo, lambda_hi, prec,
+                                                _stream()))
+        return Y
+
+    def orthonormalise(self, Y):
+        y, nb, ld = _block(Y)
+        self._check(self.lib.chebfi_orthonormalise(self.h, y, nb, ld, _stream()))
+        return Y
+
+    def rayleigh_ritz(self, Y, residuals: bool = True):
+        y, nb, ld = _block(Y)
+        ev = torch.empty(nb, dtype=torch.float64, device=Y.device)
+        rs = torch.empty(nb, dtype=torch.float64, device=Y.device) if residuals else None
+        self._check(self.lib.chebfi_rayleigh_ritz(self.h, y, ctypes.c_void_p(ev.data_ptr()),
+                                                  ctypes.c_void_p(rs.data_ptr()) if rs is not None else None,
+                                                  nb, ld, _stream()))
+        return ev, rs
+
+    def rayleigh_quotients(self, Y):
+        y, nb, ld = _block(Y)
+        rq = torch.empty(nb, dtype=torch.float64, device=Y.device)
+        self._check(self.lib.chebfi_rayleigh_quotients(self.h, y, ctypes.c_void_p(rq.data_ptr()), nb, ld,
+                                                       _stream()))
+        return rq
+
+    def solve(self, Y, degree: int, sweeps: int, prec: int = F64, bound_mode: int = BOUND_PAPER,
+              lambda_hi: float = 0.0):
+        """Algorithm 2 repeated `sweeps` times in place on Y; returns (evals, residual norms)."""
+        y, nb, ld = _block(Y)
+        ev = torch.empty(nb, dtype=torch.float64, device=Y.device)
+        rs = torch.empty(nb, dtype=torch.float64, device=Y.device)
+        p = Params(degree, sweeps, prec, bound_mode, float(lambda_hi))
+        self._check(self.lib.chebfi_solve(self.h, y, ctypes.c_void_p(ev.data_ptr()), ctypes.c_void_p(rs.data_ptr()),
+                                          nb, ld, ctypes.byref(p), _stream()))
+        return ev, rs
+
+    def sync_status(self):
+        self._check(self.lib.chebfi_sync_status(self.h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.chebfi_kernel_launches(self.h))

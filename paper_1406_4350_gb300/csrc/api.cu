@@ -1,0 +1,870 @@
+// C ABI of libchebfi: context, setup (Section 2.1 operators, Section 4.1 Woodbury core),
+// and the orchestration of Algorithm 2 (filter, Rayleigh-Ritz, sweeps) on the device.
+//
+// Internally every wavefunction block is kept in "column-sorted" plane-wave order (the
+// sphere points of one (x, y) FFT column are contiguous, z ascending), which makes the
+// FFT passes read contiguous runs; the caller's order is restored at the ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <stdexcept>
+#include <vector>
+
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace chebfi {
+
+int64_t* g_launch_counter = nullptr;
+
+void after_launch(const char* name) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error{CHEBFI_ERR_CUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e)};
+  if (g_launch_counter) ++*g_launch_counter;
+}
+
+namespace {
+
+__global__ void k_dense_from_blocks(int64_t nproj, const int32_t* atom_of, const int32_t* offs, const int64_t* blk_off,
+                                    const double* blk, double2* out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nproj * nproj) return;
+  const int64_t i = idx % nproj, j = idx / nproj;
+  const int a = atom_of[i];
+  double v = 0.0;
+  if (atom_of[j] == a) {
+    const int o = offs[a], na = offs[a + 1] - o;
+    v = blk[blk_off[a] + (i - o) * na + (j - o)];
+  }
+  out[idx] = make_double2(v, 0.0);
+}
+
+__global__ void k_add_identity(int64_t n, double2* A, int64_t lda) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[i + i * lda].x += 1.0;
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void check_status(chebfi_ctx* ctx, cudaStream_t st, const char* where) {
+  int h = 0;
+  CHEBFI_CUDA(cudaMemcpyAsync(&h, ctx->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  if (h != 0) {
+    int zero = 0;
+    CHEBFI_CUDA(cudaMemcpy(ctx->d_status.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    const char* what = h == CHEBFI_ERR_NOT_SPD ? "matrix not positive definite"
+                       : h == CHEBFI_ERR_NO_CONVERGENCE ? "Jacobi eigensolver did not converge"
+                                                         : "device error";
+    throw Error{h, std::string(where) + ": " + what};
+  }
+}
+
+void require_ready(const chebfi_ctx* ctx) {
+  CHEBFI_REQUIRE(ctx->has_cell && ctx->has_sphere && ctx->has_vloc && ctx->has_proj, CHEBFI_ERR_STATE,
+                 "set_cell, set_sphere, set_vloc and set_projectors must all be called first");
+}
+
+void require_block(const chebfi_ctx* ctx, const void* Y, int64_t nb, int64_t ld) {
+  CHEBFI_REQUIRE(nb >= 0, CHEBFI_ERR_ARG, "nb must be >= 0");
+  CHEBFI_REQUIRE(ld >= ctx->npw, CHEBFI_ERR_ARG, "ld must be >= npw");
+  CHEBFI_REQUIRE(nb == 0 || Y != nullptr, CHEBFI_ERR_ARG, "null wavefunction pointer");
+}
+
+// ------------------------------------------------------------------ operator pieces (sorted order)
+template <typename R> struct Ops;
+template <> struct Ops<double> {
+  static const double2* P(const chebfi_ctx* c) { return c->d_P.p; }
+  static const double2* G(const chebfi_ctx* c) { return c->d_G.p; }
+  static const double2* M(const chebfi_ctx* c) { return c->d_M.p; }
+  static const double* D(const chebfi_ctx* c) { return c->d_Dblk.p; }
+  static DevBuf<double2>* ws(chebfi_ctx* c) { return &c->w.splitk; }
+};
+template <> struct Ops<float> {
+  static const float2* P(const chebfi_ctx* c) { return c->d_Pf.p; }
+  static const float2* G(const chebfi_ctx* c) { return c->d_Gf.p; }
+  static const float2* M(const chebfi_ctx* c) { return c->d_Mf.p; }
+  static const float* D(const chebfi_ctx* c) { return c->d_Dblkf.p; }
+  static DevBuf<float2>* ws(chebfi_ctx* c) { return &c->w.fsplitk; }
+};
+
+// H Y (FP64 or FP32) with the projections p = P^H Y returned; sorted order, ld = npw.
+template <typename R>
+void apply_H_sorted(chebfi_ctx* ctx, const cplx<R>* Y, cplx<R>* HY, cplx<R>* p, cplx<R>* Dp, cplx<R>* T, int64_t nb,
+                    cudaStream_t st) {
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  LocalEpi<R> ep;
+  ep.Y = Y;
+  ep.ldy = npw;
+  ep.Z = HY;
+  ep.ldz = npw;
+  local_apply<R>(ctx, Y, npw, nb, T, ep, st);
+  if (nq > 0) {
+    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, p, nq, st, Ops<R>::ws(ctx));
+    blockdiag_apply<R>(ctx, Ops<R>::D(ctx), p, nq, Dp, nq, nb, st);
+    gemm<R>(false, false, npw, nb, nq, 1.0, Ops<R>::P(ctx), npw, Dp, nq, 1.0, HY, npw, st, Ops<R>::ws(ctx));
+  }
+}
+
+template <typename R> struct FilterBufs {
+  cplx<R>*Ya, *Yb, *Z, *T, *pa, *pb, *pz, *pw, *pq;
+};
+
+// Algorithm 2's inner loop with the projection-reuse identity of Section 4.1, in place on
+// Y (sorted, ld = npw, its buffer is bufs.Ya on entry).  Returns the buffer holding Y_n.
+template <typename R>
+cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb, int degree, double lo, double hi,
+                       cudaStream_t st) {
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
+  cplx<R>*cur = b.Ya, *prev = b.Yb, *pcur = b.pa, *pprev = b.pb;
+  if (nq > 0) gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st, Ops<R>::ws(ctx));
+  for (int k = 0; k < degree; ++k) {
+    const double a = (k == 0 ? 1.0 : 2.0) / r;
+    const double bp = k == 0 ? 0.0 : 1.0;
+    // Z = (K + V_loc) Y_k and T = a (Z - c Y_k) - bp Y_{k-1}, T written over Y_{k-1}
+    LocalEpi<R> ep;
+    ep.Y = cur;
+    ep.ldy = npw;
+    ep.Z = nq > 0 ? b.Z : nullptr;
+    ep.ldz = npw;
+    ep.T = prev;
+    ep.Yprev = k == 0 ? nullptr : prev;
+    ep.ldt = npw;
+    ep.a = (R)a;
+    ep.c = (R)c;
+    ep.bprev = (R)bp;
+    local_apply<R>(ctx, cur, npw, nb, b.T, ep, st);
+    if (nq > 0) {
+      // P^H H Y_k = P^H Z + G D p_k
+      gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, b.Z, npw, 0.0, b.pz, nq, st, Ops<R>::ws(ctx));
+      blockdiag_apply<R>(ctx, Ops<R>::D(ctx), pcur, nq, b.pw, nq, nb, st);
+      gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::G(ctx), nq, b.pw, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx));
+      if (ctx->paw) {
+        // q = M P^H H Y_k;  W = D p_k - q;  P^H S^{-1} H Y_k = P^H H Y_k - G q
+        gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, b.pz, nq, 0.0, b.pq, nq, st, Ops<R>::ws(ctx));
+        axpby<R>(nq, nb, (R)1, b.pw, nq, (R)-1, b.pq, nq, b.pw, nq, st);
+        gemm<R>(false, false, nq, nb, nq, -1.0, Ops<R>::G(ctx), nq, b.pq, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx));
+      }
+      // Y_{k+1} = T + a P W
+      gemm<R>(false, false, npw, nb, nq, a, Ops<R>::P(ctx), npw, b.pw, nq, 1.0, prev, npw, st, Ops<R>::ws(ctx));
+      // p_{k+1} = a (P^H S^{-1} H Y_k - c p_k) - bp p_{k-1}
+      cheb_combine<R>(nq, nb, (R)a, b.pz, nq, (R)c, pcur, nq, (R)bp, k == 0 ? nullptr : pprev, nq, pprev, nq, st);
+    }
+    std::swap(cur, prev);
+    std::swap(pcur, pprev);
+  }
+  return cur;
+}
+
+void ensure_filter_ws(chebfi_ctx* ctx, int64_t nb, int prec) {
+  const size_t ny = (size_t)ctx->npw * nb, np = (size_t)std::max<int64_t>(ctx->nproj, 1) * nb;
+  const size_t nt = local_workspace_elems(ctx, nb);
+  Work& w = ctx->w;
+  w.Ya.alloc(ny);
+  if (prec == CHEBFI_F64) {
+    w.Yb.alloc(ny);
+    w.Z.alloc(ny);
+    w.T1.alloc(nt);
+    w.pa.alloc(np);
+    w.pb.alloc(np);
+    w.pz.alloc(np);
+    w.pw.alloc(np);
+    w.pq.alloc(np);
+  } else {
+    w.fYa.alloc(ny);
+    w.fYb.alloc(ny);
+    w.fZ.alloc(ny);
+    w.fT1.alloc(nt);
+    w.fpa.alloc(np);
+    w.fpb.alloc(np);
+    w.fpz.alloc(np);
+    w.fpw.alloc(np);
+    w.fpq.alloc(np);
+  }
+}
+
+// Filter on the sorted FP64 block ctx->w.Ya (in place).
+void filter_on_Ya(chebfi_ctx* ctx, int64_t nb, int degree, double lo, double hi, int prec, cudaStream_t st) {
+  ensure_filter_ws(ctx, nb, prec);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw;
+  if (prec == CHEBFI_F64) {
+    FilterBufs<double> b{w.Ya.p, w.Yb.p, w.Z.p, w.T1.p, w.pa.p, w.pb.p, w.pz.p, w.pw.p, w.pq.p};
+    double2* out = filter_sorted<double>(ctx, b, nb, degree, lo, hi, st);
+    if (out != w.Ya.p) CHEBFI_CUDA(cudaMemcpyAsync(w.Ya.p, out, sizeof(double2) * npw * nb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    convert(npw, nb, w.Ya.p, npw, w.fYa.p, npw, st);
+    FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
+    float2* out = filter_sorted<float>(ctx, b, nb, degree, lo, hi, st);
+    convert(npw, nb, out, npw, w.Ya.p, npw, st);
+  }
+}
+
+// Rayleigh quotients of the sorted FP64 block Y.
+void rq_sorted(chebfi_ctx* ctx, const double2* Y, int64_t nb, double* rq, cudaStream_t st) {
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  const size_t np = (size_t)std::max<int64_t>(nq, 1) * nb;
+  w.HY.alloc((size_t)npw * nb);
+  w.T1.alloc(local_workspace_elems(ctx, nb));
+  w.pa.alloc(np);
+  w.pb.alloc(np);
+  w.dvec1.alloc(nb);
+  w.dvec2.alloc(nb);
+  apply_H_sorted<double>(ctx, Y, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st);
+  column_dots(npw, nb, Y, npw, w.HY.p, npw, w.dvec1.p, false, st);
+  column_dots(npw, nb, Y, npw, Y, npw, w.dvec2.p, false, st);
+  if (ctx->paw) {
+    blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
+    column_dots(nq, nb, w.pa.p, nq, w.pb.p, nq, w.dvec2.p, true, st);
+  }
+  divide(nb, w.dvec1.p, w.dvec2.p, rq, st);
+}
+
+// Rayleigh-Ritz (Algorithm 2, last three steps) on the sorted FP64 block w.Ya.
+void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStream_t st) {
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  const size_t ny = (size_t)npw * nb, np = (size_t)std::max<int64_t>(nq, 1) * nb, ns = (size_t)nb * nb;
+  w.HY.alloc(ny);
+  w.tmp.alloc(ny);
+  w.T1.alloc(local_workspace_elems(ctx, nb));
+  w.pa.alloc(np);
+  w.pb.alloc(np);
+  w.pc.alloc(np);
+  w.small1.alloc(ns);
+  w.small2.alloc(ns);
+  w.small3.alloc(ns);
+  w.small4.alloc(ns);
+  w.dvec1.alloc(nb);
+  double2* Y = w.Ya.p;
+  DevBuf<double2>* ws = &w.splitk;
+  // H Y and p = P^H Y
+  apply_H_sorted<double>(ctx, Y, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st);
+  double2 *Hs = w.small1.p, *Ss = w.small2.p, *Li = w.small3.p, *X = w.small4.p;
+  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, w.HY.p, npw, 0.0, Hs, nb, st, ws);
+  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws);
+  if (ctx->paw) {
+    blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
+    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws);
+  }
+  hermitize(nb, Hs, nb, st);
+  hermitize(nb, Ss, nb, st);
+  // columns scaled to unit S-norm: S~ = s S s, H~ = s H s with s = diag(S)^{-1/2}
+  diag_of(nb, Ss, nb, w.dvec1.p, st);
+  scale_sym(nb, Hs, nb, w.dvec1.p, st);
+  scale_sym(nb, Ss, nb, w.dvec1.p, st);
+  // S~ = L L^H, C = L^{-1} H~ L^{-H}
+  cholesky(nb, Ss, nb, ctx->d_status.p, st, ws);
+  set_identity(nb, Li, nb, st);
+  trsm_lower(nb, nb, Ss, nb, Li, nb, st, ws);
+  gemm<double>(false, false, nb, nb, nb, 1.0, Li, nb, Hs, nb, 0.0, X, nb, st, ws);
+  gemm<double>(false, true, nb, nb, nb, 1.0, X, nb, Li, nb, 0.0, Hs, nb, st, ws);
+  hermitize(nb, Hs, nb, st);
+  // C = Z Lambda Z^H
+  jacobi_eigh(nb, Hs, nb, evals, X, nb, ctx->d_status.p, st, &w.small5);
+  check_status(ctx, st, "rayleigh_ritz");
+  // rotation R = s L^{-H} Z; Y <- Y R, HY <- HY R, p <- p R
+  gemm<double>(true, false, nb, nb, nb, 1.0, Li, nb, X, nb, 0.0, Ss, nb, st, ws);
+  scale_rows(nb, nb, Ss, nb, w.dvec1.p, st);
+  gemm<double>(false, false, npw, nb, nb, 1.0, Y, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws);
+  std::swap(w.Ya.p, w.tmp.p);  // buffers have equal capacity
+  std::swap(w.Ya.n, w.tmp.n);
+  Y = w.Ya.p;
+  if (resid) {
+    gemm<double>(false, false, npw, nb, nb, 1.0, w.HY.p, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws);  // H Y_new
+    double2* SY = w.HY.p;  // reuse
+    CHEBFI_CUDA(cudaMemcpyAsync(SY, Y, sizeof(double2) * ny, cudaMemcpyDeviceToDevice, st));
+    if (ctx->paw) {
+      gemm<double>(false, false, nq, nb, nb, 1.0, w.pa.p, nq, Ss, nb, 0.0, w.pc.p, nq, st, ws);  // p_new
+      blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pc.p, nq, w.pb.p, nq, nb, st);
+      gemm<double>(false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, SY, npw, st, ws);
+    }
+    residual_norms(npw, nb, w.tmp.p, npw, SY, npw, evals, resid, st);
+  }
+}
+
+// S-orthonormalisation by Cholesky-QR on the sorted FP64 block w.Ya.
+void ortho_on_Ya(chebfi_ctx* ctx, int64_t nb, cudaStream_t st) {
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  const size_t np = (size_t)std::max<int64_t>(nq, 1) * nb, ns = (size_t)nb * nb;
+  w.tmp.alloc((size_t)npw * nb);
+  w.pa.alloc(np);
+  w.pb.alloc(np);
+  w.small2.alloc(ns);
+  w.small3.alloc(ns);
+  DevBuf<double2>* ws = &w.splitk;
+  double2 *Ss = w.small2.p, *Li = w.small3.p, *Y = w.Ya.p;
+  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws);
+  if (ctx->paw) {
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, Y, npw, 0.0, w.pa.p, nq, st, ws);
+    blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
+    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws);
+  }
+  hermitize(nb, Ss, nb, st);
+  cholesky(nb, Ss, nb, ctx->d_status.p, st, ws);
+  check_status(ctx, st, "orthonormalise");
+  set_identity(nb, Li, nb, st);
+  trsm_lower(nb, nb, Ss, nb, Li, nb, st, ws);
+  gemm<double>(false, true, npw, nb, nb, 1.0, Y, npw, Li, nb, 0.0, w.tmp.p, npw, st, ws);
+  std::swap(w.Ya.p, w.tmp.p);
+  std::swap(w.Ya.n, w.tmp.n);
+}
+
+void gather_to_Ya(chebfi_ctx* ctx, const void* Y, int64_t nb, int64_t ld, cudaStream_t st) {
+  ctx->w.Ya.alloc((size_t)ctx->npw * nb);
+  gather_rows(ctx->npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y, ld, ctx->w.Ya.p, ctx->npw, st);
+}
+void scatter_from(chebfi_ctx* ctx, const double2* src, void* Y, int64_t nb, int64_t ld, cudaStream_t st) {
+  scatter_rows(ctx->npw, nb, ctx->d_sorted_to_user.p, src, ctx->npw, (double2*)Y, ld, st);
+}
+
+double cheb_T_abs(int n, double x) {  // |T_n(x)| for |x| >= 1 by its cosh form, else <= 1
+  const double ax = std::fabs(x);
+  if (ax <= 1.0) return 1.0;
+  return std::cosh(n * std::acosh(ax));
+}
+
+double host_max(chebfi_ctx* ctx, const double* d, int64_t n, cudaStream_t st, bool minimum = false) {
+  std::vector<double> h(n);
+  CHEBFI_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  double m = minimum ? INFINITY : -INFINITY;
+  for (double v : h) m = minimum ? std::min(m, v) : std::max(m, v);
+  return m;
+}
+
+double rigorous_bound(chebfi_ctx* ctx) {
+  if (ctx->bound_rigorous >= 0.0) return ctx->bound_rigorous;
+  const int64_t nq = ctx->nproj;
+  double num = ctx->kmax + ctx->vmax;
+  double smin = 1.0;
+  if (nq > 0) {
+    cudaStream_t st = 0;
+    DevBuf<double2> Dd, T, A, V;
+    DevBuf<double> w;
+    Dd.alloc(nq * nq);
+    T.alloc(nq * nq);
+    A.alloc(nq * nq);
+    V.alloc(nq * nq);
+    w.alloc(nq);
+    DevBuf<double2>* ws = &ctx->w.splitk;
+    // eigenvalues of L^H X L, G = P^H P = L L^H, for X = D and X = Q
+    for (int which = 0; which < (ctx->paw ? 2 : 1); ++which) {
+      k_dense_from_blocks<<<nblk(nq * nq), 256>>>(nq, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
+                                                  which == 0 ? ctx->d_Dblk.p : ctx->d_Qblk.p, Dd.p);
+      after_launch("k_dense_from_blocks");
+      gemm<double>(false, false, nq, nq, nq, 1.0, Dd.p, nq, ctx->d_L.p, nq, 0.0, T.p, nq, st, ws);
+      gemm<double>(true, false, nq, nq, nq, 1.0, ctx->d_L.p, nq, T.p, nq, 0.0, A.p, nq, st, ws);
+      hermitize(nq, A.p, nq, st);
+      jacobi_eigh(nq, A.p, nq, w.p, V.p, nq, ctx->d_status.p, st, &ctx->w.small5);
+      check_status(ctx, st, "upper_bound");
+      if (which == 0) num += std::max(0.0, host_max(ctx, w.p, nq, st));
+      else smin = 1.0 + std::min(0.0, host_max(ctx, w.p, nq, st, true));
+    }
+  }
+  ctx->bound_rigorous = std::max(0.0, num) / smin;
+  return ctx->bound_rigorous;
+}
+
+}  // namespace
+}  // namespace chebfi
+
+using namespace chebfi;
+
+#define API_BEGIN(ctx)                                      \
+  if (!(ctx)) return CHEBFI_ERR_ARG;                        \
+  try {                                                     \
+    (ctx)->err.clear();                                     \
+    g_launch_counter = &(ctx)->launches;                    \
+    CHEBFI_CUDA(cudaSetDevice((ctx)->device));
+
+#define API_END(ctx)                                        \
+  }                                                         \
+  catch (const chebfi::Error& e) {                          \
+    (ctx)->err = e.msg;                                     \
+    return e.code;                                          \
+  }                                                         \
+  catch (const std::exception& e) {                         \
+    (ctx)->err = e.what();                                  \
+    return CHEBFI_ERR_CUDA;                                 \
+  }                                                         \
+  return CHEBFI_OK;
+
+extern "C" {
+
+int chebfi_create(chebfi_ctx** out, int device) {
+  if (!out) return CHEBFI_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return CHEBFI_ERR_ARG;
+  chebfi_ctx* ctx = new chebfi_ctx();
+  ctx->device = device;
+  try {
+    CHEBFI_CUDA(cudaSetDevice(device));
+    ctx->d_status.alloc(1);
+    CHEBFI_CUDA(cudaMemset(ctx->d_status.p, 0, sizeof(int)));
+  } catch (const Error&) {
+    delete ctx;
+    return CHEBFI_ERR_CUDA;
+  }
+  *out = ctx;
+  return CHEBFI_OK;
+}
+
+int chebfi_destroy(chebfi_ctx* ctx) {
+  if (!ctx) return CHEBFI_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  delete ctx;
+  return CHEBFI_OK;
+}
+
+const char* chebfi_last_error(const chebfi_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t chebfi_kernel_launches(const chebfi_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int chebfi_set_cell(chebfi_ctx* ctx, const double* lattice, const int* grid, const double* kpt) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(lattice && grid && kpt, CHEBFI_ERR_ARG, "null argument");
+  CHEBFI_REQUIRE(!ctx->has_sphere, CHEBFI_ERR_STATE, "set_cell after set_sphere");
+  for (int i = 0; i < 3; ++i) ctx->ax[i].build(grid[i]);
+  std::memcpy(ctx->lattice, lattice, sizeof(ctx->lattice));
+  std::memcpy(ctx->kpt, kpt, sizeof(ctx->kpt));
+  for (int i = 0; i < 3; ++i) ctx->grid[i] = grid[i];
+  // reciprocal rows b_j with a_i . b_j = 2 pi delta_ij: B = 2 pi (A^{-1})^T
+  const double* a = lattice;
+  const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  CHEBFI_REQUIRE(std::fabs(det) > 1e-12, CHEBFI_ERR_ARG, "singular lattice");
+  double inv[9];  // inverse of A (row-major)
+  inv[0] = (a[4] * a[8] - a[5] * a[7]) / det;
+  inv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+  inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+  inv[3] = (a[5] * a[6] - a[3] * a[8]) / det;
+  inv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+  inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+  inv[6] = (a[3] * a[7] - a[4] * a[6]) / det;
+  inv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+  inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+  for (int j = 0; j < 3; ++j)
+    for (int c = 0; c < 3; ++c) ctx->recip[j * 3 + c] = 2.0 * M_PI * inv[c * 3 + j];
+  ctx->has_cell = true;
+  API_END(ctx)
+}
+
+int chebfi_set_sphere(chebfi_ctx* ctx, int64_t npw, const int32_t* miller) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(ctx->has_cell, CHEBFI_ERR_STATE, "set_cell must precede set_sphere");
+  CHEBFI_REQUIRE(!ctx->has_sphere, CHEBFI_ERR_STATE, "the sphere is already set");
+  CHEBFI_REQUIRE(npw >= 1 && npw < (int64_t)1 << 31 && miller, CHEBFI_ERR_ARG, "bad npw or null miller");
+  const int n1 = ctx->grid[0], n2 = ctx->grid[1], n3 = ctx->grid[2];
+  std::vector<int64_t> key(npw);
+  std::vector<int> zz(npw);
+  for (int64_t i = 0; i < npw; ++i) {
+    const int m[3] = {miller[3 * i], miller[3 * i + 1], miller[3 * i + 2]};
+    for (int d = 0; d < 3; ++d)
+      CHEBFI_REQUIRE(2 * std::abs(m[d]) < ctx->grid[d], CHEBFI_ERR_ARG,
+                     "Miller index outside (-N/2, N/2) at plane wave " + std::to_string(i));
+    const int x = (m[0] % n1 + n1) % n1, y = (m[1] % n2 + n2) % n2, z = (m[2] % n3 + n3) % n3;
+    key[i] = (int64_t)x * n2 + y;
+    zz[i] = z;
+  }
+  std::vector<int32_t> order(npw);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return key[a] != key[b] ? key[a] < key[b] : zz[a] < zz[b];
+  });
+  for (int64_t j = 1; j < npw; ++j)
+    CHEBFI_REQUIRE(!(key[order[j]] == key[order[j - 1]] && zz[order[j]] == zz[order[j - 1]]), CHEBFI_ERR_ARG,
+                   "duplicate plane wave in the sphere");
+  SphereFFT& s = ctx->sph;
+  s.n1 = n1;
+  s.n2 = n2;
+  s.n3 = n3;
+  s.pitch = n2 % 2 ? n2 : n2 + 1;
+  s.zpitch = n3 % 2 ? n3 : n3 + 1;
+  std::vector<int32_t> col_start, pw_line(npw), pw_zrev(npw), col_off;
+  std::vector<char> xact(n1, 0);
+  const std::vector<int>&rx = ctx->ax[0].rev, &ry = ctx->ax[1].rev, &rz = ctx->ax[2].rev;
+  for (int64_t j = 0; j < npw; ++j) {
+    const int32_t u = order[j];
+    if (j == 0 || key[u] != key[order[j - 1]]) {
+      col_start.push_back((int32_t)j);
+      const int x = (int)(key[u] / n2), y = (int)(key[u] % n2);
+      col_off.push_back(rx[x] * s.pitch + ry[y]);
+      xact[x] = 1;
+    }
+    pw_line[j] = (int32_t)col_start.size() - 1;
+    pw_zrev[j] = rz[zz[u]];
+  }
+  s.ncol = (int)col_start.size();
+  col_start.push_back((int32_t)npw);
+  std::vector<int32_t> rows;
+  for (int x = 0; x < n1; ++x)
+    if (xact[x]) rows.push_back(rx[x] * s.pitch);
+  s.nxa = (int)rows.size();
+  s.col_start.upload(col_start.data(), col_start.size());
+  s.pw_line.upload(pw_line.data(), npw);
+  s.pw_zrev.upload(pw_zrev.data(), npw);
+  s.col_off.upload(col_off.data(), col_off.size());
+  s.rows_act.upload(rows.data(), rows.size());
+  ctx->sorted_to_user = order;
+  ctx->d_sorted_to_user.upload(order.data(), npw);
+  // kinetic diagonal |k + G|^2 / 2 (Section 2.1), sorted order
+  std::vector<double> K(npw);
+  std::vector<float> Kf(npw);
+  double kmax = 0.0;
+  for (int64_t j = 0; j < npw; ++j) {
+    const int32_t u = order[j];
+    double g[3];
+    for (int c = 0; c < 3; ++c)
+      g[c] = ctx->kpt[c] + miller[3 * u] * ctx->recip[c] + miller[3 * u + 1] * ctx->recip[3 + c] +
+             miller[3 * u + 2] * ctx->recip[6 + c];
+    K[j] = 0.5 * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    Kf[j] = (float)K[j];
+    kmax = std::max(kmax, K[j]);
+  }
+  ctx->d_K.upload(K.data(), npw);
+  ctx->d_Kf.upload(Kf.data(), npw);
+  ctx->kmax = kmax;
+  ctx->npw = npw;
+  CHEBFI_CUDA(cudaDeviceSynchronize());
+  ctx->has_sphere = true;
+  API_END(ctx)
+}
+
+int chebfi_set_vloc(chebfi_ctx* ctx, const double* vloc, int on_device) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(ctx->has_cell, CHEBFI_ERR_STATE, "set_cell must precede set_vloc");
+  CHEBFI_REQUIRE(vloc, CHEBFI_ERR_ARG, "null vloc");
+  const int n1 = ctx->grid[0], n2 = ctx->grid[1], n3 = ctx->grid[2];
+  const size_t n = (size_t)n1 * n2 * n3;
+  std::vector<double> h(n);
+  if (on_device) CHEBFI_CUDA(cudaMemcpy(h.data(), vloc, n * sizeof(double), cudaMemcpyDeviceToHost));
+  else std::memcpy(h.data(), vloc, n * sizeof(double));
+  std::vector<double> t(n);
+  std::vector<float> tf(n);
+  double vmax = -INFINITY;
+  for (int x = 0; x < n1; ++x)
+    for (int y = 0; y < n2; ++y)
+      for (int z = 0; z < n3; ++z) {
+        const double v = h[((size_t)x * n2 + y) * n3 + z];
+        CHEBFI_REQUIRE(std::isfinite(v), CHEBFI_ERR_ARG, "V_loc is not finite");
+        t[((size_t)z * n1 + x) * n2 + y] = v;
+        tf[((size_t)z * n1 + x) * n2 + y] = (float)v;
+        vmax = std::max(vmax, v);
+      }
+  ctx->d_vt.upload(t.data(), n);
+  ctx->d_vtf.upload(tf.data(), n);
+  CHEBFI_CUDA(cudaDeviceSynchronize());
+  ctx->vmax = vmax;
+  ctx->has_vloc = true;
+  ctx->bound_rigorous = -1.0;
+  API_END(ctx)
+}
+
+int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t ldP, int P_on_device, int natoms,
+                          const int32_t* proj_offsets, const double* D, const double* Q) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(ctx->has_sphere, CHEBFI_ERR_STATE, "set_sphere must precede set_projectors");
+  CHEBFI_REQUIRE(nproj >= 0 && natoms >= 0, CHEBFI_ERR_ARG, "negative size");
+  const int64_t npw = ctx->npw;
+  cudaStream_t st = 0;
+  ctx->nproj = nproj;
+  ctx->natoms = natoms;
+  ctx->paw = false;
+  ctx->bound_rigorous = -1.0;
+  ctx->has_proj = false;
+  if (nproj == 0) {
+    ctx->has_proj = true;
+    return CHEBFI_OK;
+  }
+  CHEBFI_REQUIRE(P && proj_offsets && D && ldP >= npw && natoms >= 1, CHEBFI_ERR_ARG, "bad projector arguments");
+  std::vector<int32_t> offs(proj_offsets, proj_offsets + natoms + 1);
+  CHEBFI_REQUIRE(offs[0] == 0 && offs[natoms] == nproj, CHEBFI_ERR_ARG, "proj_offsets must run from 0 to nproj");
+  std::vector<int32_t> atom_of(nproj);
+  std::vector<int64_t> blk_off(natoms);
+  int64_t nblkv = 0;
+  for (int a = 0; a < natoms; ++a) {
+    const int na = offs[a + 1] - offs[a];
+    CHEBFI_REQUIRE(na >= 1 && na <= 64, CHEBFI_ERR_ARG, "projector block sizes must be 1..64");
+    blk_off[a] = nblkv;
+    nblkv += (int64_t)na * na;
+    for (int i = offs[a]; i < offs[a + 1]; ++i) atom_of[i] = a;
+  }
+  ctx->offs = offs;
+  ctx->d_offs.upload(offs.data(), offs.size());
+  ctx->d_atom_of.upload(atom_of.data(), nproj);
+  ctx->d_blk_off.upload(blk_off.data(), natoms);
+  ctx->d_Dblk.upload(D, nblkv);
+  std::vector<float> Df(D, D + nblkv);
+  ctx->d_Dblkf.upload(Df.data(), nblkv);
+  if (Q) {
+    ctx->d_Qblk.upload(Q, nblkv);
+    ctx->paw = true;
+  }
+  // P in sorted row order
+  ctx->d_P.alloc((size_t)npw * nproj);
+  if (P_on_device) {
+    gather_rows(npw, nproj, ctx->d_sorted_to_user.p, (const double2*)P, ldP, ctx->d_P.p, npw, st);
+  } else {
+    std::vector<double2> h((size_t)npw * nproj);
+    const double2* src = (const double2*)P;
+    for (int64_t i = 0; i < nproj; ++i)
+      for (int64_t j = 0; j < npw; ++j) h[i * npw + j] = src[i * ldP + ctx->sorted_to_user[j]];
+    CHEBFI_CUDA(cudaMemcpy(ctx->d_P.p, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  }
+  DevBuf<double2>* ws = &ctx->w.splitk;
+  // G = P^H P (Section 4.1, precomputed once)
+  ctx->d_G.alloc((size_t)nproj * nproj);
+  gemm<double>(true, false, nproj, nproj, npw, 1.0, ctx->d_P.p, npw, ctx->d_P.p, npw, 0.0, ctx->d_G.p, nproj, st, ws);
+  hermitize(nproj, ctx->d_G.p, nproj, st);
+  // L = chol(G): used by the Woodbury core and the rigorous bound
+  ctx->d_L.alloc((size_t)nproj * nproj);
+  CHEBFI_CUDA(cudaMemcpyAsync(ctx->d_L.p, ctx->d_G.p, sizeof(double2) * nproj * nproj, cudaMemcpyDeviceToDevice, st));
+  cholesky(nproj, ctx->d_L.p, nproj, ctx->d_status.p, st, ws);
+  check_status(ctx, st, "set_projectors (P^H P, projectors linearly dependent?)");
+  if (ctx->paw) {
+    // M = Q (I + G Q)^{-1} = (Q L) B^{-1} L^{-1} with B = I + L^H Q L = R R^H
+    DevBuf<double2> Qd, T, B, Li, Ri, X;
+    const size_t nn = (size_t)nproj * nproj;
+    Qd.alloc(nn);
+    T.alloc(nn);
+    B.alloc(nn);
+    Li.alloc(nn);
+    Ri.alloc(nn);
+    X.alloc(nn);
+    k_dense_from_blocks<<<nblk(nproj * nproj), 256, 0, st>>>(nproj, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
+                                                             ctx->d_Qblk.p, Qd.p);
+    after_launch("k_dense_from_blocks");
+    gemm<double>(false, false, nproj, nproj, nproj, 1.0, Qd.p, nproj, ctx->d_L.p, nproj, 0.0, T.p, nproj, st, ws);
+    gemm<double>(true, false, nproj, nproj, nproj, 1.0, ctx->d_L.p, nproj, T.p, nproj, 0.0, B.p, nproj, st, ws);
+    k_add_identity<<<nblk(nproj), 256, 0, st>>>(nproj, B.p, nproj);
+    after_launch("k_add_identity");
+    hermitize(nproj, B.p, nproj, st);
+    cholesky(nproj, B.p, nproj, ctx->d_status.p, st, ws);
+    check_status(ctx, st, "set_projectors (S = I + P Q P^H is not positive definite)");
+    set_identity(nproj, Li.p, nproj, st);
+    trsm_lower(nproj, nproj, ctx->d_L.p, nproj, Li.p, nproj, st, ws);
+    set_identity(nproj, Ri.p, nproj, st);
+    trsm_lower(nproj, nproj, B.p, nproj, Ri.p, nproj, st, ws);
+    // M = T R^{-H} R^{-1} L^{-1}
+    gemm<double>(false, true, nproj, nproj, nproj, 1.0, T.p, nproj, Ri.p, nproj, 0.0, X.p, nproj, st, ws);
+    gemm<double>(false, false, nproj, nproj, nproj, 1.0, X.p, nproj, Ri.p, nproj, 0.0, B.p, nproj, st, ws);
+    ctx->d_M.alloc(nn);
+    gemm<double>(false, false, nproj, nproj, nproj, 1.0, B.p, nproj, Li.p, nproj, 0.0, ctx->d_M.p, nproj, st, ws);
+    hermitize(nproj, ctx->d_M.p, nproj, st);
+    ctx->d_Mf.alloc(nn);
+    convert(nproj, nproj, ctx->d_M.p, nproj, ctx->d_Mf.p, nproj, st);
+  }
+  ctx->d_Pf.alloc((size_t)npw * nproj);
+  convert(npw, nproj, ctx->d_P.p, npw, ctx->d_Pf.p, npw, st);
+  ctx->d_Gf.alloc((size_t)nproj * nproj);
+  convert(nproj, nproj, ctx->d_G.p, nproj, ctx->d_Gf.p, nproj, st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  ctx->has_proj = true;
+  API_END(ctx)
+}
+
+int chebfi_upper_bound(chebfi_ctx* ctx, int mode, double* lambda_hi) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  CHEBFI_REQUIRE(lambda_hi, CHEBFI_ERR_ARG, "null output");
+  if (mode == CHEBFI_BOUND_PAPER) *lambda_hi = ctx->kmax;
+  else if (mode == CHEBFI_BOUND_RIGOROUS) *lambda_hi = rigorous_bound(ctx);
+  else throw Error{CHEBFI_ERR_ARG, "unknown bound mode"};
+  API_END(ctx)
+}
+
+int chebfi_apply_H(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t ld, int prec, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || HY, CHEBFI_ERR_ARG, "null HY");
+  CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw;
+  const size_t np = (size_t)std::max<int64_t>(ctx->nproj, 1) * nb;
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  w.HY.alloc((size_t)npw * nb);
+  if (prec == CHEBFI_F64) {
+    w.T1.alloc(local_workspace_elems(ctx, nb));
+    w.pa.alloc(np);
+    w.pb.alloc(np);
+    apply_H_sorted<double>(ctx, w.Ya.p, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st);
+  } else {
+    w.fYa.alloc((size_t)npw * nb);
+    w.fZ.alloc((size_t)npw * nb);
+    w.fT1.alloc(local_workspace_elems(ctx, nb));
+    w.fpa.alloc(np);
+    w.fpb.alloc(np);
+    convert(npw, nb, w.Ya.p, npw, w.fYa.p, npw, st);
+    apply_H_sorted<float>(ctx, w.fYa.p, w.fZ.p, w.fpa.p, w.fpb.p, w.fT1.p, nb, st);
+    convert(npw, nb, w.fZ.p, npw, w.HY.p, npw, st);
+  }
+  scatter_from(ctx, w.HY.p, HY, nb, ld, st);
+  API_END(ctx)
+}
+
+int chebfi_apply_S(chebfi_ctx* ctx, const void* Y, void* SY, int64_t nb, int64_t ld, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || SY, CHEBFI_ERR_ARG, "null SY");
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  if (ctx->paw) {
+    const size_t np = (size_t)nq * nb;
+    w.pa.alloc(np);
+    w.pb.alloc(np);
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk);
+    blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
+    gemm<double>(false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk);
+  }
+  scatter_from(ctx, w.Ya.p, SY, nb, ld, st);
+  API_END(ctx)
+}
+
+int chebfi_apply_Sinv(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int64_t ld, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, X, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || out, CHEBFI_ERR_ARG, "null out");
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  gather_to_Ya(ctx, X, nb, ld, st);
+  if (ctx->paw) {
+    // S^{-1} x = x - P M P^H x (Section 4.1)
+    const size_t np = (size_t)nq * nb;
+    w.pa.alloc(np);
+    w.pb.alloc(np);
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk);
+    gemm<double>(false, false, nq, nb, nq, 1.0, ctx->d_M.p, nq, w.pa.p, nq, 0.0, w.pb.p, nq, st, &w.splitk);
+    gemm<double>(false, false, npw, nb, nq, -1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk);
+  }
+  scatter_from(ctx, w.Ya.p, out, nb, ld, st);
+  API_END(ctx)
+}
+
+int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lambda_lo,
+                       double lambda_hi, int prec, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(degree >= 0 && degree <= 1000, CHEBFI_ERR_ARG, "degree out of range");
+  CHEBFI_REQUIRE(std::isfinite(lambda_lo) && std::isfinite(lambda_hi) && lambda_hi > lambda_lo, CHEBFI_ERR_ARG,
+                 "need finite lambda_lo < lambda_hi");
+  CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
+  if (nb == 0 || degree == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  filter_on_Ya(ctx, nb, degree, lambda_lo, lambda_hi, prec, st);
+  scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  API_END(ctx)
+}
+
+int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  ctx->w.tmp.alloc(ctx->w.Ya.n);
+  ortho_on_Ya(ctx, nb, st);
+  scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+int chebfi_rayleigh_ritz(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb, int64_t ld,
+                         void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || evals, CHEBFI_ERR_ARG, "null evals");
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  ctx->w.tmp.alloc(ctx->w.Ya.n);
+  rr_on_Ya(ctx, nb, evals, resid, st);
+  scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+int chebfi_rayleigh_quotients(chebfi_ctx* ctx, const void* Y, double* rq, int64_t nb, int64_t ld, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || rq, CHEBFI_ERR_ARG, "null rq");
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  rq_sorted(ctx, ctx->w.Ya.p, nb, rq, st);
+  API_END(ctx)
+}
+
+int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb, int64_t ld,
+                 const chebfi_params* params, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(params && evals, CHEBFI_ERR_ARG, "null params or evals");
+  CHEBFI_REQUIRE(params->degree >= 1 && params->sweeps >= 1, CHEBFI_ERR_ARG, "degree and sweeps must be >= 1");
+  CHEBFI_REQUIRE(params->prec >= 0 && params->prec <= 2, CHEBFI_ERR_ARG, "bad precision");
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  double hi = params->lambda_hi;
+  if (!(hi > 0.0)) {
+    if (params->bound_mode == CHEBFI_BOUND_PAPER) hi = ctx->kmax;
+    else if (params->bound_mode == CHEBFI_BOUND_RIGOROUS) hi = rigorous_bound(ctx);
+    else throw Error{CHEBFI_ERR_ARG, "unknown bound mode"};
+  }
+  const double eps = params->prec == CHEBFI_F64 ? 2.220446049250313e-16 : params->prec == CHEBFI_F32 ? 1.1920929e-07 : 1.52587890625e-05;
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  ctx->w.tmp.alloc(ctx->w.Ya.n);
+  // the first sweep's lambda_- comes from Rayleigh quotients; later sweeps reuse the Ritz
+  // values of the previous one (the Rayleigh quotients of Ritz vectors)
+  ctx->w.dvec3.alloc(nb);
+  rq_sorted(ctx, ctx->w.Ya.p, nb, ctx->w.dvec3.p, st);
+  double lo = host_max(ctx, ctx->w.dvec3.p, nb, st);
+  double l1 = host_max(ctx, ctx->w.dvec3.p, nb, st, true);
+  for (int s = 0; s < params->sweeps; ++s) {
+    CHEBFI_REQUIRE(hi > lo, CHEBFI_ERR_ARG, "upper bound below the largest Rayleigh quotient");
+    const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
+    if (cheb_T_abs(params->degree, (l1 - c) / r) >= 1.0 / (100.0 * eps))
+      throw Error{CHEBFI_ERR_FILTER_OVERFLOW, "T_n((lambda_1 - c)/r) exceeds 1/(100 eps) of the filter precision"};
+    filter_on_Ya(ctx, nb, params->degree, lo, hi, params->prec, st);
+    ctx->w.tmp.alloc(ctx->w.Ya.n);
+    rr_on_Ya(ctx, nb, evals, resid, st);
+    lo = host_max(ctx, evals, nb, st);
+    l1 = host_max(ctx, evals, nb, st, true);
+  }
+  scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+int chebfi_sync_status(chebfi_ctx* ctx) {
+  API_BEGIN(ctx)
+  CHEBFI_CUDA(cudaDeviceSynchronize());
+  check_status(ctx, 0, "device");
+  API_END(ctx)
+}
+
+}  // extern "C"

@@ -1,0 +1,304 @@
+// Elementwise and reduction kernels of the filter and of Rayleigh-Ritz: the
+// block-diagonal coefficient matrices D_V, D_S of Section 2.1, the Chebyshev three-term
+// combination of Section 3.2, reorderings between the caller's plane-wave order and the
+// column-sorted order of the FFT, column dot products and residual norms.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace chebfi {
+namespace {
+
+inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+template <typename R>
+__global__ void k_blockdiag(int64_t nproj, int64_t nb, const int32_t* __restrict__ atom_of,
+                            const int32_t* __restrict__ offs, const int64_t* __restrict__ blk_off,
+                            const R* __restrict__ D, const cplx<R>* __restrict__ p, int64_t ldp,
+                            cplx<R>* __restrict__ out, int64_t ldo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nproj * nb) return;
+  const int64_t i = idx % nproj, b = idx / nproj;
+  const int a = atom_of[i];
+  const int o = offs[a], na = offs[a + 1] - o;
+  const R* row = D + blk_off[a] + (int64_t)(i - o) * na;
+  const cplx<R>* pb = p + b * ldp + o;
+  R sr = 0, si = 0;
+  for (int j = 0; j < na; ++j) {
+    sr = fma(row[j], pb[j].x, sr);
+    si = fma(row[j], pb[j].y, si);
+  }
+  out[b * ldo + i] = cmake<cplx<R>>(sr, si);
+}
+
+template <typename R>
+__global__ void k_cheb_combine(int64_t m, int64_t nb, R a, const cplx<R>* __restrict__ u, int64_t ldu, R c,
+                               const cplx<R>* __restrict__ x, int64_t ldx, R b, const cplx<R>* y, int64_t ldy,
+                               cplx<R>* out, int64_t ldo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, j = idx / m;
+  const cplx<R> uu = u[i + j * ldu], xx = x[i + j * ldx];
+  cplx<R> yy = cmake<cplx<R>>(0.0, 0.0);
+  if (y) yy = y[i + j * ldy];
+  cplx<R> r;
+  r.x = a * (uu.x - c * xx.x) - b * yy.x;
+  r.y = a * (uu.y - c * xx.y) - b * yy.y;
+  out[i + j * ldo] = r;
+}
+
+template <typename R>
+__global__ void k_axpby(int64_t m, int64_t nb, R alpha, const cplx<R>* x, int64_t ldx, R beta, const cplx<R>* y,
+                        int64_t ldy, cplx<R>* out, int64_t ldo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, j = idx / m;
+  const cplx<R> xx = x[i + j * ldx];
+  cplx<R> r;
+  r.x = alpha * xx.x;
+  r.y = alpha * xx.y;
+  if (y) {
+    const cplx<R> yy = y[i + j * ldy];
+    r.x += beta * yy.x;
+    r.y += beta * yy.y;
+  }
+  out[i + j * ldo] = r;
+}
+
+template <typename A, typename B>
+__global__ void k_convert(int64_t m, int64_t nb, const A* __restrict__ x, int64_t ldx, B* __restrict__ y, int64_t ldy) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, j = idx / m;
+  const A v = x[i + j * ldx];
+  B r;
+  r.x = (decltype(r.x))v.x;
+  r.y = (decltype(r.y))v.y;
+  y[i + j * ldy] = r;
+}
+
+__global__ void k_gather(int64_t m, int64_t nb, const int32_t* __restrict__ perm, const double2* __restrict__ src,
+                         int64_t lds, double2* __restrict__ dst, int64_t ldd) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, j = idx / m;
+  dst[i + j * ldd] = src[perm[i] + j * lds];
+}
+
+__global__ void k_scatter(int64_t m, int64_t nb, const int32_t* __restrict__ perm, const double2* __restrict__ src,
+                          int64_t lds, double2* __restrict__ dst, int64_t ldd) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, j = idx / m;
+  dst[perm[i] + j * ldd] = src[i + j * lds];
+}
+
+// one block per column; fixed-order tree reduction (deterministic)
+__global__ void k_column_dots(int64_t m, const double2* __restrict__ x, int64_t ldx, const double2* __restrict__ y,
+                              int64_t ldy, double* __restrict__ out, int accumulate) {
+  __shared__ double red[256];
+  const int64_t j = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const double2 a = x[i + j * ldx], b = y[i + j * ldy];
+    s += a.x * b.x + a.y * b.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = (accumulate ? out[j] : 0.0) + red[0];
+}
+
+__global__ void k_residual_norms(int64_t m, const double2* __restrict__ h, int64_t ldh, const double2* __restrict__ s,
+                                 int64_t lds, const double* __restrict__ w, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int64_t j = blockIdx.x;
+  const double lam = w[j];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const double2 a = h[i + j * ldh], b = s[i + j * lds];
+    const double rx = a.x - lam * b.x, ry = a.y - lam * b.y;
+    acc += rx * rx + ry * ry;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int hh = blockDim.x / 2; hh > 0; hh >>= 1) {
+    if ((int)threadIdx.x < hh) red[threadIdx.x] += red[threadIdx.x + hh];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sqrt(red[0]);
+}
+
+__global__ void k_divide(int64_t n, const double* num, const double* den, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = num[i] / den[i];
+}
+
+__global__ void k_identity(int64_t n, double2* A, int64_t lda) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  A[i + j * lda] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void k_diag_of(int64_t n, const double2* A, int64_t lda, double* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = A[i + i * lda].x;
+}
+
+__global__ void k_scale_sym(int64_t n, double2* A, int64_t lda, const double* d) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  const double s = 1.0 / sqrt(d[i] * d[j]);
+  double2 v = A[i + j * lda];
+  A[i + j * lda] = make_double2(v.x * s, v.y * s);
+}
+
+__global__ void k_scale_rows(int64_t n, int64_t m, double2* X, int64_t ldx, const double* d) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * m) return;
+  const int64_t i = idx % n, j = idx / n;
+  const double s = 1.0 / sqrt(d[i]);
+  double2 v = X[i + j * ldx];
+  X[i + j * ldx] = make_double2(v.x * s, v.y * s);
+}
+
+__global__ void k_hermitize(int64_t n, double2* A, int64_t lda) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  if (i > j) return;
+  const double2 a = A[i + j * lda], b = A[j + i * lda];
+  const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  A[i + j * lda] = h;
+  A[j + i * lda] = make_double2(h.x, -h.y);
+}
+
+__global__ void k_reduce_max(int64_t n, const double* x, double* out) {
+  __shared__ double red[256];
+  double m = -1e300;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, x[i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+}  // namespace
+
+template <typename R>
+void blockdiag_apply(const chebfi_ctx* ctx, const R* Dblk, const cplx<R>* p, int64_t ldp, cplx<R>* out, int64_t ldo,
+                     int64_t nb, cudaStream_t st) {
+  const int64_t n = ctx->nproj * nb;
+  if (n == 0) return;
+  k_blockdiag<R><<<nblocks(n), 256, 0, st>>>(ctx->nproj, nb, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p, Dblk,
+                                             p, ldp, out, ldo);
+  after_launch("k_blockdiag");
+}
+template void blockdiag_apply<double>(const chebfi_ctx*, const double*, const double2*, int64_t, double2*, int64_t,
+                                      int64_t, cudaStream_t);
+template void blockdiag_apply<float>(const chebfi_ctx*, const float*, const float2*, int64_t, float2*, int64_t,
+                                     int64_t, cudaStream_t);
+
+template <typename R>
+void cheb_combine(int64_t m, int64_t nb, R a, const cplx<R>* u, int64_t ldu, R c, const cplx<R>* x, int64_t ldx, R b,
+                  const cplx<R>* y, int64_t ldy, cplx<R>* out, int64_t ldo, cudaStream_t st) {
+  if (m * nb == 0) return;
+  k_cheb_combine<R><<<nblocks(m * nb), 256, 0, st>>>(m, nb, a, u, ldu, c, x, ldx, b, y, ldy, out, ldo);
+  after_launch("k_cheb_combine");
+}
+template void cheb_combine<double>(int64_t, int64_t, double, const double2*, int64_t, double, const double2*, int64_t,
+                                   double, const double2*, int64_t, double2*, int64_t, cudaStream_t);
+template void cheb_combine<float>(int64_t, int64_t, float, const float2*, int64_t, float, const float2*, int64_t,
+                                  float, const float2*, int64_t, float2*, int64_t, cudaStream_t);
+
+template <typename R>
+void axpby(int64_t m, int64_t nb, R alpha, const cplx<R>* x, int64_t ldx, R beta, const cplx<R>* y, int64_t ldy,
+           cplx<R>* out, int64_t ldo, cudaStream_t st) {
+  if (m * nb == 0) return;
+  k_axpby<R><<<nblocks(m * nb), 256, 0, st>>>(m, nb, alpha, x, ldx, beta, y, ldy, out, ldo);
+  after_launch("k_axpby");
+}
+template void axpby<double>(int64_t, int64_t, double, const double2*, int64_t, double, const double2*, int64_t,
+                            double2*, int64_t, cudaStream_t);
+template void axpby<float>(int64_t, int64_t, float, const float2*, int64_t, float, const float2*, int64_t, float2*,
+                           int64_t, cudaStream_t);
+
+void convert(int64_t m, int64_t nb, const double2* x, int64_t ldx, float2* y, int64_t ldy, cudaStream_t st) {
+  if (m * nb == 0) return;
+  k_convert<double2, float2><<<nblocks(m * nb), 256, 0, st>>>(m, nb, x, ldx, y, ldy);
+  after_launch("k_convert");
+}
+void convert(int64_t m, int64_t nb, const float2* x, int64_t ldx, double2* y, int64_t ldy, cudaStream_t st) {
+  if (m * nb == 0) return;
+  k_convert<float2, double2><<<nblocks(m * nb), 256, 0, st>>>(m, nb, x, ldx, y, ldy);
+  after_launch("k_convert");
+}
+void gather_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, double2* dst,
+                 int64_t ldd, cudaStream_t st) {
+  if (m * nb == 0) return;
+  k_gather<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd);
+  after_launch("k_gather");
+}
+void scatter_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, double2* dst,
+                  int64_t ldd, cudaStream_t st) {
+  if (m * nb == 0) return;
+  k_scatter<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd);
+  after_launch("k_scatter");
+}
+void column_dots(int64_t m, int64_t nb, const double2* x, int64_t ldx, const double2* y, int64_t ldy, double* out,
+                 bool accumulate, cudaStream_t st) {
+  if (nb == 0) return;
+  k_column_dots<<<(unsigned)nb, 256, 0, st>>>(m, x, ldx, y, ldy, out, accumulate ? 1 : 0);
+  after_launch("k_column_dots");
+}
+void residual_norms(int64_t m, int64_t nb, const double2* h, int64_t ldh, const double2* s, int64_t lds,
+                    const double* w, double* out, cudaStream_t st) {
+  if (nb == 0) return;
+  k_residual_norms<<<(unsigned)nb, 256, 0, st>>>(m, h, ldh, s, lds, w, out);
+  after_launch("k_residual_norms");
+}
+void divide(int64_t n, const double* num, const double* den, double* out, cudaStream_t st) {
+  if (n == 0) return;
+  k_divide<<<nblocks(n), 256, 0, st>>>(n, num, den, out);
+  after_launch("k_divide");
+}
+void set_identity(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
+  if (n == 0) return;
+  k_identity<<<nblocks(n * n), 256, 0, st>>>(n, A, lda);
+  after_launch("k_identity");
+}
+void diag_of(int64_t n, const double2* A, int64_t lda, double* d, cudaStream_t st) {
+  if (n == 0) return;
+  k_diag_of<<<nblocks(n), 256, 0, st>>>(n, A, lda, d);
+  after_launch("k_diag_of");
+}
+void scale_sym(int64_t n, double2* A, int64_t lda, const double* d, cudaStream_t st) {
+  if (n == 0) return;
+  k_scale_sym<<<nblocks(n * n), 256, 0, st>>>(n, A, lda, d);
+  after_launch("k_scale_sym");
+}
+void scale_rows(int64_t n, int64_t m, double2* X, int64_t ldx, const double* d, cudaStream_t st) {
+  if (n * m == 0) return;
+  k_scale_rows<<<nblocks(n * m), 256, 0, st>>>(n, m, X, ldx, d);
+  after_launch("k_scale_rows");
+}
+void hermitize(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
+  if (n == 0) return;
+  k_hermitize<<<nblocks(n * n), 256, 0, st>>>(n, A, lda);
+  after_launch("k_hermitize");
+}
+void reduce_max(int64_t n, const double* x, double* out, cudaStream_t st) {
+  k_reduce_max<<<1, 256, 0, st>>>(n, x, out);
+  after_launch("k_reduce_max");
+}
+
+}  // namespace chebfi

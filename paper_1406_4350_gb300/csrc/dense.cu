@@ -1,0 +1,375 @@
+// Dense FP64 linear algebra on the device for the Rayleigh-Ritz step of Algorithm 2 and
+// the Woodbury core of Section 4.1: blocked Cholesky, triangular solve, and a cyclic
+// Jacobi eigensolver for complex Hermitian matrices.
+//
+// Jacobi: each rotation removes one off-diagonal entry a_pq = |a_pq| e^{i phi} of the
+// 2 x 2 block [[a_pp, a_pq], [conj(a_pq), a_qq]]: U = diag(1, e^{-i phi}) [[c, s], [-s, c]]
+// with zeta = (a_qq - a_pp) / (2 |a_pq|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// c = 1/sqrt(1 + t^2), s = t c (the symmetric Schur step of Golub & Van Loan, Section 8.5),
+// applied as A <- U^H A U, V <- V U.  One step applies n/2 disjoint rotations chosen by the
+// circle method (player 0 fixed, the others rotate), one sweep is n-1 steps.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace chebfi {
+namespace {
+
+constexpr int NB = 32;
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+__device__ __forceinline__ void flag_error(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// Unblocked Cholesky of one nb x nb diagonal block (nb <= NB) in shared memory.
+__global__ void k_chol_diag(double2* A, int64_t lda, int nb, int* status) {
+  __shared__ double2 a[NB][NB + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e % nb, j = e / nb;
+    a[i][j] = A[i + j * lda];
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    __shared__ double piv;
+    if (tid == 0) {
+      double d = a[j][j].x;
+      if (!(d > 0.0)) {  // also catches NaN
+        flag_error(status, CHEBFI_ERR_NOT_SPD);
+        d = 1.0;
+      }
+      piv = sqrt(d);
+      a[j][j] = make_double2(piv, 0.0);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
+      a[i][j].x /= piv;
+      a[i][j].y /= piv;
+    }
+    __syncthreads();
+    // trailing update of the lower triangle: a[i][k] -= L[i][j] conj(L[k][j]) for i >= k > j
+    const int m = nb - j - 1;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e % m, k = j + 1 + e / m;
+      if (i >= k) {
+        const double2 li = a[i][j], lk = a[k][j];
+        a[i][k].x -= li.x * lk.x + li.y * lk.y;
+        a[i][k].y -= li.y * lk.x - li.x * lk.y;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e % nb, j = e / nb;
+    A[i + j * lda] = i >= j ? a[i][j] : make_double2(0.0, 0.0);
+  }
+}
+
+// Panel: rows of B (m x nb) <- B L^{-H}, L = nb x nb lower (diagonal real).
+__global__ void k_trsm_right_lh(const double2* __restrict__ L, int64_t ldl, double2* B, int64_t ldb, int64_t m, int nb) {
+  __shared__ double2 l[NB][NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e % nb, j = e / nb;
+    l[i][j] = L[i + j * ldl];
+  }
+  __syncthreads();
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  double2 x[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    if (j < nb) x[j] = B[r + j * ldb];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < nb) {
+      double2 s = x[j];
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k < j) {  // s -= x_k conj(L[j][k])
+          const double2 lj = l[j][k];
+          s.x -= x[k].x * lj.x + x[k].y * lj.y;
+          s.y -= x[k].y * lj.x - x[k].x * lj.y;
+        }
+      }
+      const double d = l[j][j].x;
+      x[j] = make_double2(s.x / d, s.y / d);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    if (j < nb) B[r + j * ldb] = x[j];
+}
+
+// Columns of B (nb x m) <- L^{-1} B, L = nb x nb lower.
+__global__ void k_trsm_left_l(const double2* __restrict__ L, int64_t ldl, double2* B, int64_t ldb, int64_t m, int nb) {
+  __shared__ double2 l[NB][NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e % nb, j = e / nb;
+    l[i][j] = L[i + j * ldl];
+  }
+  __syncthreads();
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  double2 x[NB];
+  double2* b = B + c * ldb;
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < nb) x[i] = b[i];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    if (i < nb) {
+      double2 s = x[i];
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k < i) {  // s -= L[i][k] x_k
+          const double2 li = l[i][k];
+          s.x -= li.x * x[k].x - li.y * x[k].y;
+          s.y -= li.x * x[k].y + li.y * x[k].x;
+        }
+      }
+      const double d = l[i][i].x;
+      x[i] = make_double2(s.x / d, s.y / d);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < nb) b[i] = x[i];
+}
+
+__global__ void k_zero_upper(int64_t n, double2* A, int64_t lda) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  if (i < j) A[i + j * lda] = make_double2(0.0, 0.0);
+}
+
+// ------------------------------------------------------------------ Jacobi
+__device__ __forceinline__ int64_t rr_player(int64_t pos, int64_t round, int64_t n) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n - 1);
+}
+
+struct Rot {
+  double c, s;
+  double2 ph;  // e^{i phi}
+};
+
+__global__ void k_jac_params(int64_t n0, int64_t n, int64_t round, const double2* __restrict__ A, int64_t lda,
+                             Rot* __restrict__ rot, int* __restrict__ pairs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n / 2) return;
+  int64_t p = rr_player(t, round, n), q = rr_player(n - 1 - t, round, n);
+  if (p > q) { const int64_t tmp = p; p = q; q = tmp; }
+  Rot r;
+  r.c = 1.0;
+  r.s = 0.0;
+  r.ph = make_double2(1.0, 0.0);
+  if (q < n0) {  // skip pairs with the padding player
+    const double2 h = A[p + q * lda];
+    const double g = hypot(h.x, h.y);
+    const double app = A[p + p * lda].x, aqq = A[q + q * lda].x;
+    if (g > 1e-300 && g > 1.1102230246251565e-16 * sqrt(fabs(app * aqq))) {
+      const double zeta = (aqq - app) / (2.0 * g);
+      const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+      r.c = 1.0 / sqrt(1.0 + t_ * t_);
+      r.s = t_ * r.c;
+      r.ph = make_double2(h.x / g, h.y / g);
+    }
+  } else {
+    q = -1;
+  }
+  rot[t] = r;
+  pairs[2 * t] = (int)p;
+  pairs[2 * t + 1] = (int)q;
+}
+
+// A <- U^H A on rows p, q (every column j).
+__global__ void k_jac_rows(int64_t h, int64_t n, double2* A, int64_t lda, const Rot* __restrict__ rot,
+                           const int* __restrict__ pairs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= h * n) return;
+  const int64_t t = idx % h, j = idx / h;
+  const int q = pairs[2 * t + 1];
+  if (q < 0) return;
+  const Rot r = rot[t];
+  if (r.s == 0.0) return;
+  const int p = pairs[2 * t];
+  const double2 ap = A[p + j * lda], aq = A[q + j * lda];
+  // conj(u00) = c, conj(u10) = -s ph, conj(u01) = s, conj(u11) = c ph
+  const double2 sph = make_double2(r.s * r.ph.x, r.s * r.ph.y), cph = make_double2(r.c * r.ph.x, r.c * r.ph.y);
+  double2 np, nq;
+  np.x = r.c * ap.x - (sph.x * aq.x - sph.y * aq.y);
+  np.y = r.c * ap.y - (sph.x * aq.y + sph.y * aq.x);
+  nq.x = r.s * ap.x + (cph.x * aq.x - cph.y * aq.y);
+  nq.y = r.s * ap.y + (cph.x * aq.y + cph.y * aq.x);
+  A[p + j * lda] = np;
+  A[q + j * lda] = nq;
+}
+
+// A <- A U and V <- V U on columns p, q (every row i).
+__global__ void k_jac_cols(int64_t h, int64_t n, double2* A, int64_t lda, double2* V, int64_t ldv,
+                           const Rot* __restrict__ rot, const int* __restrict__ pairs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = 2 * n;  // n rows of A then n rows of V
+  if (idx >= h * rows) return;
+  const int64_t i2 = idx % rows, t = idx / rows;
+  const int q = pairs[2 * t + 1];
+  if (q < 0) return;
+  const Rot r = rot[t];
+  if (r.s == 0.0) return;
+  const int p = pairs[2 * t];
+  double2* M = i2 < n ? A : V;
+  const int64_t ld = i2 < n ? lda : ldv;
+  const int64_t i = i2 < n ? i2 : i2 - n;
+  const double2 ap = M[i + p * ld], aq = M[i + q * ld];
+  // u00 = c, u10 = -s conj(ph), u01 = s, u11 = c conj(ph)
+  const double2 sc = make_double2(r.s * r.ph.x, -r.s * r.ph.y), cc = make_double2(r.c * r.ph.x, -r.c * r.ph.y);
+  double2 np, nq;
+  np.x = r.c * ap.x - (aq.x * sc.x - aq.y * sc.y);
+  np.y = r.c * ap.y - (aq.x * sc.y + aq.y * sc.x);
+  nq.x = r.s * ap.x + (aq.x * cc.x - aq.y * cc.y);
+  nq.y = r.s * ap.y + (aq.x * cc.y + aq.y * cc.x);
+  M[i + p * ld] = np;
+  M[i + q * ld] = nq;
+}
+
+// out[0] = sum of |off-diagonal|^2, out[1] = total |A|^2 (single block, fixed order).
+__global__ void k_offnorm(int64_t n, const double2* A, int64_t lda, double* out) {
+  __shared__ double r0[256], r1[256];
+  double s0 = 0, s1 = 0;
+  for (int64_t e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    const double2 a = A[i + j * lda];
+    const double v = a.x * a.x + a.y * a.y;
+    s1 += v;
+    if (i != j) s0 += v;
+  }
+  r0[threadIdx.x] = s0;
+  r1[threadIdx.x] = s1;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      r0[threadIdx.x] += r0[threadIdx.x + h];
+      r1[threadIdx.x] += r1[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = r0[0];
+    out[1] = r1[0];
+  }
+}
+
+// Sort eigenpairs ascending (stable): rank by counting, then permute w and the columns of V.
+__global__ void k_eig_sort(int64_t n, const double2* __restrict__ A, int64_t lda, const double2* __restrict__ Vin,
+                           int64_t ldvi, double* __restrict__ w, double2* __restrict__ Vout, int64_t ldvo) {
+  const int64_t i = blockIdx.x;
+  __shared__ int64_t rank;
+  const double wi = A[i + i * lda].x;
+  if (threadIdx.x == 0) rank = 0;
+  __syncthreads();
+  int64_t cnt = 0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double wj = A[j + j * lda].x;
+    if (wj < wi || (wj == wi && j < i)) ++cnt;
+  }
+  atomicAdd((unsigned long long*)&rank, (unsigned long long)cnt);
+  __syncthreads();
+  const int64_t r = rank;
+  if (threadIdx.x == 0) w[r] = wi;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) Vout[k + r * ldvo] = Vin[k + i * ldvi];
+}
+
+}  // namespace
+
+void cholesky(int64_t n, double2* A, int64_t lda, int* status, cudaStream_t st, DevBuf<double2>* ws) {
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int nb = (int)std::min<int64_t>(NB, n - k0);
+    k_chol_diag<<<1, 256, 0, st>>>(A + k0 + k0 * lda, lda, nb, status);
+    after_launch("k_chol_diag");
+    const int64_t m2 = n - k0 - nb;
+    if (m2 > 0) {
+      double2* L21 = A + (k0 + nb) + k0 * lda;
+      k_trsm_right_lh<<<nblk(m2, 128), 128, 0, st>>>(A + k0 + k0 * lda, lda, L21, lda, m2, nb);
+      after_launch("k_trsm_right_lh");
+      gemm<double>(false, true, m2, m2, nb, -1.0, L21, lda, L21, lda, 1.0, A + (k0 + nb) + (k0 + nb) * lda, lda, st,
+                   ws);
+    }
+  }
+  k_zero_upper<<<nblk(n * n), 256, 0, st>>>(n, A, lda);
+  after_launch("k_zero_upper");
+}
+
+void trsm_lower(int64_t n, int64_t m, const double2* L, int64_t ldl, double2* B, int64_t ldb, cudaStream_t st,
+                DevBuf<double2>* ws) {
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int nb = (int)std::min<int64_t>(NB, n - k0);
+    k_trsm_left_l<<<nblk(m, 128), 128, 0, st>>>(L + k0 + k0 * ldl, ldl, B + k0, ldb, m, nb);
+    after_launch("k_trsm_left_l");
+    const int64_t m2 = n - k0 - nb;
+    if (m2 > 0)
+      gemm<double>(false, false, m2, m, nb, -1.0, L + (k0 + nb) + k0 * ldl, ldl, B + k0, ldb, 1.0, B + k0 + nb, ldb, st,
+                   ws);
+  }
+}
+
+void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int64_t ldv, int* status, cudaStream_t st,
+                 DevBuf<double2>* ws) {
+  if (n0 <= 0) return;
+  if (n0 == 1) {
+    set_identity(1, V, ldv, st);
+    diag_of(1, A, lda, w, st);
+    return;
+  }
+  const int64_t n = n0 + (n0 & 1);  // a padding player never paired for real
+  // workspace: rotations, pair list, norms, and a copy of V for the final sort
+  const size_t rot_c = (size_t)(n / 2) * sizeof(Rot) / sizeof(double2) + 1;
+  const size_t pair_c = (size_t)n * sizeof(int) / sizeof(double2) + 1;
+  const size_t vtmp = (size_t)n0 * n0;
+  ws->alloc(rot_c + pair_c + 2 + vtmp);
+  Rot* rot = reinterpret_cast<Rot*>(ws->p);
+  int* pairs = reinterpret_cast<int*>(ws->p + rot_c);
+  double* nrm = reinterpret_cast<double*>(ws->p + rot_c + pair_c);
+  double2* Vtmp = ws->p + rot_c + pair_c + 2;
+  set_identity(n0, Vtmp, n0, st);
+  const int max_sweeps = 40;
+  double prev_off = INFINITY;
+  bool done = false;
+  for (int sweep = 0; sweep <= max_sweeps && !done; ++sweep) {
+    k_offnorm<<<1, 256, 0, st>>>(n0, A, lda, nrm);
+    after_launch("k_offnorm");
+    double h[2];
+    CHEBFI_CUDA(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+    const double off = std::sqrt(h[0]), tot = std::sqrt(h[1]);
+    // converged: off-diagonal at the rounding level, or no longer decreasing
+    if (off <= 1e-15 * tot || off == 0.0 || (sweep > 2 && off > 0.5 * prev_off && off <= 1e-12 * tot)) {
+      done = true;
+      break;
+    }
+    if (sweep == max_sweeps) break;
+    prev_off = off;
+    for (int64_t round = 0; round < n - 1; ++round) {
+      k_jac_params<<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs);
+      after_launch("k_jac_params");
+      k_jac_rows<<<nblk((n / 2) * n0), 256, 0, st>>>(n / 2, n0, A, lda, rot, pairs);
+      after_launch("k_jac_rows");
+      k_jac_cols<<<nblk((n / 2) * 2 * n0), 256, 0, st>>>(n / 2, n0, A, lda, Vtmp, n0, rot, pairs);
+      after_launch("k_jac_cols");
+    }
+  }
+  if (!done) {
+    int code = CHEBFI_ERR_NO_CONVERGENCE;
+    // record on the device flag as well so chebfi_sync_status sees it
+    CHEBFI_CUDA(cudaMemcpyAsync(status, &code, sizeof(int), cudaMemcpyHostToDevice, st));
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+  }
+  k_eig_sort<<<(unsigned)n0, 128, 0, st>>>(n0, A, lda, Vtmp, n0, w, V, ldv);
+  after_launch("k_eig_sort");
+}
+
+}  // namespace chebfi

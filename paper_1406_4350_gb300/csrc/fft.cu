@@ -1,0 +1,246 @@
+// Local-potential operator of Section 2.1 (Algorithm 1, second step): the sphere
+// coefficients of each band go to real space by an inverse 3D FFT, are multiplied by
+// V_loc(r), and come back by a forward 3D FFT; the kinetic diagonal |k+G|^2/2 is added
+// in the same epilogue.
+//
+// The 3D transform is pruned to the sphere and split into three passes over a
+// "column space" buffer [band][z][column] that holds only the (x, y) columns in which
+// the sphere has points (about 20 % of the N1 x N2 columns):
+//   zinv  : sphere -> z lines of each column (zero elsewhere), inverse FFT along z;
+//   plane : per (band, z) plane in shared memory: inverse FFT along y on the rows that
+//           hold columns, inverse FFT along x, multiply by V_loc, forward FFT along x,
+//           forward FFT along y on those rows; in place on the column buffer;
+//   zfwd  : forward FFT along z, pick the sphere points, scale by 1/(N1 N2 N3), add K psi,
+//           and apply the caller's epilogue (plain, or the Chebyshev three-term update).
+#include <cmath>
+
+#include "fft_core.cuh"
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace chebfi {
+
+void FFTAxis::build(int n_) {
+  n = n_;
+  CHEBFI_REQUIRE(n >= 1 && n <= kMaxN && factor_radices(n, radices), CHEBFI_ERR_ARG,
+                 "FFT size " + std::to_string(n) + " is not a product of 2, 3, 5 up to 256");
+  rev = digit_reversal(n, radices);
+  std::vector<double2> t64(n);
+  std::vector<float2> t32(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)n;
+    t64[k] = make_double2(std::cos(a), -std::sin(a));
+    t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
+  }
+  tw64.upload(t64.data(), n);
+  tw32.upload(t32.data(), n);
+  CHEBFI_CUDA(cudaDeviceSynchronize());
+}
+
+template <> FFTPlan<double> FFTAxis::plan<double>() const {
+  FFTPlan<double> p;
+  p.n = n;
+  p.nst = (int)radices.size();
+  for (int i = 0; i < p.nst; ++i) p.radix[i] = radices[i];
+  p.tw = tw64.p;
+  return p;
+}
+template <> FFTPlan<float> FFTAxis::plan<float>() const {
+  FFTPlan<float> p;
+  p.n = n;
+  p.nst = (int)radices.size();
+  for (int i = 0; i < p.nst; ++i) p.radix[i] = radices[i];
+  p.tw = tw32.p;
+  return p;
+}
+
+namespace {
+
+constexpr int kCB = 16;       // columns per z-pass block
+constexpr int kThreads = 256;
+
+struct SphArgs {
+  int ncol, n3, zpitch;
+  int64_t ldt;        // complex elements per band in the column buffer (n3 * ncolp)
+  int ncolp;
+  const int32_t* col_start;
+  const int32_t* pw_line;
+  const int32_t* pw_zrev;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_zinv(const cplx<R>* __restrict__ Y, int64_t ldy,
+                                                   cplx<R>* __restrict__ T, SphArgs sa, FFTPlan<R> pz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* lines = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int c0 = blockIdx.x * kCB;
+  const int nc = min(kCB, sa.ncol - c0);
+  const int64_t b = blockIdx.y;
+  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
+  for (int i = threadIdx.x; i < kCB * sa.zpitch; i += blockDim.x) lines[i] = zero;
+  __syncthreads();
+  const int j0 = sa.col_start[c0], j1 = sa.col_start[c0 + nc];
+  const cplx<R>* y = Y + b * ldy;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+    lines[(sa.pw_line[j] - c0) * sa.zpitch + sa.pw_zrev[j]] = y[j];
+  __syncthreads();
+  LineMap lm;
+  lm.stride = sa.zpitch;
+  block_fft_dit<+1, R>(lines, nc, lm, 1, pz);
+  cplx<R>* t = T + b * sa.ldt + c0;
+  for (int i = threadIdx.x; i < sa.n3 * nc; i += blockDim.x) {
+    const int z = i / nc, l = i - z * nc;
+    t[(int64_t)z * sa.ncolp + l] = lines[l * sa.zpitch + z];
+  }
+}
+
+struct PlaneArgs {
+  int n1, n2, n3, ncol, nxa, pitch;
+  int64_t ldt;
+  int ncolp;
+  const int32_t* col_off;
+  const int32_t* row_off;  // rev(x) * pitch of each active x
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_plane(cplx<R>* __restrict__ T, const R* __restrict__ Vt,
+                                                    PlaneArgs pa, FFTPlan<R> px, FFTPlan<R> py) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* plane = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int z = blockIdx.x;
+  const int64_t b = blockIdx.y;
+  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
+  for (int i = threadIdx.x; i < pa.n1 * pa.pitch; i += blockDim.x) plane[i] = zero;
+  __syncthreads();
+  cplx<R>* t = T + b * pa.ldt + (int64_t)z * pa.ncolp;
+  for (int c = threadIdx.x; c < pa.ncol; c += blockDim.x) plane[pa.col_off[c]] = t[c];
+  __syncthreads();
+  LineMap rows;
+  rows.off = pa.row_off;
+  LineMap cols;
+  cols.stride = 1;
+  block_fft_dit<+1, R>(plane, pa.nxa, rows, 1, py);        // along y, active rows
+  block_fft_dit<+1, R>(plane, pa.n2, cols, pa.pitch, px);  // along x, every column
+  const R* v = Vt + (int64_t)z * pa.n1 * pa.n2;
+  for (int i = threadIdx.x; i < pa.n1 * pa.n2; i += blockDim.x) {
+    const int x = i / pa.n2, yy = i - x * pa.n2;
+    cplx<R>& e = plane[x * pa.pitch + yy];
+    const R s = v[i];
+    e.x *= s;
+    e.y *= s;
+  }
+  __syncthreads();
+  block_fft_dif<-1, R>(plane, pa.n2, cols, pa.pitch, px);  // along x
+  block_fft_dif<-1, R>(plane, pa.nxa, rows, 1, py);        // along y, active rows
+  for (int c = threadIdx.x; c < pa.ncol; c += blockDim.x) t[c] = plane[pa.col_off[c]];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_zfwd(const cplx<R>* __restrict__ T, SphArgs sa, FFTPlan<R> pz,
+                                                   const R* __restrict__ K, LocalEpi<R> ep) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* lines = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int c0 = blockIdx.x * kCB;
+  const int nc = min(kCB, sa.ncol - c0);
+  const int64_t b = blockIdx.y;
+  const cplx<R>* t = T + b * sa.ldt + c0;
+  for (int i = threadIdx.x; i < sa.n3 * nc; i += blockDim.x) {
+    const int z = i / nc, l = i - z * nc;
+    lines[l * sa.zpitch + z] = t[(int64_t)z * sa.ncolp + l];
+  }
+  __syncthreads();
+  LineMap lm;
+  lm.stride = sa.zpitch;
+  block_fft_dif<-1, R>(lines, nc, lm, 1, pz);
+  const int j0 = sa.col_start[c0], j1 = sa.col_start[c0 + nc];
+  const cplx<R>* y = ep.Y + b * ep.ldy;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    cplx<R> v = lines[(sa.pw_line[j] - c0) * sa.zpitch + sa.pw_zrev[j]];
+    const cplx<R> yj = y[j];
+    const R k = K[j];
+    cplx<R> zj;
+    zj.x = v.x * ep.inv_n3 + k * yj.x;
+    zj.y = v.y * ep.inv_n3 + k * yj.y;
+    if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
+    if (ep.T) {
+      // three-term update without its nonlocal part: T = a (Z - c Y) - bprev Yprev
+      cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
+      if (ep.Yprev) tp = ep.Yprev[b * ep.ldt + j];
+      cplx<R> o;
+      o.x = ep.a * (zj.x - ep.c * yj.x) - ep.bprev * tp.x;
+      o.y = ep.a * (zj.y - ep.c * yj.y) - ep.bprev * tp.y;
+      ep.T[b * ep.ldt + j] = o;
+    }
+  }
+}
+
+template <typename R> void set_smem(const void* f, size_t bytes) {
+  CHEBFI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+}  // namespace
+
+size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb) {
+  const int ncolp = (ctx->sph.ncol + 15) / 16 * 16;
+  return (size_t)ctx->grid[2] * ncolp * (size_t)nb;
+}
+
+// (K + V_loc) applied to nb bands of sorted-order coefficients Y; the column buffer T
+// must hold local_workspace_elems(ctx, nb) complex values.
+template <typename R>
+void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T,
+                 LocalEpi<R> ep, cudaStream_t st) {
+  if (nb <= 0) return;
+  const SphereFFT& s = ctx->sph;
+  SphArgs sa;
+  sa.ncol = s.ncol;
+  sa.n3 = s.n3;
+  sa.zpitch = s.zpitch;
+  sa.ncolp = (s.ncol + 15) / 16 * 16;
+  sa.ldt = (int64_t)s.n3 * sa.ncolp;
+  sa.col_start = s.col_start.p;
+  sa.pw_line = s.pw_line.p;
+  sa.pw_zrev = s.pw_zrev.p;
+  PlaneArgs pa;
+  pa.n1 = s.n1;
+  pa.n2 = s.n2;
+  pa.n3 = s.n3;
+  pa.ncol = s.ncol;
+  pa.nxa = s.nxa;
+  pa.pitch = s.pitch;
+  pa.ldt = sa.ldt;
+  pa.ncolp = sa.ncolp;
+  pa.col_off = s.col_off.p;
+  pa.row_off = s.rows_act.p;
+  const FFTPlan<R> px = ctx->ax[0].plan<R>(), py = ctx->ax[1].plan<R>(), pz = ctx->ax[2].plan<R>();
+  const size_t zbytes = (size_t)kCB * s.zpitch * sizeof(cplx<R>);
+  const size_t pbytes = (size_t)s.n1 * s.pitch * sizeof(cplx<R>);
+  CHEBFI_REQUIRE(pbytes <= 227 * 1024, CHEBFI_ERR_ARG, "FFT plane does not fit in shared memory");
+  set_smem<R>((const void*)k_plane<R>, pbytes);
+  set_smem<R>((const void*)k_zinv<R>, zbytes);
+  set_smem<R>((const void*)k_zfwd<R>, zbytes);
+  const R* K = sizeof(R) == 8 ? (const R*)ctx->d_K.p : (const R*)ctx->d_Kf.p;
+  const R* V = sizeof(R) == 8 ? (const R*)ctx->d_vt.p : (const R*)ctx->d_vtf.p;
+  // grid.y is limited to 65535: walk the bands in chunks
+  for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
+    const int nbc = (int)std::min<int64_t>(65535, nb - b0);
+    dim3 gz((s.ncol + kCB - 1) / kCB, nbc);
+    k_zinv<R><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, sa, pz);
+    after_launch("k_zinv");
+    k_plane<R><<<dim3(s.n3, nbc), kThreads, pbytes, st>>>(T, V, pa, px, py);
+    after_launch("k_plane");
+    LocalEpi<R> e = ep;
+    e.Y = ep.Y + b0 * ep.ldy;
+    if (e.Z) e.Z = ep.Z + b0 * ep.ldz;
+    if (e.T) e.T = ep.T + b0 * ep.ldt;
+    if (e.Yprev) e.Yprev = ep.Yprev + b0 * ep.ldt;
+    e.inv_n3 = (R)(1.0 / ((double)s.n1 * s.n2 * s.n3));
+    k_zfwd<R><<<gz, kThreads, zbytes, st>>>(T, sa, pz, K, e);
+    after_launch("k_zfwd");
+  }
+}
+
+template void local_apply<double>(chebfi_ctx*, const double2*, int64_t, int64_t, double2*, LocalEpi<double>, cudaStream_t);
+template void local_apply<float>(chebfi_ctx*, const float2*, int64_t, int64_t, float2*, LocalEpi<float>, cudaStream_t);
+
+}  // namespace chebfi

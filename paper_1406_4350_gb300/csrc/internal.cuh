@@ -1,0 +1,176 @@
+// Internal declarations shared by the translation units of libchebfi.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/chebfi.h"
+
+namespace chebfi {
+
+// ----------------------------------------------------------------------------- complex
+template <typename R> struct cplx_t;
+template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<float> { using type = float2; };
+template <typename R> using cplx = typename cplx_t<R>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(double re, double im) {
+  C z; z.x = (decltype(z.x))re; z.y = (decltype(z.y))im; return z;
+}
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ double2 conjg(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 conjg(float2 a) { return make_float2(a.x, -a.y); }
+
+// ----------------------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define CHEBFI_CUDA(call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::chebfi::Error{CHEBFI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define CHEBFI_REQUIRE(cond, code, text)                                                   \
+  do {                                                                                     \
+    if (!(cond)) throw ::chebfi::Error{(code), (text)};                                    \
+  } while (0)
+
+// Checked kernel launch: counts the launch and turns a launch error into an exception.
+void after_launch(const char* name);
+extern int64_t* g_launch_counter;
+
+// ----------------------------------------------------------------------------- device buffers
+template <typename T> struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {  // discards contents
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error{CHEBFI_ERR_NOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                        " bytes: " + cudaGetErrorString(e)};
+    }
+    n = count;
+  }
+  void upload(const T* host, size_t count, cudaStream_t s = 0) {
+    alloc(count);
+    if (count) CHEBFI_CUDA(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+};
+
+// ----------------------------------------------------------------------------- FFT plan
+constexpr int kMaxStages = 12;
+constexpr int kMaxN = 256;
+
+template <typename R> struct FFTPlan {
+  int n = 0;
+  int nst = 0;
+  int radix[kMaxStages] = {0};  // DIT stage order r_1 .. r_k
+  const cplx<R>* tw = nullptr;  // tw[k] = exp(-2 pi i k / n)
+};
+
+struct FFTAxis {
+  int n = 0;
+  std::vector<int> radices;
+  std::vector<int> rev;  // digit-reversed position of index i
+  DevBuf<double2> tw64;
+  DevBuf<float2> tw32;
+  void build(int n_);
+  template <typename R> FFTPlan<R> plan() const;
+};
+
+// Geometry of the pruned 3-pass FFT (sphere -> z lines -> planes -> z lines -> sphere).
+struct SphereFFT {
+  int n1 = 0, n2 = 0, n3 = 0;
+  int ncol = 0;      // number of (x, y) columns holding sphere points
+  int nxa = 0;       // number of x indices holding any column
+  int pitch = 0;     // row pitch of a plane in shared memory (complex elements)
+  int zpitch = 0;    // pitch of a z line in shared memory
+  DevBuf<int32_t> col_start;   // ncol+1, sphere points of column c: [col_start[c], col_start[c+1])
+  DevBuf<int32_t> pw_line;     // sorted sphere point -> column index
+  DevBuf<int32_t> pw_zrev;     // sorted sphere point -> digit-reversed z position
+  DevBuf<int32_t> col_off;     // column -> offset rev(x)*pitch + rev(y) in the plane
+  DevBuf<int32_t> rows_act;    // active rows rev(x) of the plane (nxa)
+};
+
+// Workspace grown on demand (never shrinks while the context lives).
+struct Work {
+  DevBuf<double2> Ya, Yb, Yc, Z, HY, T1, T2, tmp, tmp2;   // FP64 (npw x nb or grid)
+  DevBuf<float2> fYa, fYb, fZ, fT1, fT2, ftmp;            // FP32 filter iterates
+  DevBuf<double2> pa, pb, pc, pz, pw, pq, pt;             // nproj x nb projections (FP64)
+  DevBuf<float2> fpa, fpb, fpz, fpw, fpq, fpt;            // FP32 projections
+  DevBuf<double2> small1, small2, small3, small4, small5;  // nb x nb
+  DevBuf<double> dvec1, dvec2, dvec3;
+  DevBuf<double2> splitk;
+  DevBuf<float2> fsplitk;
+};
+
+}  // namespace chebfi
+
+struct chebfi_ctx {
+  int device = 0;
+  std::string err;
+  int64_t launches = 0;
+
+  bool has_cell = false, has_sphere = false, has_vloc = false, has_proj = false;
+  double lattice[9] = {0}, recip[9] = {0}, kpt[3] = {0};
+  int grid[3] = {0, 0, 0};
+  chebfi::FFTAxis ax[3];
+
+  int64_t npw = 0;
+  std::vector<int32_t> sorted_to_user;  // host copy
+  chebfi::DevBuf<int32_t> d_sorted_to_user;
+  chebfi::SphereFFT sph;
+  chebfi::DevBuf<double> d_K;
+  chebfi::DevBuf<float> d_Kf;
+  double kmax = 0.0;
+
+  chebfi::DevBuf<double> d_vt;   // V_loc, plane-major [z][x][y]
+  chebfi::DevBuf<float> d_vtf;
+  double vmax = 0.0;
+
+  int64_t nproj = 0;
+  int natoms = 0;
+  bool paw = false;
+  std::vector<int32_t> offs;
+  chebfi::DevBuf<int32_t> d_offs;
+  chebfi::DevBuf<int32_t> d_atom_of;          // projector -> atom
+  chebfi::DevBuf<double> d_Dblk, d_Qblk;      // packed blocks (row-major per atom)
+  chebfi::DevBuf<int64_t> d_blk_off;          // atom -> offset of its block
+  chebfi::DevBuf<double2> d_P, d_G, d_M, d_L; // P sorted rows (npw x nproj), G = P^H P, Woodbury M, chol(G)
+  chebfi::DevBuf<float2> d_Pf, d_Gf, d_Mf;
+  chebfi::DevBuf<float> d_Dblkf;
+  chebfi::DevBuf<int> d_status;               // device error flag
+  chebfi::Work w;
+  double bound_rigorous = -1.0;
+};

@@ -1,0 +1,97 @@
+// Launchers of the device kernels (one translation unit each: fft.cu, gemm.cu,
+// blas.cu, dense.cu).  All matrices are column-major; complex values interleaved.
+#pragma once
+
+#include "internal.cuh"
+
+namespace chebfi {
+
+// ---------------------------------------------------------------- local operator (fft.cu)
+// Epilogue of the (K + V_loc) pass for sphere point j of band b:
+//   Z = K_j Y_j + (V_loc Y)_j                      -> Z[b*ldz + j]     (if Z)
+//   T = a (Z - c Y_j) - bprev Yprev[b*ldt + j]     -> T[b*ldt + j]     (if T; may alias Yprev)
+template <typename R> struct LocalEpi {
+  const cplx<R>* Y = nullptr;
+  int64_t ldy = 0;
+  cplx<R>* Z = nullptr;
+  int64_t ldz = 0;
+  cplx<R>* T = nullptr;
+  const cplx<R>* Yprev = nullptr;
+  int64_t ldt = 0;
+  R a = 0, c = 0, bprev = 0, inv_n3 = 0;
+};
+size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb);
+template <typename R>
+void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T, LocalEpi<R> ep,
+                 cudaStream_t st);
+
+// ---------------------------------------------------------------- complex GEMM (gemm.cu)
+// C = alpha op(A) op(B) + beta C, op = identity or conjugate transpose; real alpha, beta.
+// M x N result, inner dimension K.  ws: optional split-K workspace (nullptr = no split).
+template <typename R>
+void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A,
+          int64_t lda, const cplx<R>* B, int64_t ldb, double beta, cplx<R>* C, int64_t ldc, cudaStream_t st,
+          DevBuf<cplx<R>>* ws = nullptr);
+
+// ---------------------------------------------------------------- small kernels (blas.cu)
+// out = Dbd p: block-diagonal real D (packed row-major per-atom blocks) times complex p.
+template <typename R>
+void blockdiag_apply(const chebfi_ctx* ctx, const R* Dblk, const cplx<R>* p, int64_t ldp, cplx<R>* out,
+                     int64_t ldo, int64_t nb, cudaStream_t st);
+// out = a (u - c x) - b y   (elementwise on an m x nb block; y may be null, out may alias y)
+template <typename R>
+void cheb_combine(int64_t m, int64_t nb, R a, const cplx<R>* u, int64_t ldu, R c, const cplx<R>* x,
+                  int64_t ldx, R b, const cplx<R>* y, int64_t ldy, cplx<R>* out, int64_t ldo, cudaStream_t st);
+// out = alpha x + beta y (y may be null)
+template <typename R>
+void axpby(int64_t m, int64_t nb, R alpha, const cplx<R>* x, int64_t ldx, R beta, const cplx<R>* y, int64_t ldy,
+           cplx<R>* out, int64_t ldo, cudaStream_t st);
+// copy with precision conversion
+void convert(int64_t m, int64_t nb, const double2* x, int64_t ldx, float2* y, int64_t ldy, cudaStream_t st);
+void convert(int64_t m, int64_t nb, const float2* x, int64_t ldx, double2* y, int64_t ldy, cudaStream_t st);
+// sorted <-> caller order: dst[:, b] = src[perm[:], b]  or  dst[perm[:], b] = src[:, b]
+void gather_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, double2* dst,
+                 int64_t ldd, cudaStream_t st);
+void scatter_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, double2* dst,
+                  int64_t ldd, cudaStream_t st);
+// out[b] = Re sum_j conj(x_jb) y_jb  (+= if accumulate)
+void column_dots(int64_t m, int64_t nb, const double2* x, int64_t ldx, const double2* y, int64_t ldy,
+                 double* out, bool accumulate, cudaStream_t st);
+// out[b] = || h_b - w_b s_b ||_2
+void residual_norms(int64_t m, int64_t nb, const double2* h, int64_t ldh, const double2* s, int64_t lds,
+                    const double* w, double* out, cudaStream_t st);
+// out[b] = num[b] / den[b]
+void divide(int64_t n, const double* num, const double* den, double* out, cudaStream_t st);
+// identity matrix n x n
+void set_identity(int64_t n, double2* A, int64_t lda, cudaStream_t st);
+// A[i, j] = s_i A[i, j] s_j with s_i = 1/sqrt(Re d_i)  (d = diagonal of S taken before)
+void diag_of(int64_t n, const double2* A, int64_t lda, double* d, cudaStream_t st);
+void scale_sym(int64_t n, double2* A, int64_t lda, const double* d, cudaStream_t st);
+// rows of X scaled by 1/sqrt(d): X[i, j] /= sqrt(d_i)
+void scale_rows(int64_t n, int64_t m, double2* X, int64_t ldx, const double* d, cudaStream_t st);
+// A <- (A + A^H) / 2
+void hermitize(int64_t n, double2* A, int64_t lda, cudaStream_t st);
+// max over an array (device scalar out)
+void reduce_max(int64_t n, const double* x, double* out, cudaStream_t st);
+// y = D x for a real matrix D (n x n) applied to complex block x: used for Q p
+// zero-fill
+template <typename T> void zero(T* p, size_t count, cudaStream_t st) {
+  CHEBFI_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), st));
+}
+
+// ---------------------------------------------------------------- dense FP64 (dense.cu)
+// In-place Cholesky A = L L^H of a Hermitian positive definite n x n matrix (lower
+// triangle referenced and overwritten, upper set to zero).  On a non-positive pivot the
+// device flag *status gets CHEBFI_ERR_NOT_SPD (first failure wins) and the pivot is
+// replaced by 1 so the computation stays finite.
+void cholesky(int64_t n, double2* A, int64_t lda, int* status, cudaStream_t st, DevBuf<double2>* ws);
+// B <- L^{-1} B for lower-triangular L (n x n) and B (n x m).
+void trsm_lower(int64_t n, int64_t m, const double2* L, int64_t ldl, double2* B, int64_t ldb, cudaStream_t st,
+                DevBuf<double2>* ws);
+// Eigenvalues (ascending, w[n]) and eigenvectors (V, n x n) of a Hermitian n x n matrix A
+// (destroyed).  Cyclic Jacobi with round-robin pairs; sets *status to
+// CHEBFI_ERR_NO_CONVERGENCE on the sweep limit.  Synchronises the stream (sweep test).
+void jacobi_eigh(int64_t n, double2* A, int64_t lda, double* w, double2* V, int64_t ldv, int* status,
+                 cudaStream_t st, DevBuf<double2>* ws);
+
+}  // namespace chebfi
