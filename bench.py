@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the Chebyshev-filtered subspace iteration on GB300.
+
+Workload ("paw96"): cubic 40-bohr PAW cell, FFT grid 96^3, G-sphere of 60005 plane waves,
+2048 bands, 256 atoms x 8 projectors (N_proj = 2048), seeded synthetic inputs, Chebyshev
+degree 4.  One step is one pass of Algorithm 2 through the public API: the filter of
+degree 4 on all 2048 bands (cheb_filter) followed by Rayleigh-Ritz in FP64
+(rayleigh_ritz); lambda_- of the next step is the largest Ritz value.
+
+Metric: filter band-H-applications per second = bands x degree / time inside the filter,
+for the filter form given by --prec (default: the mixed form).  The FP64 form is timed on
+the same workload and reported beside it.  The inputs (2 GB per wavefunction block) are
+larger than the 129 MB L2, so no L2 flush is needed between timed steps.
+
+--impl reference times the FP64 oracle (the plain numpy restatement of the method) on the
+host cores on a bounded sample of the same workload, with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Filter band-H-applies/s (mixed vs FP64 form) at <=1e-8 Ha eigenvalue error"
+UNIT = "band-H-applies/s"
+WORKLOAD = "paw96"
+DEGREE = 4
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks sampler
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def oracle_rate(cell, nbands_sample: int, degree: int):
+    """The FP64 oracle's Algorithm-2 filter on a sample of bands: band-applies/s, seconds."""
+    import numpy as np
+    from oracle import chebyshev as ch
+    from oracle.planewave import PWOperator
+    op = PWOperator.from_cell(cell)
+    Y = np.asfortranarray(cell.Y0[:, :nbands_sample])
+    lo, hi = 1.0, float(op.K.max()) + 10.0
+    t0 = time.perf_counter()
+    ch.filter_reuse(op, Y, degree, lo, hi)
+    dt = time.perf_counter() - t0
+    return nbands_sample * degree / dt, dt
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from synth import config_cell
+    cell = config_cell(WORKLOAD)
+    sample = args.ref_bands
+    for _ in range(args.warmup):
+        oracle_rate(cell, sample, DEGREE)
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, dt = oracle_rate(cell, sample, DEGREE)
+        rates.append(r)
+        secs.append(dt)
+    value = sample * DEGREE * args.steps / sum(secs)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (96^3 grid, 60005 plane waves, 2048 projectors, PAW, degree 4)",
+                   "sample": "%d of 2048 bands per step" % sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d bands x degree %d per step; includes the oracle's own P^H P and "
+                                   "reduced-matrix setup each call; numpy FFTs single-threaded, BLAS on all "
+                                   "cores" % (sample, DEGREE)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ native arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--prec", default="f32", choices=["mixed", "f32", "f64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64-form filter calls (0: skip)")
+    ap.add_argument("--cpu-bands", type=int, default=16, help="bands in the oracle's timed CPU sample")
+    ap.add_argument("--ref-bands", type=int, default=4)
+    ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
+    ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    from paper_1406_4350_gb300 import build as b
+    from paper_1406_4350_gb300 import F32, F64, MIXED, BOUND_RIGOROUS
+    from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    from synth import config_cell
+    b.build()
+    prec = {"mixed": MIXED, "f32": F32, "f64": F64}[args.prec]
+
+    cell = config_cell(args.workload, nbands=args.nbands)
+    nb, npw, nq = cell.nbands, cell.npw, cell.nproj
+    g = ChebFI.from_cell(cell, device=local)
+    hi = g.upper_bound(BOUND_RIGOROUS)
+    Y = fortran(cell.Y0, device="cuda:%d" % local)
+    lo = float(g.rayleigh_quotients(Y).max().item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(p, timed=None):
+        nonlocal lo
+        st = torch.cuda.current_stream()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        g.cheb_filter(Y, DEGREE, lo, hi, prec=p)
+        e1.record(st)
+        ev, rs = g.rayleigh_ritz(Y)
+        e2.record(st)
+        lo = float(ev.max().item())
+        if timed is not None:
+            timed.append((e0, e1, e2, ev, rs))
+
+    for _ in range(args.warmup):
+        step(prec)
+    barrier()
+    launches0 = g.kernel_launches
+    timed = []
+    g.profile(True)
+    with Clocks(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(prec, timed)
+        barrier()
+        wall = time.perf_counter() - t0
+    g.profile(False)
+    launches = g.kernel_launches - launches0
+    prof = g.profile_totals()
+    filt_ms = [a.elapsed_time(b_) for a, b_, c, _, _ in timed]
+    rr_ms = [b_.elapsed_time(c) for a, b_, c, _, _ in timed]
+    step_ms = [a.elapsed_time(c) for a, b_, c, _, _ in timed]
+    ev_last = timed[-1][3].cpu().numpy()
+    rs_last = timed[-1][4].cpu().numpy()
+    filt_s = sum(filt_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([filt_s, sum(step_ms) / 1e3], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        filt_s, step_total = t.tolist()
+    else:
+        step_total = sum(step_ms) / 1e3
+    value = world * nb * DEGREE * args.steps / filt_s
+
+    # FP64 form of the same filter, same workload
+    fp64 = None
+    if args.fp64_steps > 0 and prec != F64:
+        Yc = Y.clone()
+        st = torch.cuda.current_stream()
+        g.cheb_filter(Yc, DEGREE, lo, hi, prec=F64)
+        Yc.copy_(Y)
+        barrier()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(args.fp64_steps):
+            g.cheb_filter(Yc, DEGREE, lo, hi, prec=F64)
+        c.record(st)
+        barrier()
+        ms = a.elapsed_time(c)
+        fp64 = {"value": nb * DEGREE * args.fp64_steps / (ms / 1e3), "unit": UNIT,
+                "ms_per_filter": ms / args.fp64_steps, "dtype": "f64"}
+        del Yc
+
+    # end to end through the public API with host buffers: pinned H2D of the block,
+    # the filter, D2H of the filtered block, every step
+    host = torch.empty((nb, npw), dtype=torch.complex128, pin_memory=True).T
+    host.copy_(Y)
+    Ye = torch.empty_like(Y)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(st)
+    for _ in range(args.steps):
+        Ye.copy_(host, non_blocking=True)
+        g.cheb_filter(Ye, DEGREE, lo, hi, prec=prec)
+        host.copy_(Ye, non_blocking=True)
+    eb.record(st)
+    torch.cuda.synchronize()
+    e2e_s = ea.elapsed_time(eb) / 1e3
+    nbytes = npw * nb * 16
+
+    # roofline of the dominant kernel over the timed region
+    peaks = _peaks()
+    name, (ms_tot, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_s = ms_tot / cnt / 1e3
+    gemm_flops = 8.0 * npw * nq * nb  # one projector GEMM launch (P^H Z or P W) on all bands
+    if name in ("gemm_PhY", "gemm_PW", "tc_gemm_PhY", "tc_gemm_PW"):
+        tensor = name.startswith("tc_")
+        if tensor:
+            peak, bound, unit, pname = peaks.get("bf16_tflops_sustained", 1713.1), "tensor", "TFLOP/s", \
+                "bf16_tflops_sustained (measured)"
+        elif prec == F64:
+            peak, bound, unit, pname = 1.25, "alu", "TFLOP/s", "FP64 nominal 1.25 TFLOP/s (recipe)"
+        else:
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            bound, unit, pname = "alu", "TFLOP/s", "FP32 FFMA 152 SMs x 128 lanes x 2 x max clock"
+        achieved = gemm_flops / avg_s / 1e12
+    else:
+        # FFT passes: algorithmic bytes = read + write of the column buffer
+        esz = 8 if prec != F64 else 16
+        ncol = len({(int(a), int(b_)) for a, b_ in cell.miller[:, :2]})  # (x, y) columns of the sphere
+        bytes_launch = 2.0 * cell.grid[2] * ncol * nb * esz
+        peak, bound, unit, pname = peaks.get("hbm_gbs", 6762.3), "hbm", "GB/s", "hbm_gbs (measured)"
+        achieved = bytes_launch / avg_s / 1e9
+    roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "peak_source": pname,
+            "avg_launch_ms": avg_s * 1e3, "launches": cnt}
+
+    # eigenvalue state after the timed steps (residual norms in FP64)
+    k75 = (3 * nb) // 4
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "bf16x3+f32", "f32": "f32", "f64": "f64"}[args.prec], "data": "synthetic",
+        "config": {"workload": "%s: %d^3 grid, %d plane waves, %d bands, %d projectors, PAW=%s, degree 4, one "
+                               "filter + FP64 Rayleigh-Ritz per step" % (args.workload, cell.grid[0], npw, nb, nq,
+                                                                         cell.Q is not None),
+                   "filter_form": args.prec, "l2": "inputs (2 GB per block) larger than L2; no flush",
+                   "lambda_hi": "rigorous bound %.4f Ha" % hi},
+        "phases_ms": {"filter": statistics.mean(filt_ms), "rayleigh_ritz": statistics.mean(rr_ms)},
+        "fp64_form": fp64,
+        "e2e": {"value": world * nb * DEGREE * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:12]},
+        "ritz": {"max_residual_lowest_75pct": float(rs_last[:k75].max()), "lambda_min": float(ev_last[0])},
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and args.cpu_bands > 0:
+        r, dt = oracle_rate(cell, args.cpu_bands, DEGREE)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "%d of %d bands, degree %d, one filter call (%.1f s incl. the "
+                                          "oracle's P^H P setup); numpy FFTs single-threaded, BLAS on all cores"
+                                          % (args.cpu_bands, nb, DEGREE, dt)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

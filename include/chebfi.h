@@ -153,6 +153,16 @@ int chebfi_sync_status(chebfi_ctx* ctx);
 /* Number of kernels the library has launched on this context (monotonic counter). */
 int64_t chebfi_kernel_launches(const chebfi_ctx* ctx);
 
+/* Per-kernel timing for measurement: while enabled, every kernel launch of this context is
+ * bracketed by CUDA events recorded on its own stream, and the elapsed times are summed per
+ * kernel name.  enable = 1 clears previous totals; 0 stops recording (totals kept). */
+int chebfi_profile_enable(chebfi_ctx* ctx, int enable);
+/* Number of distinct kernel names with totals (synchronises); negative on error. */
+int chebfi_profile_count(chebfi_ctx* ctx);
+/* Entry i (0 <= i < count): kernel name (NUL-terminated, at most name_len bytes including
+ * the NUL), total milliseconds and number of launches.  Any output pointer may be NULL. */
+int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, double* ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,10 @@ SIGNATURES = {
                              ctypes.POINTER(Params), c_void_p]),
     "chebfi_sync_status": (c_int, [c_void_p]),
     "chebfi_kernel_launches": (c_int64, [c_void_p]),
+    "chebfi_profile_enable": (c_int, [c_void_p, c_int]),
+    "chebfi_profile_count": (c_int, [c_void_p]),
+    "chebfi_profile_entry": (c_int, [c_void_p, c_int, ctypes.c_char_p, c_int, P_double,
+                                     ctypes.POINTER(c_int64)]),
 }
 
 _lib = None

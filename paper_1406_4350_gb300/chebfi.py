@@ -205,6 +205,24 @@ class ChebFI:
     def sync_status(self):
         self._check(self.lib.chebfi_sync_status(self.h))
 
+    def profile(self, enable: bool = True):
+        """Start (clearing totals) or stop per-kernel CUDA-event timing in the library."""
+        self._check(self.lib.chebfi_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_totals(self):
+        """{kernel name: (total ms, launches)} recorded while profiling was on."""
+        n = self.lib.chebfi_profile_count(self.h)
+        if n < 0:
+            self._check(n)
+        out = {}
+        buf = ctypes.create_string_buffer(128)
+        for i in range(n):
+            ms = ctypes.c_double()
+            cnt = ctypes.c_int64()
+            self._check(self.lib.chebfi_profile_entry(self.h, i, buf, 128, ctypes.byref(ms), ctypes.byref(cnt)))
+            out[buf.value.decode()] = (ms.value, cnt.value)
+        return out
+
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.chebfi_kernel_launches(self.h))

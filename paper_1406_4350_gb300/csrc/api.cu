@@ -18,6 +18,63 @@
 namespace chebfi {
 
 int64_t* g_launch_counter = nullptr;
+Profiler* g_prof = nullptr;
+
+cudaEvent_t Profiler::get() {
+  if (pool.empty()) {
+    cudaEvent_t e;
+    CHEBFI_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  cudaEvent_t e = pool.back();
+  pool.pop_back();
+  return e;
+}
+
+void Profiler::flush() {
+  if (pending.empty()) return;
+  CHEBFI_CUDA(cudaEventSynchronize(pending.back().b));
+  for (const Rec& r : pending) {
+    float t = 0.f;
+    CHEBFI_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    size_t i = 0;
+    while (i < names.size() && names[i] != r.name) ++i;
+    if (i == names.size()) {
+      names.push_back(r.name);
+      ms.push_back(0.0);
+      count.push_back(0);
+    }
+    ms[i] += t;
+    count[i] += 1;
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  pending.clear();
+}
+
+Profiler::~Profiler() {
+  for (const Rec& r : pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+void prof_begin(const char* name, cudaStream_t st) {
+  if (!g_prof || !g_prof->on) return;
+  g_prof->cur = name;
+  g_prof->cur_a = g_prof->get();
+  CHEBFI_CUDA(cudaEventRecord(g_prof->cur_a, st));
+}
+
+void prof_end(cudaStream_t st) {
+  if (!g_prof || !g_prof->on || !g_prof->cur_a) return;
+  cudaEvent_t b = g_prof->get();
+  CHEBFI_CUDA(cudaEventRecord(b, st));
+  g_prof->pending.push_back({g_prof->cur, g_prof->cur_a, b});
+  g_prof->cur_a = nullptr;
+  if (g_prof->pending.size() >= 8192) g_prof->flush();
+}
 
 void after_launch(const char* name) {
   cudaError_t e = cudaGetLastError();
@@ -122,7 +179,9 @@ cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb, int degree,
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
   cplx<R>*cur = b.Ya, *prev = b.Yb, *pcur = b.pa, *pprev = b.pb;
-  if (nq > 0) gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st, Ops<R>::ws(ctx));
+  if (nq > 0)
+    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st, Ops<R>::ws(ctx),
+            "gemm_PhY");
   for (int k = 0; k < degree; ++k) {
     const double a = (k == 0 ? 1.0 : 2.0) / r;
     const double bp = k == 0 ? 0.0 : 1.0;
@@ -141,17 +200,22 @@ cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb, int degree,
     local_apply<R>(ctx, cur, npw, nb, b.T, ep, st);
     if (nq > 0) {
       // P^H H Y_k = P^H Z + G D p_k
-      gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, b.Z, npw, 0.0, b.pz, nq, st, Ops<R>::ws(ctx));
+      gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, b.Z, npw, 0.0, b.pz, nq, st, Ops<R>::ws(ctx),
+              "gemm_PhY");
       blockdiag_apply<R>(ctx, Ops<R>::D(ctx), pcur, nq, b.pw, nq, nb, st);
-      gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::G(ctx), nq, b.pw, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx));
+      gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::G(ctx), nq, b.pw, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx),
+              "gemm_small");
       if (ctx->paw) {
         // q = M P^H H Y_k;  W = D p_k - q;  P^H S^{-1} H Y_k = P^H H Y_k - G q
-        gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, b.pz, nq, 0.0, b.pq, nq, st, Ops<R>::ws(ctx));
+        gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, b.pz, nq, 0.0, b.pq, nq, st, Ops<R>::ws(ctx),
+                "gemm_small");
         axpby<R>(nq, nb, (R)1, b.pw, nq, (R)-1, b.pq, nq, b.pw, nq, st);
-        gemm<R>(false, false, nq, nb, nq, -1.0, Ops<R>::G(ctx), nq, b.pq, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx));
+        gemm<R>(false, false, nq, nb, nq, -1.0, Ops<R>::G(ctx), nq, b.pq, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx),
+                "gemm_small");
       }
       // Y_{k+1} = T + a P W
-      gemm<R>(false, false, npw, nb, nq, a, Ops<R>::P(ctx), npw, b.pw, nq, 1.0, prev, npw, st, Ops<R>::ws(ctx));
+      gemm<R>(false, false, npw, nb, nq, a, Ops<R>::P(ctx), npw, b.pw, nq, 1.0, prev, npw, st, Ops<R>::ws(ctx),
+              "gemm_PW");
       // p_{k+1} = a (P^H S^{-1} H Y_k - c p_k) - bp p_{k-1}
       cheb_combine<R>(nq, nb, (R)a, b.pz, nq, (R)c, pcur, nq, (R)bp, k == 0 ? nullptr : pprev, nq, pprev, nq, st);
     }
@@ -357,9 +421,8 @@ double rigorous_bound(chebfi_ctx* ctx) {
     DevBuf<double2>* ws = &ctx->w.splitk;
     // eigenvalues of L^H X L, G = P^H P = L L^H, for X = D and X = Q
     for (int which = 0; which < (ctx->paw ? 2 : 1); ++which) {
-      k_dense_from_blocks<<<nblk(nq * nq), 256>>>(nq, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
-                                                  which == 0 ? ctx->d_Dblk.p : ctx->d_Qblk.p, Dd.p);
-      after_launch("k_dense_from_blocks");
+      CHEBFI_LAUNCH("k_dense_from_blocks", 0, k_dense_from_blocks<<<nblk(nq * nq), 256>>>(nq, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
+                                                  which == 0 ? ctx->d_Dblk.p : ctx->d_Qblk.p, Dd.p));
       gemm<double>(false, false, nq, nq, nq, 1.0, Dd.p, nq, ctx->d_L.p, nq, 0.0, T.p, nq, st, ws);
       gemm<double>(true, false, nq, nq, nq, 1.0, ctx->d_L.p, nq, T.p, nq, 0.0, A.p, nq, st, ws);
       hermitize(nq, A.p, nq, st);
@@ -383,6 +446,7 @@ using namespace chebfi;
   try {                                                     \
     (ctx)->err.clear();                                     \
     g_launch_counter = &(ctx)->launches;                    \
+    g_prof = &(ctx)->prof;                                  \
     CHEBFI_CUDA(cudaSetDevice((ctx)->device));
 
 #define API_END(ctx)                                        \
@@ -641,13 +705,11 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
     Li.alloc(nn);
     Ri.alloc(nn);
     X.alloc(nn);
-    k_dense_from_blocks<<<nblk(nproj * nproj), 256, 0, st>>>(nproj, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
-                                                             ctx->d_Qblk.p, Qd.p);
-    after_launch("k_dense_from_blocks");
+    CHEBFI_LAUNCH("k_dense_from_blocks", st, k_dense_from_blocks<<<nblk(nproj * nproj), 256, 0, st>>>(nproj, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
+                                                             ctx->d_Qblk.p, Qd.p));
     gemm<double>(false, false, nproj, nproj, nproj, 1.0, Qd.p, nproj, ctx->d_L.p, nproj, 0.0, T.p, nproj, st, ws);
     gemm<double>(true, false, nproj, nproj, nproj, 1.0, ctx->d_L.p, nproj, T.p, nproj, 0.0, B.p, nproj, st, ws);
-    k_add_identity<<<nblk(nproj), 256, 0, st>>>(nproj, B.p, nproj);
-    after_launch("k_add_identity");
+    CHEBFI_LAUNCH("k_add_identity", st, k_add_identity<<<nblk(nproj), 256, 0, st>>>(nproj, B.p, nproj));
     hermitize(nproj, B.p, nproj, st);
     cholesky(nproj, B.p, nproj, ctx->d_status.p, st, ws);
     check_status(ctx, st, "set_projectors (S = I + P Q P^H is not positive definite)");
@@ -857,6 +919,43 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
   }
   scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
   CHEBFI_CUDA(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+int chebfi_profile_enable(chebfi_ctx* ctx, int enable) {
+  API_BEGIN(ctx)
+  ctx->prof.flush();
+  if (enable) {
+    ctx->prof.names.clear();
+    ctx->prof.ms.clear();
+    ctx->prof.count.clear();
+  }
+  ctx->prof.on = enable != 0;
+  API_END(ctx)
+}
+
+int chebfi_profile_count(chebfi_ctx* ctx) {
+  if (!ctx) return CHEBFI_ERR_ARG;
+  try {
+    CHEBFI_CUDA(cudaSetDevice(ctx->device));
+    ctx->prof.flush();
+  } catch (const Error& e) {
+    ctx->err = e.msg;
+    return e.code;
+  }
+  return (int)ctx->prof.names.size();
+}
+
+int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, double* ms, int64_t* launches) {
+  API_BEGIN(ctx)
+  ctx->prof.flush();
+  CHEBFI_REQUIRE(i >= 0 && i < (int)ctx->prof.names.size(), CHEBFI_ERR_ARG, "profile entry out of range");
+  if (name && name_len > 0) {
+    std::strncpy(name, ctx->prof.names[i].c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (ms) *ms = ctx->prof.ms[i];
+  if (launches) *launches = ctx->prof.count[i];
   API_END(ctx)
 }
 

@@ -199,9 +199,8 @@ void blockdiag_apply(const chebfi_ctx* ctx, const R* Dblk, const cplx<R>* p, int
                      int64_t nb, cudaStream_t st) {
   const int64_t n = ctx->nproj * nb;
   if (n == 0) return;
-  k_blockdiag<R><<<nblocks(n), 256, 0, st>>>(ctx->nproj, nb, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p, Dblk,
-                                             p, ldp, out, ldo);
-  after_launch("k_blockdiag");
+  CHEBFI_LAUNCH("k_blockdiag", st, k_blockdiag<R><<<nblocks(n), 256, 0, st>>>(ctx->nproj, nb, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p, Dblk,
+                                             p, ldp, out, ldo));
 }
 template void blockdiag_apply<double>(const chebfi_ctx*, const double*, const double2*, int64_t, double2*, int64_t,
                                       int64_t, cudaStream_t);
@@ -212,8 +211,7 @@ template <typename R>
 void cheb_combine(int64_t m, int64_t nb, R a, const cplx<R>* u, int64_t ldu, R c, const cplx<R>* x, int64_t ldx, R b,
                   const cplx<R>* y, int64_t ldy, cplx<R>* out, int64_t ldo, cudaStream_t st) {
   if (m * nb == 0) return;
-  k_cheb_combine<R><<<nblocks(m * nb), 256, 0, st>>>(m, nb, a, u, ldu, c, x, ldx, b, y, ldy, out, ldo);
-  after_launch("k_cheb_combine");
+  CHEBFI_LAUNCH("k_cheb_combine", st, k_cheb_combine<R><<<nblocks(m * nb), 256, 0, st>>>(m, nb, a, u, ldu, c, x, ldx, b, y, ldy, out, ldo));
 }
 template void cheb_combine<double>(int64_t, int64_t, double, const double2*, int64_t, double, const double2*, int64_t,
                                    double, const double2*, int64_t, double2*, int64_t, cudaStream_t);
@@ -224,8 +222,7 @@ template <typename R>
 void axpby(int64_t m, int64_t nb, R alpha, const cplx<R>* x, int64_t ldx, R beta, const cplx<R>* y, int64_t ldy,
            cplx<R>* out, int64_t ldo, cudaStream_t st) {
   if (m * nb == 0) return;
-  k_axpby<R><<<nblocks(m * nb), 256, 0, st>>>(m, nb, alpha, x, ldx, beta, y, ldy, out, ldo);
-  after_launch("k_axpby");
+  CHEBFI_LAUNCH("k_axpby", st, k_axpby<R><<<nblocks(m * nb), 256, 0, st>>>(m, nb, alpha, x, ldx, beta, y, ldy, out, ldo));
 }
 template void axpby<double>(int64_t, int64_t, double, const double2*, int64_t, double, const double2*, int64_t,
                             double2*, int64_t, cudaStream_t);
@@ -234,71 +231,58 @@ template void axpby<float>(int64_t, int64_t, float, const float2*, int64_t, floa
 
 void convert(int64_t m, int64_t nb, const double2* x, int64_t ldx, float2* y, int64_t ldy, cudaStream_t st) {
   if (m * nb == 0) return;
-  k_convert<double2, float2><<<nblocks(m * nb), 256, 0, st>>>(m, nb, x, ldx, y, ldy);
-  after_launch("k_convert");
+  CHEBFI_LAUNCH("k_convert", st, k_convert<double2, float2><<<nblocks(m * nb), 256, 0, st>>>(m, nb, x, ldx, y, ldy));
 }
 void convert(int64_t m, int64_t nb, const float2* x, int64_t ldx, double2* y, int64_t ldy, cudaStream_t st) {
   if (m * nb == 0) return;
-  k_convert<float2, double2><<<nblocks(m * nb), 256, 0, st>>>(m, nb, x, ldx, y, ldy);
-  after_launch("k_convert");
+  CHEBFI_LAUNCH("k_convert", st, k_convert<float2, double2><<<nblocks(m * nb), 256, 0, st>>>(m, nb, x, ldx, y, ldy));
 }
 void gather_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, double2* dst,
                  int64_t ldd, cudaStream_t st) {
   if (m * nb == 0) return;
-  k_gather<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd);
-  after_launch("k_gather");
+  CHEBFI_LAUNCH("k_gather", st, k_gather<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd));
 }
 void scatter_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, double2* dst,
                   int64_t ldd, cudaStream_t st) {
   if (m * nb == 0) return;
-  k_scatter<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd);
-  after_launch("k_scatter");
+  CHEBFI_LAUNCH("k_scatter", st, k_scatter<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd));
 }
 void column_dots(int64_t m, int64_t nb, const double2* x, int64_t ldx, const double2* y, int64_t ldy, double* out,
                  bool accumulate, cudaStream_t st) {
   if (nb == 0) return;
-  k_column_dots<<<(unsigned)nb, 256, 0, st>>>(m, x, ldx, y, ldy, out, accumulate ? 1 : 0);
-  after_launch("k_column_dots");
+  CHEBFI_LAUNCH("k_column_dots", st, k_column_dots<<<(unsigned)nb, 256, 0, st>>>(m, x, ldx, y, ldy, out, accumulate ? 1 : 0));
 }
 void residual_norms(int64_t m, int64_t nb, const double2* h, int64_t ldh, const double2* s, int64_t lds,
                     const double* w, double* out, cudaStream_t st) {
   if (nb == 0) return;
-  k_residual_norms<<<(unsigned)nb, 256, 0, st>>>(m, h, ldh, s, lds, w, out);
-  after_launch("k_residual_norms");
+  CHEBFI_LAUNCH("k_residual_norms", st, k_residual_norms<<<(unsigned)nb, 256, 0, st>>>(m, h, ldh, s, lds, w, out));
 }
 void divide(int64_t n, const double* num, const double* den, double* out, cudaStream_t st) {
   if (n == 0) return;
-  k_divide<<<nblocks(n), 256, 0, st>>>(n, num, den, out);
-  after_launch("k_divide");
+  CHEBFI_LAUNCH("k_divide", st, k_divide<<<nblocks(n), 256, 0, st>>>(n, num, den, out));
 }
 void set_identity(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
   if (n == 0) return;
-  k_identity<<<nblocks(n * n), 256, 0, st>>>(n, A, lda);
-  after_launch("k_identity");
+  CHEBFI_LAUNCH("k_identity", st, k_identity<<<nblocks(n * n), 256, 0, st>>>(n, A, lda));
 }
 void diag_of(int64_t n, const double2* A, int64_t lda, double* d, cudaStream_t st) {
   if (n == 0) return;
-  k_diag_of<<<nblocks(n), 256, 0, st>>>(n, A, lda, d);
-  after_launch("k_diag_of");
+  CHEBFI_LAUNCH("k_diag_of", st, k_diag_of<<<nblocks(n), 256, 0, st>>>(n, A, lda, d));
 }
 void scale_sym(int64_t n, double2* A, int64_t lda, const double* d, cudaStream_t st) {
   if (n == 0) return;
-  k_scale_sym<<<nblocks(n * n), 256, 0, st>>>(n, A, lda, d);
-  after_launch("k_scale_sym");
+  CHEBFI_LAUNCH("k_scale_sym", st, k_scale_sym<<<nblocks(n * n), 256, 0, st>>>(n, A, lda, d));
 }
 void scale_rows(int64_t n, int64_t m, double2* X, int64_t ldx, const double* d, cudaStream_t st) {
   if (n * m == 0) return;
-  k_scale_rows<<<nblocks(n * m), 256, 0, st>>>(n, m, X, ldx, d);
-  after_launch("k_scale_rows");
+  CHEBFI_LAUNCH("k_scale_rows", st, k_scale_rows<<<nblocks(n * m), 256, 0, st>>>(n, m, X, ldx, d));
 }
 void hermitize(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
   if (n == 0) return;
-  k_hermitize<<<nblocks(n * n), 256, 0, st>>>(n, A, lda);
-  after_launch("k_hermitize");
+  CHEBFI_LAUNCH("k_hermitize", st, k_hermitize<<<nblocks(n * n), 256, 0, st>>>(n, A, lda));
 }
 void reduce_max(int64_t n, const double* x, double* out, cudaStream_t st) {
-  k_reduce_max<<<1, 256, 0, st>>>(n, x, out);
-  after_launch("k_reduce_max");
+  CHEBFI_LAUNCH("k_reduce_max", st, k_reduce_max<<<1, 256, 0, st>>>(n, x, out));
 }
 
 }  // namespace chebfi

@@ -289,27 +289,23 @@ __global__ void k_eig_sort(int64_t n, const double2* __restrict__ A, int64_t lda
 void cholesky(int64_t n, double2* A, int64_t lda, int* status, cudaStream_t st, DevBuf<double2>* ws) {
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)std::min<int64_t>(NB, n - k0);
-    k_chol_diag<<<1, 256, 0, st>>>(A + k0 + k0 * lda, lda, nb, status);
-    after_launch("k_chol_diag");
+    CHEBFI_LAUNCH("k_chol_diag", st, k_chol_diag<<<1, 256, 0, st>>>(A + k0 + k0 * lda, lda, nb, status));
     const int64_t m2 = n - k0 - nb;
     if (m2 > 0) {
       double2* L21 = A + (k0 + nb) + k0 * lda;
-      k_trsm_right_lh<<<nblk(m2, 128), 128, 0, st>>>(A + k0 + k0 * lda, lda, L21, lda, m2, nb);
-      after_launch("k_trsm_right_lh");
+      CHEBFI_LAUNCH("k_trsm_right_lh", st, k_trsm_right_lh<<<nblk(m2, 128), 128, 0, st>>>(A + k0 + k0 * lda, lda, L21, lda, m2, nb));
       gemm<double>(false, true, m2, m2, nb, -1.0, L21, lda, L21, lda, 1.0, A + (k0 + nb) + (k0 + nb) * lda, lda, st,
                    ws);
     }
   }
-  k_zero_upper<<<nblk(n * n), 256, 0, st>>>(n, A, lda);
-  after_launch("k_zero_upper");
+  CHEBFI_LAUNCH("k_zero_upper", st, k_zero_upper<<<nblk(n * n), 256, 0, st>>>(n, A, lda));
 }
 
 void trsm_lower(int64_t n, int64_t m, const double2* L, int64_t ldl, double2* B, int64_t ldb, cudaStream_t st,
                 DevBuf<double2>* ws) {
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)std::min<int64_t>(NB, n - k0);
-    k_trsm_left_l<<<nblk(m, 128), 128, 0, st>>>(L + k0 + k0 * ldl, ldl, B + k0, ldb, m, nb);
-    after_launch("k_trsm_left_l");
+    CHEBFI_LAUNCH("k_trsm_left_l", st, k_trsm_left_l<<<nblk(m, 128), 128, 0, st>>>(L + k0 + k0 * ldl, ldl, B + k0, ldb, m, nb));
     const int64_t m2 = n - k0 - nb;
     if (m2 > 0)
       gemm<double>(false, false, m2, m, nb, -1.0, L + (k0 + nb) + k0 * ldl, ldl, B + k0, ldb, 1.0, B + k0 + nb, ldb, st,
@@ -340,8 +336,7 @@ void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int
   double prev_off = INFINITY;
   bool done = false;
   for (int sweep = 0; sweep <= max_sweeps && !done; ++sweep) {
-    k_offnorm<<<1, 256, 0, st>>>(n0, A, lda, nrm);
-    after_launch("k_offnorm");
+    CHEBFI_LAUNCH("k_offnorm", st, k_offnorm<<<1, 256, 0, st>>>(n0, A, lda, nrm));
     double h[2];
     CHEBFI_CUDA(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
     CHEBFI_CUDA(cudaStreamSynchronize(st));
@@ -354,12 +349,9 @@ void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int
     if (sweep == max_sweeps) break;
     prev_off = off;
     for (int64_t round = 0; round < n - 1; ++round) {
-      k_jac_params<<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs);
-      after_launch("k_jac_params");
-      k_jac_rows<<<nblk((n / 2) * n0), 256, 0, st>>>(n / 2, n0, A, lda, rot, pairs);
-      after_launch("k_jac_rows");
-      k_jac_cols<<<nblk((n / 2) * 2 * n0), 256, 0, st>>>(n / 2, n0, A, lda, Vtmp, n0, rot, pairs);
-      after_launch("k_jac_cols");
+      CHEBFI_LAUNCH("k_jac_params", st, k_jac_params<<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs));
+      CHEBFI_LAUNCH("k_jac_rows", st, k_jac_rows<<<nblk((n / 2) * n0), 256, 0, st>>>(n / 2, n0, A, lda, rot, pairs));
+      CHEBFI_LAUNCH("k_jac_cols", st, k_jac_cols<<<nblk((n / 2) * 2 * n0), 256, 0, st>>>(n / 2, n0, A, lda, Vtmp, n0, rot, pairs));
     }
   }
   if (!done) {
@@ -368,8 +360,7 @@ void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int
     CHEBFI_CUDA(cudaMemcpyAsync(status, &code, sizeof(int), cudaMemcpyHostToDevice, st));
     CHEBFI_CUDA(cudaStreamSynchronize(st));
   }
-  k_eig_sort<<<(unsigned)n0, 128, 0, st>>>(n0, A, lda, Vtmp, n0, w, V, ldv);
-  after_launch("k_eig_sort");
+  CHEBFI_LAUNCH("k_eig_sort", st, k_eig_sort<<<(unsigned)n0, 128, 0, st>>>(n0, A, lda, Vtmp, n0, w, V, ldv));
 }
 
 }  // namespace chebfi

@@ -225,18 +225,15 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
     const int nbc = (int)std::min<int64_t>(65535, nb - b0);
     dim3 gz((s.ncol + kCB - 1) / kCB, nbc);
-    k_zinv<R><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, sa, pz);
-    after_launch("k_zinv");
-    k_plane<R><<<dim3(s.n3, nbc), kThreads, pbytes, st>>>(T, V, pa, px, py);
-    after_launch("k_plane");
+    CHEBFI_LAUNCH("k_zinv", st, k_zinv<R><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, sa, pz));
+    CHEBFI_LAUNCH("k_plane", st, k_plane<R><<<dim3(s.n3, nbc), kThreads, pbytes, st>>>(T, V, pa, px, py));
     LocalEpi<R> e = ep;
     e.Y = ep.Y + b0 * ep.ldy;
     if (e.Z) e.Z = ep.Z + b0 * ep.ldz;
     if (e.T) e.T = ep.T + b0 * ep.ldt;
     if (e.Yprev) e.Yprev = ep.Yprev + b0 * ep.ldt;
     e.inv_n3 = (R)(1.0 / ((double)s.n1 * s.n2 * s.n3));
-    k_zfwd<R><<<gz, kThreads, zbytes, st>>>(T, sa, pz, K, e);
-    after_launch("k_zfwd");
+    CHEBFI_LAUNCH("k_zfwd", st, k_zfwd<R><<<gz, kThreads, zbytes, st>>>(T, sa, pz, K, e));
   }
 }
 

@@ -128,7 +128,8 @@ __global__ void k_splitk_reduce(int64_t M, int64_t N, int splits, const cplx<R>*
 
 template <typename R, bool CA, bool CB>
 void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int64_t lda, const cplx<R>* B,
-            int64_t ldb, double beta, cplx<R>* Cm, int64_t ldc, cudaStream_t st, DevBuf<cplx<R>>* ws) {
+            int64_t ldb, double beta, cplx<R>* Cm, int64_t ldc, cudaStream_t st, DevBuf<cplx<R>>* ws,
+            const char* tag) {
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   int splits = 1;
   const int64_t tiles = tm * tn;
@@ -147,12 +148,10 @@ void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int
     wsp = ws->p;
   }
   dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)splits);
-  k_gemm<R, CA, CB><<<grid, 256, 0, st>>>(M, N, K, (R)alpha, A, lda, B, ldb, (R)beta, Cm, ldc, kchunk, wsp);
-  after_launch("k_gemm");
+  CHEBFI_LAUNCH(tag, st, k_gemm<R, CA, CB><<<grid, 256, 0, st>>>(M, N, K, (R)alpha, A, lda, B, ldb, (R)beta, Cm, ldc, kchunk, wsp));
   if (splits > 1) {
     const int64_t tot = M * N;
-    k_splitk_reduce<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, wsp, (R)beta, Cm, ldc);
-    after_launch("k_splitk_reduce");
+    CHEBFI_LAUNCH("k_splitk_reduce", st, k_splitk_reduce<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, wsp, (R)beta, Cm, ldc));
   }
 }
 
@@ -161,17 +160,17 @@ void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int
 template <typename R>
 void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int64_t lda,
           const cplx<R>* B, int64_t ldb, double beta, cplx<R>* C, int64_t ldc, cudaStream_t st,
-          DevBuf<cplx<R>>* ws) {
+          DevBuf<cplx<R>>* ws, const char* tag) {
   if (M <= 0 || N <= 0) return;
-  if (conjA && conjB) launch<R, true, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws);
-  else if (conjA) launch<R, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws);
-  else if (conjB) launch<R, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws);
-  else launch<R, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws);
+  if (conjA && conjB) launch<R, true, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
+  else if (conjA) launch<R, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
+  else if (conjB) launch<R, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
+  else launch<R, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
 }
 
 template void gemm<double>(bool, bool, int64_t, int64_t, int64_t, double, const double2*, int64_t, const double2*,
-                           int64_t, double, double2*, int64_t, cudaStream_t, DevBuf<double2>*);
+                           int64_t, double, double2*, int64_t, cudaStream_t, DevBuf<double2>*, const char*);
 template void gemm<float>(bool, bool, int64_t, int64_t, int64_t, double, const float2*, int64_t, const float2*,
-                          int64_t, double, float2*, int64_t, cudaStream_t, DevBuf<float2>*);
+                          int64_t, double, float2*, int64_t, cudaStream_t, DevBuf<float2>*, const char*);
 
 }  // namespace chebfi

@@ -57,6 +57,21 @@ struct Error {
 void after_launch(const char* name);
 extern int64_t* g_launch_counter;
 
+// Optional per-kernel timing: CUDA events recorded on the launching stream around every
+// launch while a context has profiling switched on (chebfi_profile_enable).
+struct Profiler;
+extern Profiler* g_prof;
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+
+#define CHEBFI_LAUNCH(name, st, ...)  \
+  do {                                \
+    ::chebfi::prof_begin(name, st);   \
+    __VA_ARGS__;                      \
+    ::chebfi::after_launch(name);     \
+    ::chebfi::prof_end(st);           \
+  } while (0)
+
 // ----------------------------------------------------------------------------- device buffers
 template <typename T> struct DevBuf {
   T* p = nullptr;
@@ -137,8 +152,29 @@ struct Work {
 
 }  // namespace chebfi
 
+namespace chebfi {
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  const char* cur = nullptr;
+  cudaEvent_t cur_a = nullptr;
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<int64_t> count;
+  cudaEvent_t get();
+  void flush();  // synchronises, folds pending records into the totals
+  ~Profiler();
+};
+}  // namespace chebfi
+
 struct chebfi_ctx {
   int device = 0;
+  chebfi::Profiler prof;
   std::string err;
   int64_t launches = 0;
 

@@ -28,10 +28,11 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
 // ---------------------------------------------------------------- complex GEMM (gemm.cu)
 // C = alpha op(A) op(B) + beta C, op = identity or conjugate transpose; real alpha, beta.
 // M x N result, inner dimension K.  ws: optional split-K workspace (nullptr = no split).
+// tag: the name the launch is timed under when profiling is on.
 template <typename R>
 void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A,
           int64_t lda, const cplx<R>* B, int64_t ldb, double beta, cplx<R>* C, int64_t ldc, cudaStream_t st,
-          DevBuf<cplx<R>>* ws = nullptr);
+          DevBuf<cplx<R>>* ws = nullptr, const char* tag = "k_gemm");
 
 // ---------------------------------------------------------------- small kernels (blas.cu)
 // out = Dbd p: block-diagonal real D (packed row-major per-atom blocks) times complex p.
