@@ -225,6 +225,84 @@ cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb, int degree,
   return cur;
 }
 
+// bf16 (hi, lo) embeddings of P^H, P, G and M for the tensor-core GEMMs (first use only).
+void ensure_tc(chebfi_ctx* ctx, cudaStream_t st) {
+  if (ctx->tc_ready || ctx->nproj == 0) return;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  embed_ph(npw, nq, ctx->d_P.p, npw, ctx->tcA1, st);
+  embed_n(npw, nq, ctx->d_P.p, npw, ctx->tcA2, st);
+  embed_n(nq, nq, ctx->d_G.p, nq, ctx->tcAG, st);
+  if (ctx->paw) embed_n(nq, nq, ctx->d_M.p, nq, ctx->tcAM, st);
+  ctx->tc_ready = true;
+}
+
+// Mixed form of the filter: FP32 iterates and FFT, projector GEMMs on the tensor cores
+// with split bf16 operands.  Same steps as filter_sorted; Y_0 and the result are the FP32
+// buffers b.Ya / returned pointer.
+float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb, int degree, double lo, double hi,
+                     cudaStream_t st) {
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
+  Work& w = ctx->w;
+  int* status = ctx->d_status.p;
+  float2 *cur = b.Ya, *prev = b.Yb, *pcur = b.pa, *pprev = b.pb;
+  const int64_t ldzb = (2 * npw + 7) / 8 * 8;
+  if (nq > 0) {
+    ensure_tc(ctx, st);
+    w.Zb.ld = ldzb;
+    w.Zb.alloc((size_t)ldzb * nb);
+    split_block(npw, nb, cur, npw, w.Zb, st);
+    tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)pcur, 2 * nq, status, st,
+            "tc_gemm_PhY");
+  }
+  for (int k = 0; k < degree; ++k) {
+    const double a = (k == 0 ? 1.0 : 2.0) / r;
+    const double bp = k == 0 ? 0.0 : 1.0;
+    LocalEpi<float> ep;
+    ep.Y = cur;
+    ep.ldy = npw;
+    if (nq > 0) {
+      ep.Zhi = w.Zb.hi.p;
+      ep.Zlo = w.Zb.lo.p;
+      ep.ldzb = ldzb;
+    }
+    ep.T = prev;
+    ep.Yprev = k == 0 ? nullptr : prev;
+    ep.ldt = npw;
+    ep.a = (float)a;
+    ep.c = (float)c;
+    ep.bprev = (float)bp;
+    local_apply<float>(ctx, cur, npw, nb, b.T, ep, st);
+    if (nq > 0) {
+      // P^H H Y_k = P^H Z + G D p_k
+      tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)b.pz, 2 * nq, status,
+              st, "tc_gemm_PhY");
+      blockdiag_apply<float>(ctx, ctx->d_Dblkf.p, pcur, nq, b.pw, nq, nb, st);
+      split_block(nq, nb, b.pw, nq, w.Sb, st);
+      tc_gemm(ctx->tcAG.view(), w.Sb.view(), 2 * nq, nb, 2 * nq, 1.f, 1.f, (float*)b.pz, 2 * nq, (float*)b.pz, 2 * nq,
+              status, st, "tc_gemm_small");
+      if (ctx->paw) {
+        split_block(nq, nb, b.pz, nq, w.Sb, st);
+        tc_gemm(ctx->tcAM.view(), w.Sb.view(), 2 * nq, nb, 2 * nq, 1.f, 0.f, nullptr, 0, (float*)b.pq, 2 * nq, status,
+                st, "tc_gemm_small");
+        axpby<float>(nq, nb, 1.f, b.pw, nq, -1.f, b.pq, nq, b.pw, nq, st);
+        split_block(nq, nb, b.pq, nq, w.Sb, st);
+        tc_gemm(ctx->tcAG.view(), w.Sb.view(), 2 * nq, nb, 2 * nq, -1.f, 1.f, (float*)b.pz, 2 * nq, (float*)b.pz,
+                2 * nq, status, st, "tc_gemm_small");
+      }
+      // Y_{k+1} = T + a P W
+      split_block(nq, nb, b.pw, nq, w.Sb, st);
+      tc_gemm(ctx->tcA2.view(), w.Sb.view(), 2 * npw, nb, 2 * nq, (float)a, 1.f, (float*)prev, 2 * npw, (float*)prev,
+              2 * npw, status, st, "tc_gemm_PW");
+      cheb_combine<float>(nq, nb, (float)a, b.pz, nq, (float)c, pcur, nq, (float)bp, k == 0 ? nullptr : pprev, nq,
+                          pprev, nq, st);
+    }
+    std::swap(cur, prev);
+    std::swap(pcur, pprev);
+  }
+  return cur;
+}
+
 void ensure_filter_ws(chebfi_ctx* ctx, int64_t nb, int prec) {
   const size_t ny = (size_t)ctx->npw * nb, np = (size_t)std::max<int64_t>(ctx->nproj, 1) * nb;
   const size_t nt = local_workspace_elems(ctx, nb);
@@ -264,7 +342,8 @@ void filter_on_Ya(chebfi_ctx* ctx, int64_t nb, int degree, double lo, double hi,
   } else {
     convert(npw, nb, w.Ya.p, npw, w.fYa.p, npw, st);
     FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
-    float2* out = filter_sorted<float>(ctx, b, nb, degree, lo, hi, st);
+    float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lo, hi, st)
+                                       : filter_sorted<float>(ctx, b, nb, degree, lo, hi, st);
     convert(npw, nb, out, npw, w.Ya.p, npw, st);
   }
 }
@@ -770,7 +849,28 @@ int chebfi_apply_H(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t
     w.fpa.alloc(np);
     w.fpb.alloc(np);
     convert(npw, nb, w.Ya.p, npw, w.fYa.p, npw, st);
-    apply_H_sorted<float>(ctx, w.fYa.p, w.fZ.p, w.fpa.p, w.fpb.p, w.fT1.p, nb, st);
+    if (prec == CHEBFI_MIXED && ctx->nproj > 0) {
+      // local part in FP32, projector products on the tensor cores
+      const int64_t nq = ctx->nproj;
+      ensure_tc(ctx, st);
+      LocalEpi<float> ep;
+      ep.Y = w.fYa.p;
+      ep.ldy = npw;
+      ep.Z = w.fZ.p;
+      ep.ldz = npw;
+      local_apply<float>(ctx, w.fYa.p, npw, nb, w.fT1.p, ep, st);
+      w.Zb.ld = (2 * npw + 7) / 8 * 8;
+      w.Zb.alloc((size_t)w.Zb.ld * nb);
+      split_block(npw, nb, w.fYa.p, npw, w.Zb, st);
+      tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)w.fpa.p, 2 * nq,
+              ctx->d_status.p, st, "tc_gemm_PhY");
+      blockdiag_apply<float>(ctx, ctx->d_Dblkf.p, w.fpa.p, nq, w.fpb.p, nq, nb, st);
+      split_block(nq, nb, w.fpb.p, nq, w.Sb, st);
+      tc_gemm(ctx->tcA2.view(), w.Sb.view(), 2 * npw, nb, 2 * nq, 1.f, 1.f, (float*)w.fZ.p, 2 * npw, (float*)w.fZ.p,
+              2 * npw, ctx->d_status.p, st, "tc_gemm_PW");
+    } else {
+      apply_H_sorted<float>(ctx, w.fYa.p, w.fZ.p, w.fpa.p, w.fpb.p, w.fT1.p, nb, st);
+    }
     convert(npw, nb, w.fZ.p, npw, w.HY.p, npw, st);
   }
   scatter_from(ctx, w.HY.p, HY, nb, ld, st);

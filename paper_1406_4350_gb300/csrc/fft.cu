@@ -162,6 +162,16 @@ __global__ void __launch_bounds__(kThreads) k_zfwd(const cplx<R>* __restrict__ T
     zj.x = v.x * ep.inv_n3 + k * yj.x;
     zj.y = v.y * ep.inv_n3 + k * yj.y;
     if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
+    if (ep.Zhi) {
+      const float zr = (float)zj.x, zi = (float)zj.y;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi);
+      __nv_bfloat16* ph = ep.Zhi + b * ep.ldzb + 2 * j;
+      __nv_bfloat16* pl = ep.Zlo + b * ep.ldzb + 2 * j;
+      ph[0] = hr;
+      ph[1] = hi_;
+      pl[0] = __float2bfloat16_rn(zr - __bfloat162float(hr));
+      pl[1] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
+    }
     if (ep.T) {
       // three-term update without its nonlocal part: T = a (Z - c Y) - bprev Yprev
       cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
@@ -230,6 +240,10 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
     LocalEpi<R> e = ep;
     e.Y = ep.Y + b0 * ep.ldy;
     if (e.Z) e.Z = ep.Z + b0 * ep.ldz;
+    if (e.Zhi) {
+      e.Zhi = ep.Zhi + b0 * ep.ldzb;
+      e.Zlo = ep.Zlo + b0 * ep.ldzb;
+    }
     if (e.T) e.T = ep.T + b0 * ep.ldt;
     if (e.Yprev) e.Yprev = ep.Yprev + b0 * ep.ldt;
     e.inv_n3 = (R)(1.0 / ((double)s.n1 * s.n2 * s.n3));

@@ -1,0 +1,415 @@
+// Tensor-core GEMM of the mixed-precision filter on sm_103a (tcgen05 + TMA + TMEM).
+//
+// Computes D = alpha * A B (+ beta * C) for real matrices with FP32 accumulation, where
+// A (M x K) and B (K x N) are both K-major (K contiguous) and given as bf16 pairs
+// (hi, lo) with x ~= hi + lo; the product uses the three terms
+//     A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (the lo * lo term is below the FP32 accumulation error), which carries about 16
+// significant bits per operand instead of bf16's 8.  D and C are FP32 column-major.
+//
+// Complex projector products of Section 4.1 map onto it through the real embedding of
+// interleaved complex data: with z stored as (re, im) pairs, P^H z and P w become real
+// GEMMs whose A matrices (built once from P at setup) hold the 2 x 2 blocks
+// [[Re, Im], [-Im, Re]] and [[Re, -Im], [Im, Re]].
+//
+// One CTA computes one 128 x 256 tile: warp 0 issues the TMA loads (128-byte swizzle,
+// two-stage mbarrier ring), warp 1 allocates 256 TMEM columns and issues the MMAs
+// (tcgen05.mma cta_group::1 kind::f16, M = 128, N = 256, K = 16), warps 2-5 drain the
+// accumulator with tcgen05.ld and write FP32 with the alpha/beta epilogue.  Every wait
+// on an mbarrier gives up after a fixed time, records an error code and lets the CTA
+// finish (the TMEM is released on every path).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace chebfi {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;                     // 16 KB
+constexpr int B_BYTES = BN * BK * 2;                     // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of both: 96 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;    // 2 s per wait
+
+struct Args {
+  int M, N, K;
+  float alpha, beta;
+  float* D;
+  int64_t ldd;
+  const float* C;
+  int64_t ldc;
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the given phase parity: false after WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (now_ns() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle: start address,
+// leading byte offset 16 (unused for this layout), stride byte offset 1024 (eight 128-byte
+// rows), descriptor version 1 (bit 46), swizzle mode 2 = 128B (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D format F32 (bits 4-5 = 1), A and B format BF16
+// (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void flag(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, Args args) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int num_k = (args.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kt = 0; kt < num_k; ++kt) {
+        const int s = kt % STAGES;
+        const uint32_t par = (kt / STAGES) & 1;
+        if (kt >= STAGES && !mbar_wait(&empty[s], par ^ 1)) {
+          flag(args.status, CHEBFI_ERR_CUDA);
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        const int x = kt * BK;
+        tma_load_2d(st, &tmAh, x, m0, &full[s]);
+        tma_load_2d(st + A_BYTES, &tmAl, x, m0, &full[s]);
+        tma_load_2d(st + 2 * A_BYTES, &tmBh, x, n0, &full[s]);
+        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmBl, x, n0, &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+      bool ok = true;
+      for (int kt = 0; kt < num_k; ++kt) {
+        const int s = kt % STAGES;
+        const uint32_t par = (kt / STAGES) & 1;
+        if (!mbar_wait(&full[s], par)) {
+          flag(args.status, CHEBFI_ERR_CUDA);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t off = kk * 32;  // 16 bf16 along K
+          const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + A_BYTES + off);
+          const uint64_t bh = sw128_desc(base + 2 * A_BYTES + off), bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + off);
+          mma_bf16(tmem, ah, bh, idesc, (kt | kk) != 0);
+          mma_bf16(tmem, ah, bl, idesc, 1);
+          mma_bf16(tmem, al, bh, idesc, 1);
+        }
+        mma_commit(&empty[s]);
+      }
+      (void)ok;
+      mma_commit(accum);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. tile rows
+    const int lane_base = 32 * (warp % 4);
+    const int m = m0 + lane_base + lane;
+    if (mbar_wait(accum, 0)) {
+      tc_fence_after();
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c, v);
+        if (m < args.M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c + j;
+            if (n < args.N) {
+              float o = args.alpha * v[j];
+              if (args.beta != 0.f) o = fmaf(args.beta, args.C[(int64_t)m + (int64_t)n * args.ldc], o);
+              args.D[(int64_t)m + (int64_t)n * args.ldd] = o;
+            }
+          }
+        }
+      }
+    } else {
+      flag(args.status, CHEBFI_ERR_CUDA);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  CHEBFI_REQUIRE(fn != nullptr, CHEBFI_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  return fn;
+}
+
+// 2-D bf16 map over a K-major matrix with `rows` rows of `k` elements (row stride ld
+// elements, a multiple of 8), boxes of BK x box_rows, 128-byte swizzle, zero fill.
+CUtensorMap make_map(const __nv_bfloat16* base, int64_t k, int64_t rows, int64_t ld, int box_rows) {
+  CHEBFI_REQUIRE(ld % 8 == 0 && (reinterpret_cast<uintptr_t>(base) % 16) == 0, CHEBFI_ERR_ARG,
+                 "tensor-core operand must be 16-byte aligned with a row stride multiple of 8");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CHEBFI_REQUIRE(r == CUDA_SUCCESS, CHEBFI_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+}  // namespace tc
+
+void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64_t K, float alpha, float beta,
+             const float* C, int64_t ldc, float* D, int64_t ldd, int* status, cudaStream_t st, const char* tag) {
+  if (M <= 0 || N <= 0) return;
+  CHEBFI_REQUIRE(K > 0, CHEBFI_ERR_ARG, "tensor-core GEMM with K = 0");
+  CHEBFI_REQUIRE(M < (1ll << 31) && N < (1ll << 31) && K < (1ll << 31), CHEBFI_ERR_ARG, "GEMM too large");
+  CHEBFI_REQUIRE(A.ld >= K && B.ld >= K, CHEBFI_ERR_ARG, "operand leading dimension below K");
+  const CUtensorMap ah = tc::make_map(A.hi, K, M, A.ld, tc::BM), al = tc::make_map(A.lo, K, M, A.ld, tc::BM);
+  const CUtensorMap bh = tc::make_map(B.hi, K, N, B.ld, tc::BN), bl = tc::make_map(B.lo, K, N, B.ld, tc::BN);
+  tc::Args a;
+  a.M = (int)M;
+  a.N = (int)N;
+  a.K = (int)K;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.D = D;
+  a.ldd = ldd;
+  a.C = C;
+  a.ldc = ldc;
+  a.status = status;
+  CHEBFI_CUDA(cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  dim3 grid((unsigned)((N + tc::BN - 1) / tc::BN), (unsigned)((M + tc::BM - 1) / tc::BM));
+  CHEBFI_REQUIRE(grid.y <= 65535, CHEBFI_ERR_ARG, "GEMM M too large");
+  CHEBFI_LAUNCH(tag, st, tc::k_tc_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(ah, al, bh, bl, a));
+}
+
+}  // namespace chebfi
+
+// ---------------------------------------------------------------- operand preparation
+namespace chebfi {
+namespace {
+
+__device__ __forceinline__ void split2(double v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(v);
+  lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+}
+__device__ __forceinline__ void split2f(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Real embedding of y = P^H x (P: npw x nq complex, column-major, ld = npw):
+// row 2i holds (Re P_gi, Im P_gi) at columns (2g, 2g+1); row 2i+1 holds (-Im P_gi, Re P_gi).
+__global__ void k_embed_ph(int64_t npw, int64_t nq, const double2* __restrict__ P, int64_t ldp,
+                           __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t ld) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npw * nq) return;
+  const int64_t g = idx % npw, i = idx / npw;
+  const double2 p = P[g + i * ldp];
+  const int64_t r0 = (2 * i) * ld + 2 * g, r1 = (2 * i + 1) * ld + 2 * g;
+  split2(p.x, hi[r0], lo[r0]);
+  split2(p.y, hi[r0 + 1], lo[r0 + 1]);
+  split2(-p.y, hi[r1], lo[r1]);
+  split2(p.x, hi[r1 + 1], lo[r1 + 1]);
+}
+
+// Real embedding of y = A x for a complex A (m x k, column-major, ld = lda):
+// row 2g holds (Re A_gj, -Im A_gj) at columns (2j, 2j+1); row 2g+1 holds (Im A_gj, Re A_gj).
+__global__ void k_embed_n(int64_t m, int64_t k, const double2* __restrict__ A, int64_t lda,
+                          __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t ld) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * k) return;
+  const int64_t g = idx % m, j = idx / m;
+  const double2 a = A[g + j * lda];
+  const int64_t r0 = (2 * g) * ld + 2 * j, r1 = (2 * g + 1) * ld + 2 * j;
+  split2(a.x, hi[r0], lo[r0]);
+  split2(-a.y, hi[r0 + 1], lo[r0 + 1]);
+  split2(a.y, hi[r1], lo[r1]);
+  split2(a.x, hi[r1 + 1], lo[r1 + 1]);
+}
+
+// Complex FP32 block (m x nb, column-major) -> bf16 (hi, lo) K-major operand: column b holds
+// the 2m interleaved reals.
+__global__ void k_split_block(int64_t m, int64_t nb, const float2* __restrict__ x, int64_t ldx,
+                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t ld) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, b = idx / m;
+  const float2 v = x[i + b * ldx];
+  const int64_t o = b * ld + 2 * i;
+  split2f(v.x, hi[o], lo[o]);
+  split2f(v.y, hi[o + 1], lo[o + 1]);
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
+
+}  // namespace
+
+void embed_ph(int64_t npw, int64_t nq, const double2* P, int64_t ldp, SplitBF16Buf& out, cudaStream_t st) {
+  out.ld = (2 * npw + 7) / 8 * 8;
+  out.alloc((size_t)out.ld * 2 * nq);
+  CHEBFI_CUDA(cudaMemsetAsync(out.hi.p, 0, out.hi.n * sizeof(__nv_bfloat16), st));
+  CHEBFI_CUDA(cudaMemsetAsync(out.lo.p, 0, out.lo.n * sizeof(__nv_bfloat16), st));
+  CHEBFI_LAUNCH("k_embed_ph", st, k_embed_ph<<<nblk(npw * nq), 256, 0, st>>>(npw, nq, P, ldp, out.hi.p, out.lo.p, out.ld));
+}
+
+void embed_n(int64_t m, int64_t k, const double2* A, int64_t lda, SplitBF16Buf& out, cudaStream_t st) {
+  out.ld = (2 * k + 7) / 8 * 8;
+  out.alloc((size_t)out.ld * 2 * m);
+  CHEBFI_CUDA(cudaMemsetAsync(out.hi.p, 0, out.hi.n * sizeof(__nv_bfloat16), st));
+  CHEBFI_CUDA(cudaMemsetAsync(out.lo.p, 0, out.lo.n * sizeof(__nv_bfloat16), st));
+  CHEBFI_LAUNCH("k_embed_n", st, k_embed_n<<<nblk(m * k), 256, 0, st>>>(m, k, A, lda, out.hi.p, out.lo.p, out.ld));
+}
+
+void split_block(int64_t m, int64_t nb, const float2* x, int64_t ldx, SplitBF16Buf& out, cudaStream_t st) {
+  out.ld = (2 * m + 7) / 8 * 8;
+  out.alloc((size_t)out.ld * nb);
+  CHEBFI_LAUNCH("k_split_block", st, k_split_block<<<nblk(m * nb), 256, 0, st>>>(m, nb, x, ldx, out.hi.p, out.lo.p, out.ld));
+}
+
+}  // namespace chebfi

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libchebfi.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -103,6 +104,23 @@ template <typename T> struct DevBuf {
   }
 };
 
+// bf16 pair (hi, lo) of a K-major real matrix: row r (of the M or N dimension) starts at
+// r * ld elements; x ~= hi + lo carries about 16 significant bits.
+struct SplitBF16 {
+  const __nv_bfloat16* hi = nullptr;
+  const __nv_bfloat16* lo = nullptr;
+  int64_t ld = 0;
+};
+struct SplitBF16Buf {
+  DevBuf<__nv_bfloat16> hi, lo;
+  int64_t ld = 0;
+  void alloc(size_t count) {
+    hi.alloc(count);
+    lo.alloc(count);
+  }
+  SplitBF16 view() const { return SplitBF16{hi.p, lo.p, ld}; }
+};
+
 // ----------------------------------------------------------------------------- FFT plan
 constexpr int kMaxStages = 12;
 constexpr int kMaxN = 256;
@@ -148,6 +166,7 @@ struct Work {
   DevBuf<double> dvec1, dvec2, dvec3;
   DevBuf<double2> splitk;
   DevBuf<float2> fsplitk;
+  SplitBF16Buf Zb, Sb;  // bf16 pairs of Z (or Y) and of the projection-space operands
 };
 
 }  // namespace chebfi
@@ -207,6 +226,9 @@ struct chebfi_ctx {
   chebfi::DevBuf<float2> d_Pf, d_Gf, d_Mf;
   chebfi::DevBuf<float> d_Dblkf;
   chebfi::DevBuf<int> d_status;               // device error flag
+  // mixed form: bf16 (hi, lo) real embeddings of P^H, P, G and M, built on first use
+  bool tc_ready = false;
+  chebfi::SplitBF16Buf tcA1, tcA2, tcAG, tcAM;
   chebfi::Work w;
   double bound_rigorous = -1.0;
 };

@@ -2,6 +2,8 @@
 // blas.cu, dense.cu).  All matrices are column-major; complex values interleaved.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace chebfi {
@@ -10,11 +12,15 @@ namespace chebfi {
 // Epilogue of the (K + V_loc) pass for sphere point j of band b:
 //   Z = K_j Y_j + (V_loc Y)_j                      -> Z[b*ldz + j]     (if Z)
 //   T = a (Z - c Y_j) - bprev Yprev[b*ldt + j]     -> T[b*ldt + j]     (if T; may alias Yprev)
+//   (hi, lo) bf16 pair of Z, 2 reals per point           -> Zhi/Zlo[b*ldzb + 2j + {0,1}] (if Zhi)
 template <typename R> struct LocalEpi {
   const cplx<R>* Y = nullptr;
   int64_t ldy = 0;
   cplx<R>* Z = nullptr;
   int64_t ldz = 0;
+  __nv_bfloat16* Zhi = nullptr;
+  __nv_bfloat16* Zlo = nullptr;
+  int64_t ldzb = 0;
   cplx<R>* T = nullptr;
   const cplx<R>* Yprev = nullptr;
   int64_t ldt = 0;
@@ -33,6 +39,18 @@ template <typename R>
 void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A,
           int64_t lda, const cplx<R>* B, int64_t ldb, double beta, cplx<R>* C, int64_t ldc, cudaStream_t st,
           DevBuf<cplx<R>>* ws = nullptr, const char* tag = "k_gemm");
+
+// ---------------------------------------------------------------- tensor cores (gemm_tc.cu)
+// D (M x N, FP32 column-major) = alpha A B + beta C with A (M x K) and B (K x N) K-major
+// bf16 pairs; tcgen05 tensor cores with FP32 accumulation.  C may equal D.
+void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64_t K, float alpha, float beta,
+             const float* C, int64_t ldc, float* D, int64_t ldd, int* status, cudaStream_t st, const char* tag);
+// Real embeddings (bf16 pairs) of complex operators applied to interleaved complex data:
+// embed_ph: the (2 nq) x (2 npw) matrix of x -> P^H x;  embed_n: the (2m) x (2k) matrix of x -> A x.
+void embed_ph(int64_t npw, int64_t nq, const double2* P, int64_t ldp, SplitBF16Buf& out, cudaStream_t st);
+void embed_n(int64_t m, int64_t k, const double2* A, int64_t lda, SplitBF16Buf& out, cudaStream_t st);
+// complex FP32 block (m x nb) -> K-major bf16 pair with 2m reals per column
+void split_block(int64_t m, int64_t nb, const float2* x, int64_t ldx, SplitBF16Buf& out, cudaStream_t st);
 
 // ---------------------------------------------------------------- small kernels (blas.cu)
 // out = Dbd p: block-diagonal real D (packed row-major per-atom blocks) times complex p.

@@ -23,6 +23,9 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 TOL64 = 1e-11
 TOL32 = 2e-5
+# mixed form: projector products from bf16 (hi, lo) pairs (about 16 significant bits, unit
+# roundoff 2^-17 = 7.6e-6) with FP32 accumulation over up to 1.2e5 terms
+TOLMIX = 1e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -84,6 +87,31 @@ def test_apply_H_fp32(name):
     op = PWOperator.from_cell(cell)
     g = _ctx(cell)
     _close(_np(g.apply_H(_F(cell.Y0), prec=F32)), op.apply_H(cell.Y0), TOL32)
+
+
+@pytest.mark.parametrize("name", ["tiny_paw", "nc24", "paw48_37"])
+def test_apply_H_mixed_tensor_cores(name):
+    from paper_1406_4350_gb300 import MIXED
+    cell = CELLS[name]()
+    op = PWOperator.from_cell(cell)
+    g = _ctx(cell)
+    _close(_np(g.apply_H(_F(cell.Y0), prec=MIXED)), op.apply_H(cell.Y0), TOLMIX)
+    g.sync_status()
+
+
+@pytest.mark.parametrize("name,degree", [("tiny_paw", 5), ("nc24", 8), ("paw48_37", 10)])
+def test_cheb_filter_mixed(name, degree):
+    from paper_1406_4350_gb300 import MIXED
+    cell = CELLS[name]()
+    op = PWOperator.from_cell(cell)
+    lo = float(ch.rayleigh_quotients(op, cell.Y0).max())
+    hi = ch.upper_bound(op, "rigorous")
+    ref = ch.filter_reuse(op, cell.Y0, degree, lo, hi)
+    g = _ctx(cell)
+    Y = _F(cell.Y0)
+    g.cheb_filter(Y, degree, lo, hi, prec=MIXED)
+    g.sync_status()
+    _close(_np(Y), ref, TOLMIX * degree)
 
 
 @pytest.mark.parametrize("name,degree", [("tiny_paw", 5), ("tiny_nc", 3), ("nc24", 8), ("paw48_37", 10)])
@@ -149,7 +177,7 @@ def _golden(name):
     return np.loadtxt(os.path.join(HERE, "golden", "%s_exact_eigs.txt" % name))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_solve_nc24_reaches_exact_eigenvalues(prec):
     """Config nc24 (degree 8; 7 sweeps, the count that reaches the target from the random
     start): lowest 75 % of the bands within 1e-8 Ha of the exact pencil eigenvalues
@@ -273,9 +301,13 @@ def paw96():
 def test_full_size_apply_H_sampled_bands(paw96):
     """The 96^3 / 60005-plane-wave / 2048-projector workload: a sample of bands against
     the oracle, through the same entry points the benchmark uses."""
+    from paper_1406_4350_gb300 import MIXED
     cols = [0, 777, 2047]
     Ys = np.asfortranarray(paw96.Y0[:, cols])
     op = PWOperator.from_cell(paw96)
     g = _ctx(paw96)
-    _close(_np(g.apply_H(_F(Ys))), op.apply_H(Ys), TOL64)
+    ref = op.apply_H(Ys)
+    _close(_np(g.apply_H(_F(Ys))), ref, TOL64)
     _close(_np(g.apply_Sinv(_F(Ys))), op.apply_Sinv(Ys), TOL64)
+    _close(_np(g.apply_H(_F(Ys), prec=MIXED)), ref, TOLMIX)
+    g.sync_status()
