@@ -188,15 +188,32 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    prof_acc = {"filter": {}, "rr": {}}
+
+    def _acc(phase):
+        for k, (ms, cnt, wk) in g.profile_totals().items():
+            a = prof_acc[phase].setdefault(k, [0.0, 0, 0.0])
+            a[0] += ms
+            a[1] += cnt
+            a[2] += wk
+
     def step(p, timed=None):
         nonlocal lo
         st = torch.cuda.current_stream()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        if timed is not None:
+            g.profile(True)
         e0.record(st)
         g.cheb_filter(Y, DEGREE, lo, hi, prec=p)
         e1.record(st)
+        if timed is not None:
+            _acc("filter")
+            g.profile(True)
         ev, rs = g.rayleigh_ritz(Y)
         e2.record(st)
+        if timed is not None:
+            _acc("rr")
+            g.profile(False)
         lo = float(ev.max().item())
         if timed is not None:
             timed.append((e0, e1, e2, ev, rs))
@@ -206,7 +223,6 @@ def main():
     barrier()
     launches0 = g.kernel_launches
     timed = []
-    g.profile(True)
     with Clocks(local) as clk:
         barrier()
         t0 = time.perf_counter()
@@ -214,9 +230,7 @@ def main():
             step(prec, timed)
         barrier()
         wall = time.perf_counter() - t0
-    g.profile(False)
     launches = g.kernel_launches - launches0
-    prof = g.profile_totals()
     filt_ms = [a.elapsed_time(b_) for a, b_, c, _, _ in timed]
     rr_ms = [b_.elapsed_time(c) for a, b_, c, _, _ in timed]
     step_ms = [a.elapsed_time(c) for a, b_, c, _, _ in timed]
@@ -268,32 +282,36 @@ def main():
     e2e_s = ea.elapsed_time(eb) / 1e3
     nbytes = npw * nb * 16
 
-    # roofline of the dominant kernel over the timed region
+    # roofline of the dominant kernel over the timed region, from the library's per-launch
+    # CUDA events and each launch's algorithmic work (flops for GEMMs, bytes for the FFT passes)
     peaks = _peaks()
-    name, (ms_tot, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
-    avg_s = ms_tot / cnt / 1e3
-    gemm_flops = 8.0 * npw * nq * nb  # one projector GEMM launch (P^H Z or P W) on all bands
-    if name in ("gemm_PhY", "gemm_PW", "tc_gemm_PhY", "tc_gemm_PW"):
-        tensor = name.startswith("tc_")
-        if tensor:
-            peak, bound, unit, pname = peaks.get("bf16_tflops_sustained", 1713.1), "tensor", "TFLOP/s", \
-                "bf16_tflops_sustained (measured)"
-        elif prec == F64:
-            peak, bound, unit, pname = 1.25, "alu", "TFLOP/s", "FP64 nominal 1.25 TFLOP/s (recipe)"
+
+    def roofline(phase, name):
+        ms_tot, cnt, work = prof_acc[phase][name]
+        avg_s = ms_tot / cnt / 1e3
+        if name.startswith("tc_"):
+            peak, bound, unit, src = peaks.get("bf16_tflops_sustained", 1713.1), "tensor", "TFLOP/s", \
+                "bf16_tflops_sustained (measured); bf16x3 executes 3x the algorithmic flops"
+        elif "gemm" in name:
+            fp64 = phase == "rr" or prec == F64
+            if fp64:
+                peak, bound, unit, src = 1.25, "alu", "TFLOP/s", "FP64 nominal 1.25 TFLOP/s (recipe)"
+            else:
+                peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                bound, unit, src = "alu", "TFLOP/s", "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max clock"
         else:
-            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            bound, unit, pname = "alu", "TFLOP/s", "FP32 FFMA 152 SMs x 128 lanes x 2 x max clock"
-        achieved = gemm_flops / avg_s / 1e12
-    else:
-        # FFT passes: algorithmic bytes = read + write of the column buffer
-        esz = 8 if prec != F64 else 16
-        ncol = len({(int(a), int(b_)) for a, b_ in cell.miller[:, :2]})  # (x, y) columns of the sphere
-        bytes_launch = 2.0 * cell.grid[2] * ncol * nb * esz
-        peak, bound, unit, pname = peaks.get("hbm_gbs", 6762.3), "hbm", "GB/s", "hbm_gbs (measured)"
-        achieved = bytes_launch / avg_s / 1e9
-    roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "peak_source": pname,
-            "avg_launch_ms": avg_s * 1e3, "launches": cnt}
+            peak, bound, unit, src = peaks.get("hbm_gbs", 6762.3), "hbm", "GB/s", "hbm_gbs (measured)"
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        achieved = work / cnt / avg_s / scale
+        return {"bound": bound, "kernel": name, "phase": phase, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
+                "launches_per_step": cnt / args.steps, "work_per_launch": work / cnt}
+
+    allk = [(v[0], ph, k) for ph in prof_acc for k, v in prof_acc[ph].items()]
+    _, ph_dom, k_dom = max(allk)
+    roof = roofline(ph_dom, k_dom)
+    _, k_fdom = max((v[0], k) for k, v in prof_acc["filter"].items())
+    roof_filter = roofline("filter", k_fdom)
 
     # eigenvalue state after the timed steps (residual norms in FP64)
     k75 = (3 * nb) // 4
@@ -314,7 +332,10 @@ def main():
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "roofline": roof,
-        "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:12]},
+        "filter_roofline": roof_filter,
+        "kernels_ms": {ph: {k: round(v[0] / args.steps, 3) for k, v in sorted(prof_acc[ph].items(),
+                                                                              key=lambda kv: -kv[1][0])[:10]}
+                       for ph in prof_acc},
         "ritz": {"max_residual_lowest_75pct": float(rs_last[:k75].max()), "lambda_min": float(ev_last[0])},
         "clocks": clocks,
         "wall_s_timed": wall,

@@ -160,8 +160,11 @@ int chebfi_profile_enable(chebfi_ctx* ctx, int enable);
 /* Number of distinct kernel names with totals (synchronises); negative on error. */
 int chebfi_profile_count(chebfi_ctx* ctx);
 /* Entry i (0 <= i < count): kernel name (NUL-terminated, at most name_len bytes including
- * the NUL), total milliseconds and number of launches.  Any output pointer may be NULL. */
-int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, double* ms, int64_t* launches);
+ * the NUL), total milliseconds, number of launches, and the summed algorithmic work of
+ * those launches (flops for GEMMs, 8 M N K complex or 2 M N K real; bytes read + written
+ * for the FFT passes).  Any output pointer may be NULL. */
+int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, double* ms, int64_t* launches,
+                         double* work);
 
 #ifdef __cplusplus
 }

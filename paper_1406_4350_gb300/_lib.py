@@ -51,7 +51,7 @@ SIGNATURES = {
     "chebfi_profile_enable": (c_int, [c_void_p, c_int]),
     "chebfi_profile_count": (c_int, [c_void_p]),
     "chebfi_profile_entry": (c_int, [c_void_p, c_int, ctypes.c_char_p, c_int, P_double,
-                                     ctypes.POINTER(c_int64)]),
+                                     ctypes.POINTER(c_int64), P_double]),
 }
 
 _lib = None

@@ -210,7 +210,7 @@ class ChebFI:
         self._check(self.lib.chebfi_profile_enable(self.h, 1 if enable else 0))
 
     def profile_totals(self):
-        """{kernel name: (total ms, launches)} recorded while profiling was on."""
+        """{kernel name: (total ms, launches, algorithmic work)} recorded while profiling was on."""
         n = self.lib.chebfi_profile_count(self.h)
         if n < 0:
             self._check(n)
@@ -219,8 +219,10 @@ class ChebFI:
         for i in range(n):
             ms = ctypes.c_double()
             cnt = ctypes.c_int64()
-            self._check(self.lib.chebfi_profile_entry(self.h, i, buf, 128, ctypes.byref(ms), ctypes.byref(cnt)))
-            out[buf.value.decode()] = (ms.value, cnt.value)
+            wk = ctypes.c_double()
+            self._check(self.lib.chebfi_profile_entry(self.h, i, buf, 128, ctypes.byref(ms), ctypes.byref(cnt),
+                                                      ctypes.byref(wk)))
+            out[buf.value.decode()] = (ms.value, cnt.value, wk.value)
         return out
 
     @property

@@ -43,9 +43,11 @@ void Profiler::flush() {
       names.push_back(r.name);
       ms.push_back(0.0);
       count.push_back(0);
+      work.push_back(0.0);
     }
     ms[i] += t;
     count[i] += 1;
+    work[i] += r.work;
     pool.push_back(r.a);
     pool.push_back(r.b);
   }
@@ -60,9 +62,10 @@ Profiler::~Profiler() {
   for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
-void prof_begin(const char* name, cudaStream_t st) {
+void prof_begin(const char* name, cudaStream_t st, double work) {
   if (!g_prof || !g_prof->on) return;
   g_prof->cur = name;
+  g_prof->cur_work = work;
   g_prof->cur_a = g_prof->get();
   CHEBFI_CUDA(cudaEventRecord(g_prof->cur_a, st));
 }
@@ -71,7 +74,7 @@ void prof_end(cudaStream_t st) {
   if (!g_prof || !g_prof->on || !g_prof->cur_a) return;
   cudaEvent_t b = g_prof->get();
   CHEBFI_CUDA(cudaEventRecord(b, st));
-  g_prof->pending.push_back({g_prof->cur, g_prof->cur_a, b});
+  g_prof->pending.push_back({g_prof->cur, g_prof->cur_a, b, g_prof->cur_work});
   g_prof->cur_a = nullptr;
   if (g_prof->pending.size() >= 8192) g_prof->flush();
 }
@@ -152,7 +155,7 @@ template <> struct Ops<float> {
 // H Y (FP64 or FP32) with the projections p = P^H Y returned; sorted order, ld = npw.
 template <typename R>
 void apply_H_sorted(chebfi_ctx* ctx, const cplx<R>* Y, cplx<R>* HY, cplx<R>* p, cplx<R>* Dp, cplx<R>* T, int64_t nb,
-                    cudaStream_t st) {
+                    cudaStream_t st, const char* tag = "gemm_H") {
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   LocalEpi<R> ep;
   ep.Y = Y;
@@ -161,9 +164,9 @@ void apply_H_sorted(chebfi_ctx* ctx, const cplx<R>* Y, cplx<R>* HY, cplx<R>* p, 
   ep.ldz = npw;
   local_apply<R>(ctx, Y, npw, nb, T, ep, st);
   if (nq > 0) {
-    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, p, nq, st, Ops<R>::ws(ctx));
+    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, p, nq, st, Ops<R>::ws(ctx), tag);
     blockdiag_apply<R>(ctx, Ops<R>::D(ctx), p, nq, Dp, nq, nb, st);
-    gemm<R>(false, false, npw, nb, nq, 1.0, Ops<R>::P(ctx), npw, Dp, nq, 1.0, HY, npw, st, Ops<R>::ws(ctx));
+    gemm<R>(false, false, npw, nb, nq, 1.0, Ops<R>::P(ctx), npw, Dp, nq, 1.0, HY, npw, st, Ops<R>::ws(ctx), tag);
   }
 }
 
@@ -388,13 +391,13 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   double2* Y = w.Ya.p;
   DevBuf<double2>* ws = &w.splitk;
   // H Y and p = P^H Y
-  apply_H_sorted<double>(ctx, Y, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st);
+  apply_H_sorted<double>(ctx, Y, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st, "gemm_rr");
   double2 *Hs = w.small1.p, *Ss = w.small2.p, *Li = w.small3.p, *X = w.small4.p;
-  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, w.HY.p, npw, 0.0, Hs, nb, st, ws);
-  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws);
+  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, w.HY.p, npw, 0.0, Hs, nb, st, ws, "gemm_rr");
+  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws, "gemm_rr");
   if (ctx->paw) {
     blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
-    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws);
+    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws, "gemm_rr");
   }
   hermitize(nb, Hs, nb, st);
   hermitize(nb, Ss, nb, st);
@@ -406,27 +409,27 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   cholesky(nb, Ss, nb, ctx->d_status.p, st, ws);
   set_identity(nb, Li, nb, st);
   trsm_lower(nb, nb, Ss, nb, Li, nb, st, ws);
-  gemm<double>(false, false, nb, nb, nb, 1.0, Li, nb, Hs, nb, 0.0, X, nb, st, ws);
-  gemm<double>(false, true, nb, nb, nb, 1.0, X, nb, Li, nb, 0.0, Hs, nb, st, ws);
+  gemm<double>(false, false, nb, nb, nb, 1.0, Li, nb, Hs, nb, 0.0, X, nb, st, ws, "gemm_rr");
+  gemm<double>(false, true, nb, nb, nb, 1.0, X, nb, Li, nb, 0.0, Hs, nb, st, ws, "gemm_rr");
   hermitize(nb, Hs, nb, st);
   // C = Z Lambda Z^H
   jacobi_eigh(nb, Hs, nb, evals, X, nb, ctx->d_status.p, st, &w.small5);
   check_status(ctx, st, "rayleigh_ritz");
   // rotation R = s L^{-H} Z; Y <- Y R, HY <- HY R, p <- p R
-  gemm<double>(true, false, nb, nb, nb, 1.0, Li, nb, X, nb, 0.0, Ss, nb, st, ws);
+  gemm<double>(true, false, nb, nb, nb, 1.0, Li, nb, X, nb, 0.0, Ss, nb, st, ws, "gemm_rr");
   scale_rows(nb, nb, Ss, nb, w.dvec1.p, st);
-  gemm<double>(false, false, npw, nb, nb, 1.0, Y, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws);
+  gemm<double>(false, false, npw, nb, nb, 1.0, Y, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws, "gemm_rr");
   std::swap(w.Ya.p, w.tmp.p);  // buffers have equal capacity
   std::swap(w.Ya.n, w.tmp.n);
   Y = w.Ya.p;
   if (resid) {
-    gemm<double>(false, false, npw, nb, nb, 1.0, w.HY.p, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws);  // H Y_new
+    gemm<double>(false, false, npw, nb, nb, 1.0, w.HY.p, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws, "gemm_rr");  // H Y_new
     double2* SY = w.HY.p;  // reuse
     CHEBFI_CUDA(cudaMemcpyAsync(SY, Y, sizeof(double2) * ny, cudaMemcpyDeviceToDevice, st));
     if (ctx->paw) {
-      gemm<double>(false, false, nq, nb, nb, 1.0, w.pa.p, nq, Ss, nb, 0.0, w.pc.p, nq, st, ws);  // p_new
+      gemm<double>(false, false, nq, nb, nb, 1.0, w.pa.p, nq, Ss, nb, 0.0, w.pc.p, nq, st, ws, "gemm_rr");  // p_new
       blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pc.p, nq, w.pb.p, nq, nb, st);
-      gemm<double>(false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, SY, npw, st, ws);
+      gemm<double>(false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, SY, npw, st, ws, "gemm_rr");
     }
     residual_norms(npw, nb, w.tmp.p, npw, SY, npw, evals, resid, st);
   }
@@ -1029,6 +1032,7 @@ int chebfi_profile_enable(chebfi_ctx* ctx, int enable) {
     ctx->prof.names.clear();
     ctx->prof.ms.clear();
     ctx->prof.count.clear();
+    ctx->prof.work.clear();
   }
   ctx->prof.on = enable != 0;
   API_END(ctx)
@@ -1046,7 +1050,8 @@ int chebfi_profile_count(chebfi_ctx* ctx) {
   return (int)ctx->prof.names.size();
 }
 
-int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, double* ms, int64_t* launches) {
+int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, double* ms, int64_t* launches,
+                         double* work) {
   API_BEGIN(ctx)
   ctx->prof.flush();
   CHEBFI_REQUIRE(i >= 0 && i < (int)ctx->prof.names.size(), CHEBFI_ERR_ARG, "profile entry out of range");
@@ -1056,6 +1061,7 @@ int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, doubl
   }
   if (ms) *ms = ctx->prof.ms[i];
   if (launches) *launches = ctx->prof.count[i];
+  if (work) *work = ctx->prof.work[i];
   API_END(ctx)
 }
 

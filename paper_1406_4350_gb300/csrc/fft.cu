@@ -235,8 +235,9 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
     const int nbc = (int)std::min<int64_t>(65535, nb - b0);
     dim3 gz((s.ncol + kCB - 1) / kCB, nbc);
-    CHEBFI_LAUNCH("k_zinv", st, k_zinv<R><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, sa, pz));
-    CHEBFI_LAUNCH("k_plane", st, k_plane<R><<<dim3(s.n3, nbc), kThreads, pbytes, st>>>(T, V, pa, px, py));
+    const double esz = sizeof(cplx<R>), col = (double)s.n3 * s.ncol * nbc * esz, sph = (double)ctx->npw * nbc * esz;
+    CHEBFI_LAUNCH_W("k_zinv", st, sph + col, k_zinv<R><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, sa, pz));
+    CHEBFI_LAUNCH_W("k_plane", st, 2.0 * col, k_plane<R><<<dim3(s.n3, nbc), kThreads, pbytes, st>>>(T, V, pa, px, py));
     LocalEpi<R> e = ep;
     e.Y = ep.Y + b0 * ep.ldy;
     if (e.Z) e.Z = ep.Z + b0 * ep.ldz;
@@ -247,7 +248,10 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
     if (e.T) e.T = ep.T + b0 * ep.ldt;
     if (e.Yprev) e.Yprev = ep.Yprev + b0 * ep.ldt;
     e.inv_n3 = (R)(1.0 / ((double)s.n1 * s.n2 * s.n3));
-    CHEBFI_LAUNCH("k_zfwd", st, k_zfwd<R><<<gz, kThreads, zbytes, st>>>(T, sa, pz, K, e));
+    // column buffer in, Y in, and the epilogue's sphere reads and writes
+    const double epi = sph * (1.0 + (e.Z ? 1.0 : 0.0) + (e.T ? 1.0 : 0.0) + (e.Yprev ? 1.0 : 0.0)) +
+                       (e.Zhi ? (double)ctx->npw * nbc * 8.0 : 0.0);
+    CHEBFI_LAUNCH_W("k_zfwd", st, col + epi, k_zfwd<R><<<gz, kThreads, zbytes, st>>>(T, sa, pz, K, e));
   }
 }
 

@@ -148,7 +148,7 @@ void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int
     wsp = ws->p;
   }
   dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)splits);
-  CHEBFI_LAUNCH(tag, st, k_gemm<R, CA, CB><<<grid, 256, 0, st>>>(M, N, K, (R)alpha, A, lda, B, ldb, (R)beta, Cm, ldc, kchunk, wsp));
+  CHEBFI_LAUNCH_W(tag, st, 8.0 * (double)M * (double)N * (double)K, k_gemm<R, CA, CB><<<grid, 256, 0, st>>>(M, N, K, (R)alpha, A, lda, B, ldb, (R)beta, Cm, ldc, kchunk, wsp));
   if (splits > 1) {
     const int64_t tot = M * N;
     CHEBFI_LAUNCH("k_splitk_reduce", st, k_splitk_reduce<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, wsp, (R)beta, Cm, ldc));

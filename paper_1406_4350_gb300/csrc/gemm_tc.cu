@@ -207,13 +207,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-      bool ok = true;
       for (int kt = 0; kt < num_k; ++kt) {
         const int s = kt % STAGES;
         const uint32_t par = (kt / STAGES) & 1;
         if (!mbar_wait(&full[s], par)) {
           flag(args.status, CHEBFI_ERR_CUDA);
-          ok = false;
           break;
         }
         tc_fence_after();
@@ -229,7 +227,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mma_commit(&empty[s]);
       }
-      (void)ok;
       mma_commit(accum);
     }
   } else {
@@ -325,7 +322,7 @@ void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64
   CHEBFI_CUDA(cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
   dim3 grid((unsigned)((N + tc::BN - 1) / tc::BN), (unsigned)((M + tc::BM - 1) / tc::BM));
   CHEBFI_REQUIRE(grid.y <= 65535, CHEBFI_ERR_ARG, "GEMM M too large");
-  CHEBFI_LAUNCH(tag, st, tc::k_tc_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(ah, al, bh, bl, a));
+  CHEBFI_LAUNCH_W(tag, st, 2.0 * (double)M * (double)N * (double)K, tc::k_tc_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(ah, al, bh, bl, a));
 }
 
 }  // namespace chebfi

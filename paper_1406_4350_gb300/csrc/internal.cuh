@@ -62,16 +62,18 @@ extern int64_t* g_launch_counter;
 // launch while a context has profiling switched on (chebfi_profile_enable).
 struct Profiler;
 extern Profiler* g_prof;
-void prof_begin(const char* name, cudaStream_t st);
+// work: the launch's algorithmic flops (GEMMs) or bytes (FFT passes), summed per name.
+void prof_begin(const char* name, cudaStream_t st, double work = 0.0);
 void prof_end(cudaStream_t st);
 
-#define CHEBFI_LAUNCH(name, st, ...)  \
-  do {                                \
-    ::chebfi::prof_begin(name, st);   \
-    __VA_ARGS__;                      \
-    ::chebfi::after_launch(name);     \
-    ::chebfi::prof_end(st);           \
+#define CHEBFI_LAUNCH_W(name, st, work, ...) \
+  do {                                       \
+    ::chebfi::prof_begin(name, st, work);    \
+    __VA_ARGS__;                             \
+    ::chebfi::after_launch(name);            \
+    ::chebfi::prof_end(st);                  \
   } while (0)
+#define CHEBFI_LAUNCH(name, st, ...) CHEBFI_LAUNCH_W(name, st, 0.0, __VA_ARGS__)
 
 // ----------------------------------------------------------------------------- device buffers
 template <typename T> struct DevBuf {
@@ -177,14 +179,17 @@ struct Profiler {
   struct Rec {
     const char* name;
     cudaEvent_t a, b;
+    double work;
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
   const char* cur = nullptr;
   cudaEvent_t cur_a = nullptr;
+  double cur_work = 0.0;
   std::vector<std::string> names;
   std::vector<double> ms;
   std::vector<int64_t> count;
+  std::vector<double> work;
   cudaEvent_t get();
   void flush();  // synchronises, folds pending records into the totals
   ~Profiler();
