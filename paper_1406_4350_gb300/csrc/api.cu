@@ -636,7 +636,7 @@ int chebfi_set_sphere(chebfi_ctx* ctx, int64_t npw, const int32_t* miller) {
   s.n3 = n3;
   s.pitch = n2 % 2 ? n2 : n2 + 1;
   s.zpitch = n3 % 2 ? n3 : n3 + 1;
-  std::vector<int32_t> col_start, pw_line(npw), pw_zrev(npw), col_off;
+  std::vector<int32_t> col_start, pw_line(npw), pw_zrev(npw), col_off, pw_znat(npw), col_nat;
   std::vector<char> xact(n1, 0);
   const std::vector<int>&rx = ctx->ax[0].rev, &ry = ctx->ax[1].rev, &rz = ctx->ax[2].rev;
   for (int64_t j = 0; j < npw; ++j) {
@@ -645,22 +645,30 @@ int chebfi_set_sphere(chebfi_ctx* ctx, int64_t npw, const int32_t* miller) {
       col_start.push_back((int32_t)j);
       const int x = (int)(key[u] / n2), y = (int)(key[u] % n2);
       col_off.push_back(rx[x] * s.pitch + ry[y]);
+      col_nat.push_back(x * s.pitch + y);
       xact[x] = 1;
     }
     pw_line[j] = (int32_t)col_start.size() - 1;
     pw_zrev[j] = rz[zz[u]];
+    pw_znat[j] = zz[u];
   }
   s.ncol = (int)col_start.size();
   col_start.push_back((int32_t)npw);
-  std::vector<int32_t> rows;
+  std::vector<int32_t> rows, rows_nat;
   for (int x = 0; x < n1; ++x)
-    if (xact[x]) rows.push_back(rx[x] * s.pitch);
+    if (xact[x]) {
+      rows.push_back(rx[x] * s.pitch);
+      rows_nat.push_back(x * s.pitch);
+    }
   s.nxa = (int)rows.size();
   s.col_start.upload(col_start.data(), col_start.size());
   s.pw_line.upload(pw_line.data(), npw);
   s.pw_zrev.upload(pw_zrev.data(), npw);
   s.col_off.upload(col_off.data(), col_off.size());
   s.rows_act.upload(rows.data(), rows.size());
+  s.pw_z.upload(pw_znat.data(), npw);
+  s.col_off_nat.upload(col_nat.data(), col_nat.size());
+  s.rows_nat.upload(rows_nat.data(), rows_nat.size());
   ctx->sorted_to_user = order;
   ctx->d_sorted_to_user.upload(order.data(), npw);
   // kinetic diagonal |k + G|^2 / 2 (Section 2.1), sorted order
@@ -709,6 +717,23 @@ int chebfi_set_vloc(chebfi_ctx* ctx, const double* vloc, int on_device) {
       }
   ctx->d_vt.upload(t.data(), n);
   ctx->d_vtf.upload(tf.data(), n);
+  ctx->fast_fft = fast_fft_supported(n1, n2, n3);
+  if (ctx->fast_fft) {
+    // position (z', x', y') of the two-pass kernels holds real-space point
+    // (split_index(x'), split_index(y'), split_index(z'))
+    std::vector<double> vs(n);
+    std::vector<float> vsf(n);
+    for (int pz = 0; pz < n3; ++pz)
+      for (int px = 0; px < n1; ++px)
+        for (int py = 0; py < n2; ++py) {
+          const int x = split_index(n1, px), y = split_index(n2, py), z = split_index(n3, pz);
+          const double v = h[((size_t)x * n2 + y) * n3 + z];
+          vs[((size_t)pz * n1 + px) * n2 + py] = v;
+          vsf[((size_t)pz * n1 + px) * n2 + py] = (float)v;
+        }
+    ctx->d_vs.upload(vs.data(), n);
+    ctx->d_vsf.upload(vsf.data(), n);
+  }
   CHEBFI_CUDA(cudaDeviceSynchronize());
   ctx->vmax = vmax;
   ctx->has_vloc = true;
@@ -1000,7 +1025,9 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
     else if (params->bound_mode == CHEBFI_BOUND_RIGOROUS) hi = rigorous_bound(ctx);
     else throw Error{CHEBFI_ERR_ARG, "unknown bound mode"};
   }
-  const double eps = params->prec == CHEBFI_F64 ? 2.220446049250313e-16 : params->prec == CHEBFI_F32 ? 1.1920929e-07 : 1.52587890625e-05;
+  // precision in which the filtered vectors are held (FP32 for both FP32 and mixed forms;
+  // the mixed form's tensor-core products perturb each application, not the storage)
+  const double eps = params->prec == CHEBFI_F64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
   gather_to_Ya(ctx, Y, nb, ld, st);
   ctx->w.tmp.alloc(ctx->w.Ya.n);
   // the first sweep's lambda_- comes from Rayleigh quotients; later sweeps reuse the Ritz

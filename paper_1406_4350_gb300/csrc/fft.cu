@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "fft_core.cuh"
+#include "fft_fast.cuh"
 #include "internal.cuh"
 #include "kernels.cuh"
 
@@ -184,6 +185,142 @@ __global__ void __launch_bounds__(kThreads) k_zfwd(const cplx<R>* __restrict__ T
   }
 }
 
+// ---------------------------------------------------------------- compile-time-length path
+// Same three passes with two-pass register codelets (fft_fast.cuh): the inverse transforms
+// leave real space in split order and the forward transforms read it back, so the z index
+// of the column buffer and the plane's (x, y) are split positions; V_loc is stored in the
+// same order.  Sphere points and columns are addressed at natural indices.
+constexpr int kCBF = 32;  // columns per z-pass block
+
+struct FastArgs {
+  int ncol, nxa, pitch, zpitch, ncolp;
+  int64_t ldt;
+  const int32_t* col_start;
+  const int32_t* pw_line;
+  const int32_t* pw_z;      // natural z of each sorted sphere point
+  const int32_t* col_off;   // natural x * pitch + y of each column
+  const int32_t* row_off;   // natural x * pitch of each active x
+};
+
+template <typename R, int N>
+__device__ __forceinline__ void load_tw(cplx<R>* s, const cplx<R>* g) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s[i] = g[i];
+}
+
+template <typename R, int N3>
+__global__ void __launch_bounds__(kThreads) k_zinv_f(const cplx<R>* __restrict__ Y, int64_t ldy,
+                                                     cplx<R>* __restrict__ T, FastArgs fa, const cplx<R>* __restrict__ twz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* lines = tw + N3;
+  load_tw<R, N3>(tw, twz);
+  const int c0 = blockIdx.x * kCBF;
+  const int nc = min(kCBF, fa.ncol - c0);
+  const int64_t b = blockIdx.y;
+  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
+  for (int i = threadIdx.x; i < kCBF * fa.zpitch; i += blockDim.x) lines[i] = zero;
+  __syncthreads();
+  const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
+  const cplx<R>* y = Y + b * ldy;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+    lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]] = y[j];
+  __syncthreads();
+  LineMap lm;
+  lm.stride = fa.zpitch;
+  fast::lines_F<N3, +1>(lines, nc, lm, 1, tw);
+  cplx<R>* t = T + b * fa.ldt + c0;
+  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
+    const int z = i / nc, l = i - z * nc;
+    t[(int64_t)z * fa.ncolp + l] = lines[l * fa.zpitch + z];
+  }
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(kThreads) k_plane_f(cplx<R>* __restrict__ T, const R* __restrict__ Vs, FastArgs fa,
+                                                      const cplx<R>* __restrict__ twxy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* plane = tw + N;
+  load_tw<R, N>(tw, twxy);
+  const int z = blockIdx.x;
+  const int64_t b = blockIdx.y;
+  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
+  for (int i = threadIdx.x; i < N * fa.pitch; i += blockDim.x) plane[i] = zero;
+  __syncthreads();
+  cplx<R>* t = T + b * fa.ldt + (int64_t)z * fa.ncolp;
+  for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) plane[fa.col_off[c]] = t[c];
+  __syncthreads();
+  LineMap rows;
+  rows.off = fa.row_off;
+  LineMap cols;
+  cols.stride = 1;
+  fast::lines_F<N, +1>(plane, fa.nxa, rows, 1, tw);       // along y on the rows that hold columns
+  fast::lines_F<N, +1>(plane, N, cols, fa.pitch, tw);     // along x on every y
+  const R* v = Vs + (int64_t)z * N * N;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int x = i / N, yy = i - x * N;
+    cplx<R>& e = plane[x * fa.pitch + yy];
+    const R s = v[i];
+    e.x *= s;
+    e.y *= s;
+  }
+  __syncthreads();
+  fast::lines_G<N, -1>(plane, N, cols, fa.pitch, tw);     // along x back to natural order
+  fast::lines_G<N, -1>(plane, fa.nxa, rows, 1, tw);       // along y on the needed rows
+  for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) t[c] = plane[fa.col_off[c]];
+}
+
+template <typename R, int N3>
+__global__ void __launch_bounds__(kThreads) k_zfwd_f(const cplx<R>* __restrict__ T, FastArgs fa,
+                                                     const cplx<R>* __restrict__ twz, const R* __restrict__ K,
+                                                     LocalEpi<R> ep) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* lines = tw + N3;
+  load_tw<R, N3>(tw, twz);
+  const int c0 = blockIdx.x * kCBF;
+  const int nc = min(kCBF, fa.ncol - c0);
+  const int64_t b = blockIdx.y;
+  const cplx<R>* t = T + b * fa.ldt + c0;
+  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
+    const int z = i / nc, l = i - z * nc;
+    lines[l * fa.zpitch + z] = t[(int64_t)z * fa.ncolp + l];
+  }
+  __syncthreads();
+  LineMap lm;
+  lm.stride = fa.zpitch;
+  fast::lines_G<N3, -1>(lines, nc, lm, 1, tw);
+  const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
+  const cplx<R>* y = ep.Y + b * ep.ldy;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const cplx<R> v = lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]];
+    const cplx<R> yj = y[j];
+    const R k = K[j];
+    cplx<R> zj;
+    zj.x = v.x * ep.inv_n3 + k * yj.x;
+    zj.y = v.y * ep.inv_n3 + k * yj.y;
+    if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
+    if (ep.Zhi) {
+      const float zr = (float)zj.x, zi = (float)zj.y;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi);
+      __nv_bfloat16* ph = ep.Zhi + b * ep.ldzb + 2 * j;
+      __nv_bfloat16* pl = ep.Zlo + b * ep.ldzb + 2 * j;
+      ph[0] = hr;
+      ph[1] = hi_;
+      pl[0] = __float2bfloat16_rn(zr - __bfloat162float(hr));
+      pl[1] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
+    }
+    if (ep.T) {
+      cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
+      if (ep.Yprev) tp = ep.Yprev[b * ep.ldt + j];
+      cplx<R> o;
+      o.x = ep.a * (zj.x - ep.c * yj.x) - ep.bprev * tp.x;
+      o.y = ep.a * (zj.y - ep.c * yj.y) - ep.bprev * tp.y;
+      ep.T[b * ep.ldt + j] = o;
+    }
+  }
+}
+
 template <typename R> void set_smem(const void* f, size_t bytes) {
   CHEBFI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
@@ -193,6 +330,86 @@ template <typename R> void set_smem(const void* f, size_t bytes) {
 size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb) {
   const int ncolp = (ctx->sph.ncol + 15) / 16 * 16;
   return (size_t)ctx->grid[2] * ncolp * (size_t)nb;
+}
+
+template <typename R, int N>
+void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T, LocalEpi<R> ep,
+                 cudaStream_t st, const R* K) {
+  const SphereFFT& s = ctx->sph;
+  FastArgs fa;
+  fa.ncol = s.ncol;
+  fa.nxa = s.nxa;
+  fa.pitch = s.pitch;
+  fa.zpitch = s.zpitch;
+  fa.ncolp = (s.ncol + 15) / 16 * 16;
+  fa.ldt = (int64_t)N * fa.ncolp;
+  fa.col_start = s.col_start.p;
+  fa.pw_line = s.pw_line.p;
+  fa.pw_z = s.pw_z.p;
+  fa.col_off = s.col_off_nat.p;
+  fa.row_off = s.rows_nat.p;
+  const cplx<R>* tw = sizeof(R) == 8 ? (const cplx<R>*)ctx->ax[0].tw64.p : (const cplx<R>*)ctx->ax[0].tw32.p;
+  const R* Vs = sizeof(R) == 8 ? (const R*)ctx->d_vs.p : (const R*)ctx->d_vsf.p;
+  const size_t zbytes = (size_t)(N + kCBF * s.zpitch) * sizeof(cplx<R>);
+  const size_t pbytes = (size_t)(N + N * s.pitch) * sizeof(cplx<R>);
+  set_smem<R>((const void*)k_plane_f<R, N>, pbytes);
+  set_smem<R>((const void*)k_zinv_f<R, N>, zbytes);
+  set_smem<R>((const void*)k_zfwd_f<R, N>, zbytes);
+  for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
+    const int nbc = (int)std::min<int64_t>(65535, nb - b0);
+    dim3 gz((s.ncol + kCBF - 1) / kCBF, nbc);
+    const double esz = sizeof(cplx<R>), col = (double)N * s.ncol * nbc * esz, sph = (double)ctx->npw * nbc * esz;
+    CHEBFI_LAUNCH_W("k_zinv", st, sph + col, k_zinv_f<R, N><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, fa, tw));
+    CHEBFI_LAUNCH_W("k_plane", st, 2.0 * col, k_plane_f<R, N><<<dim3(N, nbc), kThreads, pbytes, st>>>(T, Vs, fa, tw));
+    LocalEpi<R> e = ep;
+    e.Y = ep.Y + b0 * ep.ldy;
+    if (e.Z) e.Z = ep.Z + b0 * ep.ldz;
+    if (e.Zhi) {
+      e.Zhi = ep.Zhi + b0 * ep.ldzb;
+      e.Zlo = ep.Zlo + b0 * ep.ldzb;
+    }
+    if (e.T) e.T = ep.T + b0 * ep.ldt;
+    if (e.Yprev) e.Yprev = ep.Yprev + b0 * ep.ldt;
+    e.inv_n3 = (R)(1.0 / ((double)N * N * N));
+    const double epi = sph * (1.0 + (e.Z ? 1.0 : 0.0) + (e.T ? 1.0 : 0.0) + (e.Yprev ? 1.0 : 0.0)) +
+                       (e.Zhi ? (double)ctx->npw * nbc * 8.0 : 0.0);
+    CHEBFI_LAUNCH_W("k_zfwd", st, col + epi, k_zfwd_f<R, N><<<gz, kThreads, zbytes, st>>>(T, fa, tw, K, e));
+  }
+}
+
+// Compile-time-length path for cubic grids of the supported sizes; false = not taken.
+template <typename R>
+bool fast_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T, LocalEpi<R> ep,
+                cudaStream_t st, const R* K) {
+  switch (ctx->grid[0]) {
+    case 24: fast_launch<R, 24>(ctx, Y, ldy, nb, T, ep, st, K); return true;
+    case 32: fast_launch<R, 32>(ctx, Y, ldy, nb, T, ep, st, K); return true;
+    case 48: fast_launch<R, 48>(ctx, Y, ldy, nb, T, ep, st, K); return true;
+    case 64: fast_launch<R, 64>(ctx, Y, ldy, nb, T, ep, st, K); return true;
+    case 72: fast_launch<R, 72>(ctx, Y, ldy, nb, T, ep, st, K); return true;
+    case 96: fast_launch<R, 96>(ctx, Y, ldy, nb, T, ep, st, K); return true;
+    default: return false;
+  }
+}
+
+bool fast_fft_supported(int n1, int n2, int n3) {
+  if (n1 != n2 || n1 != n3) return false;
+  switch (n1) {
+    case 24: case 32: case 48: case 64: case 72: case 96: return true;
+    default: return false;
+  }
+}
+
+int split_index(int n, int p) {
+  switch (n) {
+    case 24: return fast::split_index<24>(p);
+    case 32: return fast::split_index<32>(p);
+    case 48: return fast::split_index<48>(p);
+    case 64: return fast::split_index<64>(p);
+    case 72: return fast::split_index<72>(p);
+    case 96: return fast::split_index<96>(p);
+    default: return p;
+  }
 }
 
 // (K + V_loc) applied to nb bands of sorted-order coefficients Y; the column buffer T
@@ -231,6 +448,7 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   set_smem<R>((const void*)k_zfwd<R>, zbytes);
   const R* K = sizeof(R) == 8 ? (const R*)ctx->d_K.p : (const R*)ctx->d_Kf.p;
   const R* V = sizeof(R) == 8 ? (const R*)ctx->d_vt.p : (const R*)ctx->d_vtf.p;
+  if (ctx->fast_fft && fast_apply<R>(ctx, Y, ldy, nb, T, ep, st, K)) return;
   // grid.y is limited to 65535: walk the bands in chunks
   for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
     const int nbc = (int)std::min<int64_t>(65535, nb - b0);

@@ -12,12 +12,15 @@
 // GEMMs whose A matrices (built once from P at setup) hold the 2 x 2 blocks
 // [[Re, Im], [-Im, Re]] and [[Re, -Im], [Im, Re]].
 //
-// One CTA computes one 128 x 256 tile: warp 0 issues the TMA loads (128-byte swizzle,
-// two-stage mbarrier ring), warp 1 allocates 256 TMEM columns and issues the MMAs
-// (tcgen05.mma cta_group::1 kind::f16, M = 128, N = 256, K = 16), warps 2-5 drain the
-// accumulator with tcgen05.ld and write FP32 with the alpha/beta epilogue.  Every wait
-// on an mbarrier gives up after a fixed time, records an error code and lets the CTA
-// finish (the TMEM is released on every path).
+// One CTA computes one 128 x 128 tile: warp 0 issues the TMA loads (128-byte swizzle,
+// three-stage mbarrier ring), warp 1 allocates 256 TMEM columns and issues the MMAs
+// (tcgen05.mma cta_group::1 kind::f16, M = 128, N = 128, K = 16), warps 2-5 read the
+// accumulator with tcgen05.ld.  The long contractions of the projector products (K up to
+// 1.2e5) would lose accuracy in one tensor-core accumulator, so K is cut into chunks of
+// 8 k-tiles (96 MMAs): each chunk accumulates in one of two TMEM buffers while the
+// epilogue warps add the other, finished one into FP32 registers; the alpha/beta epilogue
+// writes the register sums.  Every wait on an mbarrier gives up after a fixed time,
+// records an error code and lets the CTA finish (the TMEM is released on every path).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -30,13 +33,14 @@
 namespace chebfi {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int CHUNK = 8;                                 // k-tiles per TMEM accumulation
 constexpr int A_BYTES = BM * BK * 2;                     // 16 KB
-constexpr int B_BYTES = BN * BK * 2;                     // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of both: 96 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
+constexpr int B_BYTES = BN * BK * 2;                     // 16 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of both: 64 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 2 * BN;                   // two accumulators
 constexpr unsigned long long WAIT_NS = 2000000000ull;    // 2 s per wait
 
 struct Args {
@@ -63,6 +67,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -160,19 +168,24 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* acc_full = empty + STAGES;   // [2]: MMAs of a chunk done
+  uint64_t* acc_empty = acc_full + 2;    // [2]: epilogue has drained the buffer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
   const int num_k = (args.K + BK - 1) / BK;
+  const int num_chunks = (num_k + CHUNK - 1) / CHUNK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -207,51 +220,80 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-      for (int kt = 0; kt < num_k; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t par = (kt / STAGES) & 1;
-        if (!mbar_wait(&full[s], par)) {
+      bool ok = true;
+      int kt = 0;
+      for (int ch = 0; ch < num_chunks && ok; ++ch) {
+        const int acc = ch & 1;
+        if (ch >= 2 && !mbar_wait(&acc_empty[acc], ((ch >> 1) - 1) & 1)) {
           flag(args.status, CHEBFI_ERR_CUDA);
           break;
         }
         tc_fence_after();
-        const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        const int kend = min(num_k, (ch + 1) * CHUNK);
+        for (; kt < kend; ++kt) {
+          const int s = kt % STAGES;
+          const uint32_t par = (kt / STAGES) & 1;
+          if (!mbar_wait(&full[s], par)) {
+            flag(args.status, CHEBFI_ERR_CUDA);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+          const bool first = kt == ch * CHUNK;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t off = kk * 32;  // 16 bf16 along K
-          const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + A_BYTES + off);
-          const uint64_t bh = sw128_desc(base + 2 * A_BYTES + off), bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + off);
-          mma_bf16(tmem, ah, bh, idesc, (kt | kk) != 0);
-          mma_bf16(tmem, ah, bl, idesc, 1);
-          mma_bf16(tmem, al, bh, idesc, 1);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;  // 16 bf16 along K
+            const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + A_BYTES + off);
+            const uint64_t bh = sw128_desc(base + 2 * A_BYTES + off),
+                           bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + off);
+            mma_bf16(d, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
+            mma_bf16(d, ah, bl, idesc, 1);
+            mma_bf16(d, al, bh, idesc, 1);
+          }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        mma_commit(&acc_full[acc]);
       }
-      mma_commit(accum);
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. tile rows
+    // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31, i.e. tile rows
     const int lane_base = 32 * (warp % 4);
     const int m = m0 + lane_base + lane;
-    if (mbar_wait(accum, 0)) {
+    float racc[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) racc[j] = 0.f;
+    bool ok = true;
+    for (int ch = 0; ch < num_chunks; ++ch) {
+      const int acc = ch & 1;
+      if (!mbar_wait(&acc_full[acc], (ch >> 1) & 1)) {
+        flag(args.status, CHEBFI_ERR_CUDA);
+        ok = false;
+        break;
+      }
       tc_fence_after();
+#pragma unroll
       for (int c = 0; c < BN; c += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c, v);
-        if (m < args.M) {
+        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(acc * BN + c), v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c + j;
-            if (n < args.N) {
-              float o = args.alpha * v[j];
-              if (args.beta != 0.f) o = fmaf(args.beta, args.C[(int64_t)m + (int64_t)n * args.ldc], o);
-              args.D[(int64_t)m + (int64_t)n * args.ldd] = o;
-            }
-          }
+        for (int j = 0; j < 32; ++j) racc[c + j] += v[j];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+    }
+    if (ok && m < args.M) {
+#pragma unroll
+      for (int j = 0; j < BN; ++j) {
+        const int n = n0 + j;
+        if (n < args.N) {
+          float o = args.alpha * racc[j];
+          if (args.beta != 0.f) o = fmaf(args.beta, args.C[(int64_t)m + (int64_t)n * args.ldc], o);
+          args.D[(int64_t)m + (int64_t)n * args.ldd] = o;
         }
       }
-    } else {
-      flag(args.status, CHEBFI_ERR_CUDA);
     }
   }
   tc_fence_before();

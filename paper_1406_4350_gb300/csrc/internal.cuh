@@ -156,6 +156,10 @@ struct SphereFFT {
   DevBuf<int32_t> pw_zrev;     // sorted sphere point -> digit-reversed z position
   DevBuf<int32_t> col_off;     // column -> offset rev(x)*pitch + rev(y) in the plane
   DevBuf<int32_t> rows_act;    // active rows rev(x) of the plane (nxa)
+  // natural-index maps of the compile-time-length path
+  DevBuf<int32_t> pw_z;        // sorted sphere point -> z
+  DevBuf<int32_t> col_off_nat; // column -> x * pitch + y
+  DevBuf<int32_t> rows_nat;    // active rows x * pitch
 };
 
 // Workspace grown on demand (never shrinks while the context lives).
@@ -217,6 +221,9 @@ struct chebfi_ctx {
 
   chebfi::DevBuf<double> d_vt;   // V_loc, plane-major [z][x][y]
   chebfi::DevBuf<float> d_vtf;
+  bool fast_fft = false;         // cubic grid of a compiled size: two-pass FFT kernels
+  chebfi::DevBuf<double> d_vs;   // V_loc in split order [z'][x'][y'] for those kernels
+  chebfi::DevBuf<float> d_vsf;
   double vmax = 0.0;
 
   int64_t nproj = 0;

@@ -27,6 +27,10 @@ template <typename R> struct LocalEpi {
   R a = 0, c = 0, bprev = 0, inv_n3 = 0;
 };
 size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb);
+// the two-pass FFT kernels cover cubic grids of a few compiled sizes; split_index(n, p) is
+// the natural index held at position p of their split order
+bool fast_fft_supported(int n1, int n2, int n3);
+int split_index(int n, int p);
 template <typename R>
 void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T, LocalEpi<R> ep,
                  cudaStream_t st);
