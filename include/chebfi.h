@@ -147,6 +147,26 @@ int chebfi_rayleigh_quotients(chebfi_ctx* ctx, const void* Y, double* rq, int64_
 int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb, int64_t ld,
                  const chebfi_params* params, void* stream);
 
+/* Allocation-free variant of chebfi_apply_H (FP64): HY = H Y with the same arguments and
+ * result, for callers that cannot allocate device memory where they make the call -- host
+ * callbacks or latency-critical sections that must not take the CUDA allocator's lock,
+ * frameworks that own every byte of device memory through their own pool, and processes
+ * that have already reserved all of it.  The paper has no counterpart; this is a
+ * deployment convenience of this library.
+ *  - It calls no cudaMalloc / cudaFree and no allocating routine.  Its scratch is one
+ *    file-scope device array of 32 MiB inside the library; every GPU that loads the library
+ *    holds that array until the process exits.  (The context's own buffers were allocated
+ *    earlier, by the setters.)
+ *  - Bands are processed in chunks that fit the array.  A problem whose single band needs
+ *    more than 32 MiB of scratch (FFT column buffer N3 x columns, plus 2 npw + 2 nproj, in
+ *    complex doubles) is rejected with CHEBFI_ERR_ARG and a message naming the sizes.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the previous call's contents (nothing in it
+ *    needs to start at zero); calls that overlap on the GPU (other streams, other contexts
+ *    on the same device, other host threads) race on it. */
+int chebfi_apply_H_noalloc(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t ld, void* stream);
+
 /* Synchronise the context's work and return the first device-detected error, if any. */
 int chebfi_sync_status(chebfi_ctx* ctx);
 

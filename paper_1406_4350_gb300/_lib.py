@@ -36,6 +36,7 @@ SIGNATURES = {
                                       P_double, P_double]),
     "chebfi_upper_bound": (c_int, [c_void_p, c_int, P_double]),
     "chebfi_apply_H": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p]),
+    "chebfi_apply_H_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_apply_S": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_apply_Sinv": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_cheb_filter": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_double, c_double,
