@@ -48,3 +48,20 @@ def test_fft_stage_code_on_host(tmp_path):
     for n, d64a, d64b, d32a, d32b in rows:
         assert d64a < 2e-15 and d64b < 2e-15, n
         assert d32a < 1e-6 and d32b < 1e-6, n
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="nvcc not available")
+def test_two_pass_fft_code_on_host(tmp_path):
+    """The compile-time-length line FFTs (split-order F and its transpose G) against a
+    direct DFT, run pass by pass on the host."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    src = os.path.join(HERE, "native", "fft_fast_check.cu")
+    exe = str(tmp_path / "fftfast")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-x", "cu", src, "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    rows = [list(map(float, l.split())) for l in out if l.strip()]
+    assert [int(r[0]) for r in rows] == [16, 24, 32, 48, 64, 72, 96, 120, 128, 144]
+    for n, f64, g64, f32, g32 in rows:
+        assert f64 < 2e-15 and g64 < 2e-15, n
+        assert f32 < 1e-6 and g32 < 1e-6, n
