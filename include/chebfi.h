@@ -113,6 +113,23 @@ int chebfi_upper_bound(chebfi_ctx* ctx, int mode, double* lambda_hi);
  * as F32 here).  Y and HY must not overlap. */
 int chebfi_apply_H(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t ld,
                    int prec, void* stream);
+/* Replace the nonlocal coefficients D_V (Section 2.1) without rebuilding the projector
+ * data: D in the packed per-atom block layout of chebfi_set_projectors, host or device.
+ * G = P^H P and the Woodbury core do not depend on D.  Synchronises. */
+int chebfi_set_D(chebfi_ctx* ctx, const double* D, int on_device);
+
+/* Reverse-mode derivative of Algorithm 1's HY = H Y (FP64) for a real loss L, given
+ * G = the gradient of L at HY in the convention dL = Re sum conj(G) dHY (PyTorch's):
+ *   gY = H G                                               (H is Hermitian)
+ *   gV(r) = (1/(N1 N2 N3)) Re sum_n conj(g_n(r)) psi_n(r)  (g_n, psi_n: real-space values of
+ *           the columns of G and Y; gV laid out like V_loc in chebfi_set_vloc)
+ *   gD    = Re sum_n conj((P^H G)_in) (P^H Y)_jn on the per-atom blocks (packed like D).
+ * Any of gY (device, like Y), gV (device, N1*N2*N3 doubles), gD (device, packed) may be
+ * NULL to skip it.  With Y = G = an S-normalised eigenvector, gV is the Hellmann-Feynman
+ * derivative d lambda / d V_loc(r). */
+int chebfi_apply_H_backward(chebfi_ctx* ctx, const void* Y, const void* G, void* gY, double* gV, double* gD,
+                            int64_t nb, int64_t ld, void* stream);
+
 /* Algorithm 1: SY = S Y = Y + P Q P^H Y (FP64). */
 int chebfi_apply_S(chebfi_ctx* ctx, const void* Y, void* SY, int64_t nb, int64_t ld, void* stream);
 /* Section 4.1 (Woodbury): out = S^{-1} X = X - P M P^H X (FP64). */

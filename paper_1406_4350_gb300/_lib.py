@@ -37,6 +37,9 @@ SIGNATURES = {
     "chebfi_upper_bound": (c_int, [c_void_p, c_int, P_double]),
     "chebfi_apply_H": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p]),
     "chebfi_apply_H_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
+    "chebfi_set_D": (c_int, [c_void_p, c_void_p, c_int]),
+    "chebfi_apply_H_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
+                                        c_int64, c_void_p]),
     "chebfi_apply_S": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_apply_Sinv": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_cheb_filter": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_double, c_double,

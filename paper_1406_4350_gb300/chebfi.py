@@ -120,6 +120,15 @@ class ChebFI:
         del keep
         self.nproj = nproj
 
+    def set_D(self, D):
+        """Replace the nonlocal coefficient blocks D (packed like set_projectors' D)."""
+        if isinstance(D, torch.Tensor) and D.is_cuda:
+            d = D.detach().to(torch.float64).contiguous()
+            self._check(self.lib.chebfi_set_D(self.h, ctypes.c_void_p(d.data_ptr()), 1))
+        else:
+            d = np.ascontiguousarray(np.asarray(D, dtype=np.float64))
+            self._check(self.lib.chebfi_set_D(self.h, ctypes.c_void_p(d.ctypes.data), 0))
+
     @classmethod
     def from_cell(cls, cell, device: int = 0):
         """Context set up from a ``synth.Cell``-like object (lattice, grid, kpt, miller, vloc,
@@ -148,6 +157,24 @@ class ChebFI:
             raise ValueError("Y and out must share a leading dimension")
         self._check(self.lib.chebfi_apply_H(self.h, y, o, nb, ld, prec, _stream()))
         return out
+
+    def apply_H_backward(self, Y, G, grid, nD, want_Y=True, want_V=True, want_D=True):
+        """Gradients of a real loss through HY = H Y given G = dL/d(HY) (PyTorch convention):
+        returns (gY = H G, gV on the grid, gD packed like D); entries not wanted are None."""
+        y, nb, ld = _block(Y)
+        g, nbg, ldg = _block(G)
+        if nbg != nb or ldg != ld:
+            raise ValueError("Y and G must have the same shape and leading dimension")
+        gY = self._out_like(Y) if want_Y else None
+        gV = torch.empty(tuple(int(x) for x in grid), dtype=torch.float64, device=Y.device) if want_V else None
+        gD = torch.empty(int(nD), dtype=torch.float64, device=Y.device) if want_D else None
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        if gY is not None:
+            _, _, ldo = _block(gY)
+            if ldo != ld:
+                gY = torch.empty((nb, ld), dtype=torch.complex128, device=Y.device).T[: Y.shape[0]]
+        self._check(self.lib.chebfi_apply_H_backward(self.h, y, g, ptr(gY), ptr(gV), ptr(gD), nb, ld, _stream()))
+        return gY, gV, gD
 
     def apply_S(self, Y, out=None):
         out = self._out_like(Y) if out is None else out

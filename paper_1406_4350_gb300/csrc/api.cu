@@ -393,14 +393,15 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   // H Y and p = P^H Y
   apply_H_sorted<double>(ctx, Y, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st, "gemm_rr");
   double2 *Hs = w.small1.p, *Ss = w.small2.p, *Li = w.small3.p, *X = w.small4.p;
-  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, w.HY.p, npw, 0.0, Hs, nb, st, ws, "gemm_rr");
-  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws, "gemm_rr");
+  // H_Psi and S_Psi are Hermitian: only their lower triangles are computed, then mirrored
+  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, w.HY.p, npw, 0.0, Hs, nb, st, ws, "gemm_rr", true);
+  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws, "gemm_rr", true);
   if (ctx->paw) {
     blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
-    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws, "gemm_rr");
+    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws, "gemm_rr", true);
   }
-  hermitize(nb, Hs, nb, st);
-  hermitize(nb, Ss, nb, st);
+  mirror_lower(nb, Hs, nb, st);
+  mirror_lower(nb, Ss, nb, st);
   // columns scaled to unit S-norm: S~ = s S s, H~ = s H s with s = diag(S)^{-1/2}
   diag_of(nb, Ss, nb, w.dvec1.p, st);
   scale_sym(nb, Hs, nb, w.dvec1.p, st);
@@ -1089,6 +1090,65 @@ int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, doubl
   if (ms) *ms = ctx->prof.ms[i];
   if (launches) *launches = ctx->prof.count[i];
   if (work) *work = ctx->prof.work[i];
+  API_END(ctx)
+}
+
+int chebfi_set_D(chebfi_ctx* ctx, const double* D, int on_device) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(ctx->has_proj && ctx->nproj > 0, CHEBFI_ERR_STATE, "set_projectors (with projectors) first");
+  CHEBFI_REQUIRE(D, CHEBFI_ERR_ARG, "null D");
+  int64_t nblkv = 0;
+  for (int a = 0; a < ctx->natoms; ++a) {
+    const int64_t na = ctx->offs[a + 1] - ctx->offs[a];
+    nblkv += na * na;
+  }
+  std::vector<double> h(nblkv);
+  if (on_device) CHEBFI_CUDA(cudaMemcpy(h.data(), D, sizeof(double) * nblkv, cudaMemcpyDeviceToHost));
+  else std::memcpy(h.data(), D, sizeof(double) * nblkv);
+  for (double v : h) CHEBFI_REQUIRE(std::isfinite(v), CHEBFI_ERR_ARG, "D is not finite");
+  ctx->d_Dblk.upload(h.data(), nblkv);
+  std::vector<float> hf(h.begin(), h.end());
+  ctx->d_Dblkf.upload(hf.data(), nblkv);
+  CHEBFI_CUDA(cudaDeviceSynchronize());
+  ctx->bound_rigorous = -1.0;
+  API_END(ctx)
+}
+
+int chebfi_apply_H_backward(chebfi_ctx* ctx, const void* Y, const void* G, void* gY, double* gV, double* gD, int64_t nb,
+                            int64_t ld, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || G, CHEBFI_ERR_ARG, "null G");
+  cudaStream_t st = S(stream);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  if (nb == 0) {
+    if (gV) CHEBFI_CUDA(cudaMemsetAsync(gV, 0, sizeof(double) * ctx->grid[0] * ctx->grid[1] * ctx->grid[2], st));
+    return CHEBFI_OK;
+  }
+  // sorted copies: Y -> Ya, G -> Yb
+  w.Ya.alloc((size_t)npw * nb);
+  w.Yb.alloc((size_t)npw * nb);
+  gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y, ld, w.Ya.p, npw, st);
+  gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)G, ld, w.Yb.p, npw, st);
+  if (gY) {  // H is Hermitian: the gradient with respect to Y is H G
+    const size_t np = (size_t)std::max<int64_t>(nq, 1) * nb;
+    w.HY.alloc((size_t)npw * nb);
+    w.T1.alloc(local_workspace_elems(ctx, nb));
+    w.pa.alloc(np);
+    w.pb.alloc(np);
+    apply_H_sorted<double>(ctx, w.Yb.p, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st, "gemm_H");
+    scatter_from(ctx, w.HY.p, gY, nb, ld, st);
+  }
+  if (gD && nq > 0) {  // gD_ij = sum_n Re(conj((P^H G)_in) (P^H Y)_jn) on the atom blocks
+    w.pa.alloc((size_t)nq * nb);
+    w.pc.alloc((size_t)nq * nb);
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Yb.p, npw, 0.0, w.pa.p, nq, st, &w.splitk, "gemm_H");
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pc.p, nq, st, &w.splitk, "gemm_H");
+    block_outer_grad(ctx, w.pa.p, w.pc.p, nq, nb, gD, st);
+  }
+  if (gV) vloc_gradient(ctx, w.Ya.p, w.Yb.p, nb, gV, st, w.T2, w.tmp, w.tmp2);
   API_END(ctx)
 }
 

@@ -179,6 +179,38 @@ __global__ void k_hermitize(int64_t n, double2* A, int64_t lda) {
   A[j + i * lda] = make_double2(h.x, -h.y);
 }
 
+// one thread per (projector i, position j within i's atom block)
+__global__ void k_block_outer_grad(int64_t nproj, const int32_t* __restrict__ atom_of, const int32_t* __restrict__ offs,
+                                   const int64_t* __restrict__ blk_off, const double2* __restrict__ q,
+                                   const double2* __restrict__ p, int64_t ldp, int64_t nb, double* __restrict__ gD) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nproj * 64) return;
+  const int64_t i = idx / 64;
+  const int jl = (int)(idx % 64);
+  const int a = atom_of[i];
+  const int o = offs[a], na = offs[a + 1] - o;
+  if (jl >= na) return;
+  const int64_t j = o + jl;
+  double acc = 0.0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const double2 u = q[i + b * ldp], v = p[j + b * ldp];
+    acc += u.x * v.x + u.y * v.y;
+  }
+  gD[blk_off[a] + (i - o) * na + jl] = acc;
+}
+
+__global__ void k_mirror_lower(int64_t n, double2* A, int64_t lda) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  if (i < j) {
+    const double2 v = A[j + i * lda];
+    A[i + j * lda] = make_double2(v.x, -v.y);
+  } else if (i == j) {
+    A[i + i * lda].y = 0.0;
+  }
+}
+
 __global__ void k_reduce_max(int64_t n, const double* x, double* out) {
   __shared__ double red[256];
   double m = -1e300;
@@ -280,6 +312,17 @@ void scale_rows(int64_t n, int64_t m, double2* X, int64_t ldx, const double* d, 
 void hermitize(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
   if (n == 0) return;
   CHEBFI_LAUNCH("k_hermitize", st, k_hermitize<<<nblocks(n * n), 256, 0, st>>>(n, A, lda));
+}
+void block_outer_grad(const chebfi_ctx* ctx, const double2* q, const double2* p, int64_t ldp, int64_t nb, double* gD,
+                      cudaStream_t st) {
+  if (ctx->nproj == 0) return;
+  CHEBFI_LAUNCH("k_block_outer_grad", st,
+                k_block_outer_grad<<<nblocks(ctx->nproj * 64), 256, 0, st>>>(ctx->nproj, ctx->d_atom_of.p, ctx->d_offs.p,
+                                                                          ctx->d_blk_off.p, q, p, ldp, nb, gD));
+}
+void mirror_lower(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
+  if (n == 0) return;
+  CHEBFI_LAUNCH("k_mirror_lower", st, k_mirror_lower<<<nblocks(n * n), 256, 0, st>>>(n, A, lda));
 }
 void reduce_max(int64_t n, const double* x, double* out, cudaStream_t st) {
   CHEBFI_LAUNCH("k_reduce_max", st, k_reduce_max<<<1, 256, 0, st>>>(n, x, out));

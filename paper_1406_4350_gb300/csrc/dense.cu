@@ -187,54 +187,182 @@ __global__ void k_jac_params(int64_t n0, int64_t n, int64_t round, const double2
   pairs[2 * t + 1] = (int)q;
 }
 
-// A <- U^H A on rows p, q (every column j).
-__global__ void k_jac_rows(int64_t h, int64_t n, double2* A, int64_t lda, const Rot* __restrict__ rot,
-                           const int* __restrict__ pairs) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= h * n) return;
-  const int64_t t = idx % h, j = idx / h;
+// One round of rotations in one pass: thread (t1, t2) maps the 2 x 2 block of A on rows
+// {p1, q1} and columns {p2, q2} to U1^H A U2 (the pairs are disjoint, so every element of A
+// belongs to exactly one block); the remaining threads apply V <- V U2 on columns {p2, q2}.
+__device__ __forceinline__ void jac_apply_item(int64_t idx, int64_t h, int64_t n, double2* A, int64_t lda, double2* V,
+                                               int64_t ldv, const Rot* __restrict__ rot, const int* __restrict__ pairs) {
+  const int64_t nblk_a = h * h;
+  if (idx < nblk_a) {
+    const int64_t t1 = idx % h, t2 = idx / h;
+    const int q1 = pairs[2 * t1 + 1], q2 = pairs[2 * t2 + 1];
+    const int p1 = pairs[2 * t1], p2 = pairs[2 * t2];
+    const Rot r1 = rot[t1], r2 = rot[t2];
+    const bool act1 = q1 >= 0 && r1.s != 0.0, act2 = q2 >= 0 && r2.s != 0.0;
+    if (!act1 && !act2) return;
+    // the padding player (q < 0) never owns a row or column of A
+    if (q1 < 0 || q2 < 0) {
+      // a real pair against the padding: only the real pair's own rotation applies on its
+      // side of the blocks it shares with other pairs; handled as a 1 x 2 or 2 x 1 block
+      if (q1 < 0 && q2 < 0) return;
+      if (q1 < 0) {  // row p1 alone, columns {p2, q2} rotate by U2
+        double2 a = A[p1 + (int64_t)p2 * lda], b = A[p1 + (int64_t)q2 * lda];
+        const double2 sc = make_double2(r2.s * r2.ph.x, -r2.s * r2.ph.y), cc = make_double2(r2.c * r2.ph.x, -r2.c * r2.ph.y);
+        double2 na, nb;
+        na.x = r2.c * a.x - (b.x * sc.x - b.y * sc.y);
+        na.y = r2.c * a.y - (b.x * sc.y + b.y * sc.x);
+        nb.x = r2.s * a.x + (b.x * cc.x - b.y * cc.y);
+        nb.y = r2.s * a.y + (b.x * cc.y + b.y * cc.x);
+        A[p1 + (int64_t)p2 * lda] = na;
+        A[p1 + (int64_t)q2 * lda] = nb;
+      } else {  // column p2 alone, rows {p1, q1} rotate by U1^H
+        double2 a = A[p1 + (int64_t)p2 * lda], b = A[q1 + (int64_t)p2 * lda];
+        const double2 sph = make_double2(r1.s * r1.ph.x, r1.s * r1.ph.y), cph = make_double2(r1.c * r1.ph.x, r1.c * r1.ph.y);
+        double2 na, nb;
+        na.x = r1.c * a.x - (sph.x * b.x - sph.y * b.y);
+        na.y = r1.c * a.y - (sph.x * b.y + sph.y * b.x);
+        nb.x = r1.s * a.x + (cph.x * b.x - cph.y * b.y);
+        nb.y = r1.s * a.y + (cph.x * b.y + cph.y * b.x);
+        A[p1 + (int64_t)p2 * lda] = na;
+        A[q1 + (int64_t)p2 * lda] = nb;
+      }
+      return;
+    }
+    double2 m00 = A[p1 + (int64_t)p2 * lda], m10 = A[q1 + (int64_t)p2 * lda];
+    double2 m01 = A[p1 + (int64_t)q2 * lda], m11 = A[q1 + (int64_t)q2 * lda];
+    if (act1) {  // rows: [m0*; m1*] <- U1^H [m0*; m1*]
+      const double2 sph = make_double2(r1.s * r1.ph.x, r1.s * r1.ph.y), cph = make_double2(r1.c * r1.ph.x, r1.c * r1.ph.y);
+      double2 a0, a1;
+      a0.x = r1.c * m00.x - (sph.x * m10.x - sph.y * m10.y);
+      a0.y = r1.c * m00.y - (sph.x * m10.y + sph.y * m10.x);
+      a1.x = r1.s * m00.x + (cph.x * m10.x - cph.y * m10.y);
+      a1.y = r1.s * m00.y + (cph.x * m10.y + cph.y * m10.x);
+      m00 = a0;
+      m10 = a1;
+      a0.x = r1.c * m01.x - (sph.x * m11.x - sph.y * m11.y);
+      a0.y = r1.c * m01.y - (sph.x * m11.y + sph.y * m11.x);
+      a1.x = r1.s * m01.x + (cph.x * m11.x - cph.y * m11.y);
+      a1.y = r1.s * m01.y + (cph.x * m11.y + cph.y * m11.x);
+      m01 = a0;
+      m11 = a1;
+    }
+    if (act2) {  // columns: [m*0, m*1] <- [m*0, m*1] U2
+      const double2 sc = make_double2(r2.s * r2.ph.x, -r2.s * r2.ph.y), cc = make_double2(r2.c * r2.ph.x, -r2.c * r2.ph.y);
+      double2 b0, b1;
+      b0.x = r2.c * m00.x - (m01.x * sc.x - m01.y * sc.y);
+      b0.y = r2.c * m00.y - (m01.x * sc.y + m01.y * sc.x);
+      b1.x = r2.s * m00.x + (m01.x * cc.x - m01.y * cc.y);
+      b1.y = r2.s * m00.y + (m01.x * cc.y + m01.y * cc.x);
+      m00 = b0;
+      m01 = b1;
+      b0.x = r2.c * m10.x - (m11.x * sc.x - m11.y * sc.y);
+      b0.y = r2.c * m10.y - (m11.x * sc.y + m11.y * sc.x);
+      b1.x = r2.s * m10.x + (m11.x * cc.x - m11.y * cc.y);
+      b1.y = r2.s * m10.y + (m11.x * cc.y + m11.y * cc.x);
+      m10 = b0;
+      m11 = b1;
+    }
+    A[p1 + (int64_t)p2 * lda] = m00;
+    A[q1 + (int64_t)p2 * lda] = m10;
+    A[p1 + (int64_t)q2 * lda] = m01;
+    A[q1 + (int64_t)q2 * lda] = m11;
+    return;
+  }
+  const int64_t vidx = idx - nblk_a;
+  if (vidx >= n * h) return;
+  const int64_t i = vidx % n, t = vidx / n;
   const int q = pairs[2 * t + 1];
   if (q < 0) return;
   const Rot r = rot[t];
   if (r.s == 0.0) return;
   const int p = pairs[2 * t];
-  const double2 ap = A[p + j * lda], aq = A[q + j * lda];
-  // conj(u00) = c, conj(u10) = -s ph, conj(u01) = s, conj(u11) = c ph
-  const double2 sph = make_double2(r.s * r.ph.x, r.s * r.ph.y), cph = make_double2(r.c * r.ph.x, r.c * r.ph.y);
-  double2 np, nq;
-  np.x = r.c * ap.x - (sph.x * aq.x - sph.y * aq.y);
-  np.y = r.c * ap.y - (sph.x * aq.y + sph.y * aq.x);
-  nq.x = r.s * ap.x + (cph.x * aq.x - cph.y * aq.y);
-  nq.y = r.s * ap.y + (cph.x * aq.y + cph.y * aq.x);
-  A[p + j * lda] = np;
-  A[q + j * lda] = nq;
-}
-
-// A <- A U and V <- V U on columns p, q (every row i).
-__global__ void k_jac_cols(int64_t h, int64_t n, double2* A, int64_t lda, double2* V, int64_t ldv,
-                           const Rot* __restrict__ rot, const int* __restrict__ pairs) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t rows = 2 * n;  // n rows of A then n rows of V
-  if (idx >= h * rows) return;
-  const int64_t i2 = idx % rows, t = idx / rows;
-  const int q = pairs[2 * t + 1];
-  if (q < 0) return;
-  const Rot r = rot[t];
-  if (r.s == 0.0) return;
-  const int p = pairs[2 * t];
-  double2* M = i2 < n ? A : V;
-  const int64_t ld = i2 < n ? lda : ldv;
-  const int64_t i = i2 < n ? i2 : i2 - n;
-  const double2 ap = M[i + p * ld], aq = M[i + q * ld];
-  // u00 = c, u10 = -s conj(ph), u01 = s, u11 = c conj(ph)
+  const double2 ap = V[i + (int64_t)p * ldv], aq = V[i + (int64_t)q * ldv];
   const double2 sc = make_double2(r.s * r.ph.x, -r.s * r.ph.y), cc = make_double2(r.c * r.ph.x, -r.c * r.ph.y);
   double2 np, nq;
   np.x = r.c * ap.x - (aq.x * sc.x - aq.y * sc.y);
   np.y = r.c * ap.y - (aq.x * sc.y + aq.y * sc.x);
   nq.x = r.s * ap.x + (aq.x * cc.x - aq.y * cc.y);
   nq.y = r.s * ap.y + (aq.x * cc.y + aq.y * cc.x);
-  M[i + p * ld] = np;
-  M[i + q * ld] = nq;
+  V[i + (int64_t)p * ldv] = np;
+  V[i + (int64_t)q * ldv] = nq;
+}
+
+__global__ void k_jac_apply(int64_t h, int64_t n, double2* A, int64_t lda, double2* V, int64_t ldv,
+                            const Rot* __restrict__ rot, const int* __restrict__ pairs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  jac_apply_item(idx, h, n, A, lda, V, ldv, rot, pairs);
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks resident).  The wait is bounded:
+// after ~1 s it records CHEBFI_ERR_CUDA and lets the block go on.
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = atomicAdd(gen, 0u);
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned long long t0, t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      while (atomicAdd(gen, 0u) == g) {
+        __nanosleep(32);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull) {
+          flag_error(status, CHEBFI_ERR_CUDA);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// All n-1 rounds of one Jacobi sweep in one cooperative launch: per round, the rotation
+// parameters of the n/2 pairs, a grid barrier, the one-pass update of A and V, a barrier.
+__global__ void k_jac_sweep(int64_t n0, int64_t n, double2* A, int64_t lda, double2* V, int64_t ldv, Rot* rot,
+                            int* pairs, unsigned* bar, int* status) {
+  const int64_t h = n / 2;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t round = 0; round < n - 1; ++round) {
+    // parameters (same arithmetic as k_jac_params)
+    for (int64_t t = tid; t < h; t += nthreads) {
+      int64_t p = rr_player(t, round, n), q = rr_player(n - 1 - t, round, n);
+      if (p > q) {
+        const int64_t tmp = p;
+        p = q;
+        q = tmp;
+      }
+      Rot r;
+      r.c = 1.0;
+      r.s = 0.0;
+      r.ph = make_double2(1.0, 0.0);
+      if (q < n0) {
+        const double2 hh = A[p + q * lda];
+        const double g = hypot(hh.x, hh.y);
+        const double app = A[p + p * lda].x, aqq = A[q + q * lda].x;
+        if (g > 1e-300 && g > 1.1102230246251565e-16 * sqrt(fabs(app * aqq))) {
+          const double zeta = (aqq - app) / (2.0 * g);
+          const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+          r.c = 1.0 / sqrt(1.0 + t_ * t_);
+          r.s = t_ * r.c;
+          r.ph = make_double2(hh.x / g, hh.y / g);
+        }
+      } else {
+        q = -1;
+      }
+      rot[t] = r;
+      pairs[2 * t] = (int)p;
+      pairs[2 * t + 1] = (int)q;
+    }
+    grid_barrier(bar, bar + 1, gridDim.x, status);
+    for (int64_t i = tid; i < h * h + n0 * h; i += nthreads) jac_apply_item(i, h, n0, A, lda, V, ldv, rot, pairs);
+    grid_barrier(bar, bar + 1, gridDim.x, status);
+  }
 }
 
 // out[0] = sum of |off-diagonal|^2, out[1] = total |A|^2 (single block, fixed order).
@@ -326,11 +454,20 @@ void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int
   const size_t rot_c = (size_t)(n / 2) * sizeof(Rot) / sizeof(double2) + 1;
   const size_t pair_c = (size_t)n * sizeof(int) / sizeof(double2) + 1;
   const size_t vtmp = (size_t)n0 * n0;
-  ws->alloc(rot_c + pair_c + 2 + vtmp);
+  ws->alloc(rot_c + pair_c + 3 + vtmp);
   Rot* rot = reinterpret_cast<Rot*>(ws->p);
   int* pairs = reinterpret_cast<int*>(ws->p + rot_c);
   double* nrm = reinterpret_cast<double*>(ws->p + rot_c + pair_c);
-  double2* Vtmp = ws->p + rot_c + pair_c + 2;
+  unsigned* bar = reinterpret_cast<unsigned*>(ws->p + rot_c + pair_c + 2);
+  double2* Vtmp = ws->p + rot_c + pair_c + 3;
+  CHEBFI_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  // one cooperative launch per sweep when the device allows it (all blocks resident)
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  CHEBFI_CUDA(cudaGetDevice(&dev));
+  CHEBFI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  CHEBFI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CHEBFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_sweep, 256, 0));
+  const int coop_blocks = std::min(sms * std::min(per_sm, 4), 1024);
   set_identity(n0, Vtmp, n0, st);
   const int max_sweeps = 40;
   double prev_off = INFINITY;
@@ -348,10 +485,21 @@ void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int
     }
     if (sweep == max_sweeps) break;
     prev_off = off;
-    for (int64_t round = 0; round < n - 1; ++round) {
-      CHEBFI_LAUNCH("k_jac_params", st, k_jac_params<<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs));
-      CHEBFI_LAUNCH("k_jac_rows", st, k_jac_rows<<<nblk((n / 2) * n0), 256, 0, st>>>(n / 2, n0, A, lda, rot, pairs));
-      CHEBFI_LAUNCH("k_jac_cols", st, k_jac_cols<<<nblk((n / 2) * 2 * n0), 256, 0, st>>>(n / 2, n0, A, lda, Vtmp, n0, rot, pairs));
+    if (coop && coop_blocks > 0) {
+      int64_t n0a = n0, na = n, ldaa = lda, ldva = n0;
+      double2* Aa = A;
+      double2* Va = Vtmp;
+      void* args[] = {&n0a, &na, &Aa, &ldaa, &Va, &ldva, &rot, &pairs, &bar, &status};
+      CHEBFI_LAUNCH("k_jac_sweep", st,
+                    CHEBFI_CUDA(cudaLaunchCooperativeKernel((const void*)k_jac_sweep, dim3(coop_blocks), dim3(256), args,
+                                                            0, st)));
+    } else {
+      for (int64_t round = 0; round < n - 1; ++round) {
+        CHEBFI_LAUNCH("k_jac_params", st, k_jac_params<<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs));
+        const int64_t h = n / 2;
+        CHEBFI_LAUNCH("k_jac_apply", st,
+                      k_jac_apply<<<nblk(h * h + n0 * h), 256, 0, st>>>(h, n0, A, lda, Vtmp, n0, rot, pairs));
+      }
     }
   }
   if (!done) {

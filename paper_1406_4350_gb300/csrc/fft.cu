@@ -185,6 +185,53 @@ __global__ void __launch_bounds__(kThreads) k_zfwd(const cplx<R>* __restrict__ T
   }
 }
 
+// Real-space values on the full grid for the derivative with respect to V_loc: after the
+// inverse z pass, each (band, z) plane is transformed back along y and x and written out
+// as out[band][z][x][y] (natural order).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_plane_real(const cplx<R>* __restrict__ T, PlaneArgs pa, FFTPlan<R> px,
+                                                         FFTPlan<R> py, cplx<R>* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* plane = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int z = blockIdx.x;
+  const int64_t b = blockIdx.y;
+  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
+  for (int i = threadIdx.x; i < pa.n1 * pa.pitch; i += blockDim.x) plane[i] = zero;
+  __syncthreads();
+  const cplx<R>* t = T + b * pa.ldt + (int64_t)z * pa.ncolp;
+  for (int c = threadIdx.x; c < pa.ncol; c += blockDim.x) plane[pa.col_off[c]] = t[c];
+  __syncthreads();
+  LineMap rows;
+  rows.off = pa.row_off;
+  LineMap cols;
+  cols.stride = 1;
+  block_fft_dit<+1, R>(plane, pa.nxa, rows, 1, py);
+  block_fft_dit<+1, R>(plane, pa.n2, cols, pa.pitch, px);
+  cplx<R>* o = out + (b * pa.n3 + z) * (int64_t)pa.n1 * pa.n2;
+  for (int i = threadIdx.x; i < pa.n1 * pa.n2; i += blockDim.x) {
+    const int x = i / pa.n2, yy = i - x * pa.n2;
+    o[i] = plane[x * pa.pitch + yy];
+  }
+}
+
+// gV[(x n2 + y) n3 + z] += scale * sum_b Re(conj(g_b(r)) psi_b(r)), r = (x, y, z); fixed band order.
+template <typename R>
+__global__ void k_density_accum(int n1, int n2, int n3, int64_t nbc, const cplx<R>* __restrict__ psi,
+                                const cplx<R>* __restrict__ g, double scale, double* __restrict__ gV) {
+  const int64_t n = (int64_t)n1 * n2 * n3;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double acc = 0.0;
+  for (int64_t b = 0; b < nbc; ++b) {
+    const cplx<R> u = psi[b * n + r], v = g[b * n + r];
+    acc += (double)v.x * (double)u.x + (double)v.y * (double)u.y;
+  }
+  const int64_t plane = (int64_t)n1 * n2;
+  const int z = (int)(r / plane), rem = (int)(r - (int64_t)z * plane);
+  const int x = rem / n2, y = rem - x * n2;
+  gV[((int64_t)x * n2 + y) * n3 + z] += scale * acc;
+}
+
 // ---------------------------------------------------------------- compile-time-length path
 // Same three passes with two-pass register codelets (fft_fast.cuh): the inverse transforms
 // leave real space in split order and the forward transforms read it back, so the z index
@@ -255,17 +302,36 @@ __global__ void __launch_bounds__(kThreads) k_plane_f(cplx<R>* __restrict__ T, c
   LineMap cols;
   cols.stride = 1;
   fast::lines_F<N, +1>(plane, fa.nxa, rows, 1, tw);       // along y on the rows that hold columns
-  fast::lines_F<N, +1>(plane, N, cols, fa.pitch, tw);     // along x on every y
-  const R* v = Vs + (int64_t)z * N * N;
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    const int x = i / N, yy = i - x * N;
-    cplx<R>& e = plane[x * fa.pitch + yy];
-    const R s = v[i];
-    e.x *= s;
-    e.y *= s;
+  // along x on every y: F's pass A; then, per contiguous group, F's pass B, the multiply by
+  // V_loc and G's pass B in registers; then G's pass A
+  fast::F_passA<N, +1>(plane, N, cols, fa.pitch, tw, threadIdx.x, blockDim.x);
+  __syncthreads();
+  {
+    constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB;
+    const R* v = Vs + (int64_t)z * N * N;
+    for (int t = threadIdx.x; t < N * NA; t += blockDim.x) {
+      const int ka = t / N, yy = t - ka * N;
+      cplx<R>* a = plane + yy + NB * ka * fa.pitch;
+      const R* vv = v + (NB * ka) * N + yy;
+      cplx<R> u[NB];
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb) u[nb] = a[nb * fa.pitch];
+      fast::dft<NB, +1>(u);
+#pragma unroll
+      for (int kb = 0; kb < NB; ++kb) {
+        const R s = vv[kb * N];
+        u[kb].x *= s;
+        u[kb].y *= s;
+      }
+      fast::dft<NB, -1>(u);
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb)
+        a[nb * fa.pitch] = (ka == 0 || nb == 0) ? u[nb] : u[nb] * fast::twN<-1>(tw, nb * ka);
+    }
   }
   __syncthreads();
-  fast::lines_G<N, -1>(plane, N, cols, fa.pitch, tw);     // along x back to natural order
+  fast::G_passA<N, -1>(plane, N, cols, fa.pitch, threadIdx.x, blockDim.x);
+  __syncthreads();
   fast::lines_G<N, -1>(plane, fa.nxa, rows, 1, tw);       // along y on the needed rows
   for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) t[c] = plane[fa.col_off[c]];
 }
@@ -470,6 +536,60 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
     const double epi = sph * (1.0 + (e.Z ? 1.0 : 0.0) + (e.T ? 1.0 : 0.0) + (e.Yprev ? 1.0 : 0.0)) +
                        (e.Zhi ? (double)ctx->npw * nbc * 8.0 : 0.0);
     CHEBFI_LAUNCH_W("k_zfwd", st, col + epi, k_zfwd<R><<<gz, kThreads, zbytes, st>>>(T, sa, pz, K, e));
+  }
+}
+
+void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_t nb, double* gV, cudaStream_t st,
+                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb) {
+  const SphereFFT& s = ctx->sph;
+  const int n1 = s.n1, n2 = s.n2, n3 = s.n3;
+  const int64_t n = (int64_t)n1 * n2 * n3;
+  CHEBFI_CUDA(cudaMemsetAsync(gV, 0, sizeof(double) * n, st));
+  if (nb <= 0) return;
+  SphArgs sa;
+  sa.ncol = s.ncol;
+  sa.n3 = s.n3;
+  sa.zpitch = s.zpitch;
+  sa.ncolp = (s.ncol + 15) / 16 * 16;
+  sa.ldt = (int64_t)s.n3 * sa.ncolp;
+  sa.col_start = s.col_start.p;
+  sa.pw_line = s.pw_line.p;
+  sa.pw_zrev = s.pw_zrev.p;
+  PlaneArgs pa;
+  pa.n1 = n1;
+  pa.n2 = n2;
+  pa.n3 = n3;
+  pa.ncol = s.ncol;
+  pa.nxa = s.nxa;
+  pa.pitch = s.pitch;
+  pa.ldt = sa.ldt;
+  pa.ncolp = sa.ncolp;
+  pa.col_off = s.col_off.p;
+  pa.row_off = s.rows_act.p;
+  const FFTPlan<double> px = ctx->ax[0].plan<double>(), py = ctx->ax[1].plan<double>(), pz = ctx->ax[2].plan<double>();
+  const size_t zbytes = (size_t)kCB * s.zpitch * sizeof(double2);
+  const size_t pbytes = (size_t)n1 * s.pitch * sizeof(double2);
+  CHEBFI_REQUIRE(pbytes <= 227 * 1024, CHEBFI_ERR_ARG, "FFT plane does not fit in shared memory");
+  set_smem<double>((const void*)k_zinv<double>, zbytes);
+  set_smem<double>((const void*)k_plane_real<double>, pbytes);
+  // bands per chunk: two full grids per band, at most ~512 MB of grids
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nb, ((int64_t)1 << 25) / n));
+  T.alloc((size_t)sa.ldt * chunk);
+  Rb.alloc((size_t)n * chunk);
+  Gb.alloc((size_t)n * chunk);
+  for (int64_t b0 = 0; b0 < nb; b0 += chunk) {
+    const int nbc = (int)std::min<int64_t>(chunk, nb - b0);
+    dim3 gz((s.ncol + kCB - 1) / kCB, nbc);
+    for (int which = 0; which < 2; ++which) {
+      const double2* src = (which == 0 ? Ys : Gs) + b0 * ctx->npw;
+      double2* dst = which == 0 ? Rb.p : Gb.p;
+      CHEBFI_LAUNCH("k_zinv", st, k_zinv<double><<<gz, kThreads, zbytes, st>>>(src, ctx->npw, T.p, sa, pz));
+      CHEBFI_LAUNCH("k_plane_real", st,
+                    k_plane_real<double><<<dim3(n3, nbc), kThreads, pbytes, st>>>(T.p, pa, px, py, dst));
+    }
+    CHEBFI_LAUNCH("k_density_accum", st,
+                  k_density_accum<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n1, n2, n3, nbc, Rb.p, Gb.p,
+                                                                                    1.0 / (double)n, gV));
   }
 }
 

@@ -25,8 +25,9 @@ template <typename R, bool CA, bool CB>
 __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, R alpha, const cplx<R>* __restrict__ A,
                                               int64_t lda, const cplx<R>* __restrict__ B, int64_t ldb, R beta,
                                               cplx<R>* __restrict__ Cm, int64_t ldc, int64_t kchunk,
-                                              cplx<R>* __restrict__ ws) {
+                                              cplx<R>* __restrict__ ws, int lower) {
   using C = cplx<R>;
+  if (lower && blockIdx.x < blockIdx.y) return;  // tile strictly above the diagonal
   __shared__ C As[BK][BM + 1];
   __shared__ C Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -129,7 +130,7 @@ __global__ void k_splitk_reduce(int64_t M, int64_t N, int splits, const cplx<R>*
 template <typename R, bool CA, bool CB>
 void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int64_t lda, const cplx<R>* B,
             int64_t ldb, double beta, cplx<R>* Cm, int64_t ldc, cudaStream_t st, DevBuf<cplx<R>>* ws,
-            const char* tag) {
+            const char* tag, bool lower) {
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   int splits = 1;
   const int64_t tiles = tm * tn;
@@ -148,7 +149,10 @@ void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int
     wsp = ws->p;
   }
   dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)splits);
-  CHEBFI_LAUNCH_W(tag, st, 8.0 * (double)M * (double)N * (double)K, k_gemm<R, CA, CB><<<grid, 256, 0, st>>>(M, N, K, (R)alpha, A, lda, B, ldb, (R)beta, Cm, ldc, kchunk, wsp));
+  const double tiles_done = lower ? (double)(tm * (tm + 1) / 2) / (double)(tm * tn) : 1.0;
+  CHEBFI_LAUNCH_W(tag, st, 8.0 * (double)M * (double)N * (double)K * tiles_done,
+                  k_gemm<R, CA, CB><<<grid, 256, 0, st>>>(M, N, K, (R)alpha, A, lda, B, ldb, (R)beta, Cm, ldc, kchunk,
+                                                          wsp, lower ? 1 : 0));
   if (splits > 1) {
     const int64_t tot = M * N;
     CHEBFI_LAUNCH("k_splitk_reduce", st, k_splitk_reduce<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, wsp, (R)beta, Cm, ldc));
@@ -160,17 +164,18 @@ void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int
 template <typename R>
 void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int64_t lda,
           const cplx<R>* B, int64_t ldb, double beta, cplx<R>* C, int64_t ldc, cudaStream_t st,
-          DevBuf<cplx<R>>* ws, const char* tag) {
+          DevBuf<cplx<R>>* ws, const char* tag, bool lower) {
   if (M <= 0 || N <= 0) return;
-  if (conjA && conjB) launch<R, true, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
-  else if (conjA) launch<R, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
-  else if (conjB) launch<R, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
-  else launch<R, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag);
+  CHEBFI_REQUIRE(!lower || M == N, CHEBFI_ERR_ARG, "lower-triangle GEMM needs a square result");
+  if (conjA && conjB) launch<R, true, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag, lower);
+  else if (conjA) launch<R, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag, lower);
+  else if (conjB) launch<R, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag, lower);
+  else launch<R, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag, lower);
 }
 
 template void gemm<double>(bool, bool, int64_t, int64_t, int64_t, double, const double2*, int64_t, const double2*,
-                           int64_t, double, double2*, int64_t, cudaStream_t, DevBuf<double2>*, const char*);
+                           int64_t, double, double2*, int64_t, cudaStream_t, DevBuf<double2>*, const char*, bool);
 template void gemm<float>(bool, bool, int64_t, int64_t, int64_t, double, const float2*, int64_t, const float2*,
-                          int64_t, double, float2*, int64_t, cudaStream_t, DevBuf<float2>*, const char*);
+                          int64_t, double, float2*, int64_t, cudaStream_t, DevBuf<float2>*, const char*, bool);
 
 }  // namespace chebfi

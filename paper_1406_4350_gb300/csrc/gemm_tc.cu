@@ -12,7 +12,8 @@
 // GEMMs whose A matrices (built once from P at setup) hold the 2 x 2 blocks
 // [[Re, Im], [-Im, Re]] and [[Re, -Im], [Im, Re]].
 //
-// One CTA computes one 128 x 128 tile: warp 0 issues the TMA loads (128-byte swizzle,
+// Persistent kernel, one CTA per SM looping over 128 x 128 tiles: warp 0 issues the TMA
+// loads (128-byte swizzle,
 // three-stage mbarrier ring), warp 1 allocates 256 TMEM columns and issues the MMAs
 // (tcgen05.mma cta_group::1 kind::f16, M = 128, N = 128, K = 16), warps 2-5 read the
 // accumulator with tcgen05.ld.  The long contractions of the projector products (K up to
@@ -173,9 +174,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
   const int num_k = (args.K + BK - 1) / BK;
   const int num_chunks = (num_k + CHUNK - 1) / CHUNK;
+  const int tiles_n = (args.N + BN - 1) / BN;
+  const int tiles = tiles_n * ((args.M + BM - 1) / BM);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -199,99 +201,116 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // Persistent: CTA b takes tiles b, b + gridDim.x, ...; tiles are numbered n-fastest so
+  // the CTAs running together share rows of A (L2 reuse).  The k-tile and chunk counters
+  // run on across tiles and give the ring slots and the mbarrier phases.
   if (warp == 0) {
     if (lane == 0) {
-      for (int kt = 0; kt < num_k; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t par = (kt / STAGES) & 1;
-        if (kt >= STAGES && !mbar_wait(&empty[s], par ^ 1)) {
-          flag(args.status, CHEBFI_ERR_CUDA);
-          break;
+      int g = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int n0 = (tile % tiles_n) * BN, m0 = (tile / tiles_n) * BM;
+        for (int kt = 0; kt < num_k; ++kt, ++g) {
+          const int s = g % STAGES;
+          const uint32_t par = (g / STAGES) & 1;
+          if (g >= STAGES && !mbar_wait(&empty[s], par ^ 1)) {
+            flag(args.status, CHEBFI_ERR_CUDA);
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          const int x = kt * BK;
+          tma_load_2d(st, &tmAh, x, m0, &full[s]);
+          tma_load_2d(st + A_BYTES, &tmAl, x, m0, &full[s]);
+          tma_load_2d(st + 2 * A_BYTES, &tmBh, x, n0, &full[s]);
+          tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmBl, x, n0, &full[s]);
         }
-        uint8_t* st = smem + s * STAGE_BYTES;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        const int x = kt * BK;
-        tma_load_2d(st, &tmAh, x, m0, &full[s]);
-        tma_load_2d(st + A_BYTES, &tmAl, x, m0, &full[s]);
-        tma_load_2d(st + 2 * A_BYTES, &tmBh, x, n0, &full[s]);
-        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmBl, x, n0, &full[s]);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
       bool ok = true;
-      int kt = 0;
-      for (int ch = 0; ch < num_chunks && ok; ++ch) {
-        const int acc = ch & 1;
-        if (ch >= 2 && !mbar_wait(&acc_empty[acc], ((ch >> 1) - 1) & 1)) {
-          flag(args.status, CHEBFI_ERR_CUDA);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * BN);
-        const int kend = min(num_k, (ch + 1) * CHUNK);
-        for (; kt < kend; ++kt) {
-          const int s = kt % STAGES;
-          const uint32_t par = (kt / STAGES) & 1;
-          if (!mbar_wait(&full[s], par)) {
+      int g = 0, gch = 0;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        int kt = 0;
+        for (int ch = 0; ch < num_chunks && ok; ++ch, ++gch) {
+          const int acc = gch & 1;
+          if (gch >= 2 && !mbar_wait(&acc_empty[acc], ((gch >> 1) - 1) & 1)) {
             flag(args.status, CHEBFI_ERR_CUDA);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-          const bool first = kt == ch * CHUNK;
+          const uint32_t d = tmem + (uint32_t)(acc * BN);
+          const int kend = min(num_k, (ch + 1) * CHUNK);
+          for (; kt < kend; ++kt, ++g) {
+            const int s = g % STAGES;
+            const uint32_t par = (g / STAGES) & 1;
+            if (!mbar_wait(&full[s], par)) {
+              flag(args.status, CHEBFI_ERR_CUDA);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+            const bool first = kt == ch * CHUNK;
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t off = kk * 32;  // 16 bf16 along K
-            const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + A_BYTES + off);
-            const uint64_t bh = sw128_desc(base + 2 * A_BYTES + off),
-                           bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + off);
-            mma_bf16(d, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
-            mma_bf16(d, ah, bl, idesc, 1);
-            mma_bf16(d, al, bh, idesc, 1);
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t off = kk * 32;  // 16 bf16 along K
+              const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + A_BYTES + off);
+              const uint64_t bh = sw128_desc(base + 2 * A_BYTES + off),
+                             bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + off);
+              mma_bf16(d, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
+              mma_bf16(d, ah, bl, idesc, 1);
+              mma_bf16(d, al, bh, idesc, 1);
+            }
+            mma_commit(&empty[s]);
           }
-          mma_commit(&empty[s]);
+          mma_commit(&acc_full[acc]);
         }
-        mma_commit(&acc_full[acc]);
       }
     }
   } else {
     // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31, i.e. tile rows
     const int lane_base = 32 * (warp % 4);
-    const int m = m0 + lane_base + lane;
-    float racc[BN];
-#pragma unroll
-    for (int j = 0; j < BN; ++j) racc[j] = 0.f;
     bool ok = true;
-    for (int ch = 0; ch < num_chunks; ++ch) {
-      const int acc = ch & 1;
-      if (!mbar_wait(&acc_full[acc], (ch >> 1) & 1)) {
-        flag(args.status, CHEBFI_ERR_CUDA);
-        ok = false;
-        break;
+    int gch = 0;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      const int n0 = (tile % tiles_n) * BN, m0 = (tile / tiles_n) * BM;
+      const int m = m0 + lane_base + lane;
+      float racc[BN];
+#pragma unroll
+      for (int j = 0; j < BN; ++j) racc[j] = 0.f;
+      for (int ch = 0; ch < num_chunks; ++ch, ++gch) {
+        const int acc = gch & 1;
+        if (!mbar_wait(&acc_full[acc], (gch >> 1) & 1)) {
+          flag(args.status, CHEBFI_ERR_CUDA);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < BN; c += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(acc * BN + c), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) racc[c + j] += v[j];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[acc]);
       }
-      tc_fence_after();
+      if (ok && m < args.M) {
 #pragma unroll
-      for (int c = 0; c < BN; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(acc * BN + c), v);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) racc[c + j] += v[j];
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[acc]);
-    }
-    if (ok && m < args.M) {
-#pragma unroll
-      for (int j = 0; j < BN; ++j) {
-        const int n = n0 + j;
-        if (n < args.N) {
-          float o = args.alpha * racc[j];
-          if (args.beta != 0.f) o = fmaf(args.beta, args.C[(int64_t)m + (int64_t)n * args.ldc], o);
-          args.D[(int64_t)m + (int64_t)n * args.ldd] = o;
+        for (int j = 0; j < BN; ++j) {
+          const int n = n0 + j;
+          if (n < args.N) {
+            float o = args.alpha * racc[j];
+            if (args.beta != 0.f) o = fmaf(args.beta, args.C[(int64_t)m + (int64_t)n * args.ldc], o);
+            args.D[(int64_t)m + (int64_t)n * args.ldd] = o;
+          }
         }
       }
     }
@@ -362,8 +381,16 @@ void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64
   a.ldc = ldc;
   a.status = status;
   CHEBFI_CUDA(cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-  dim3 grid((unsigned)((N + tc::BN - 1) / tc::BN), (unsigned)((M + tc::BM - 1) / tc::BM));
-  CHEBFI_REQUIRE(grid.y <= 65535, CHEBFI_ERR_ARG, "GEMM M too large");
+  // persistent grid: one CTA per SM (the shared-memory ring admits one per SM)
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CHEBFI_CUDA(cudaGetDevice(&dev));
+    CHEBFI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t tiles = ((N + tc::BN - 1) / tc::BN) * ((M + tc::BM - 1) / tc::BM);
+  CHEBFI_REQUIRE(tiles < (1ll << 31), CHEBFI_ERR_ARG, "GEMM too large");
+  dim3 grid((unsigned)std::min<int64_t>(tiles, sms));
   CHEBFI_LAUNCH_W(tag, st, 2.0 * (double)M * (double)N * (double)K, tc::k_tc_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(ah, al, bh, bl, a));
 }
 

@@ -27,6 +27,14 @@ template <typename R> struct LocalEpi {
   R a = 0, c = 0, bprev = 0, inv_n3 = 0;
 };
 size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb);
+// Derivative of (V_loc psi) with respect to V_loc for a real loss whose gradient at the
+// output is g: gV(x, y, z) = (1/N^3) sum_b Re(conj(g_b(r)) psi_b(r)) with psi_b, g_b the
+// real-space values of sorted-order sphere blocks Ys, Gs (ld = npw).  FP64.
+void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_t nb, double* gV, cudaStream_t st,
+                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb);
+// gD[entry (i, j) of atom block a] = sum_b Re(conj(q_ib) p_jb)
+void block_outer_grad(const chebfi_ctx* ctx, const double2* q, const double2* p, int64_t ldp, int64_t nb, double* gD,
+                      cudaStream_t st);
 // the two-pass FFT kernels cover cubic grids of a few compiled sizes; split_index(n, p) is
 // the natural index held at position p of their split order
 bool fast_fft_supported(int n1, int n2, int n3);
@@ -38,11 +46,12 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
 // ---------------------------------------------------------------- complex GEMM (gemm.cu)
 // C = alpha op(A) op(B) + beta C, op = identity or conjugate transpose; real alpha, beta.
 // M x N result, inner dimension K.  ws: optional split-K workspace (nullptr = no split).
-// tag: the name the launch is timed under when profiling is on.
+// tag: the name the launch is timed under when profiling is on.  lower: square result,
+// only tiles touching the lower triangle are computed (the rest of C is left undefined).
 template <typename R>
 void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A,
           int64_t lda, const cplx<R>* B, int64_t ldb, double beta, cplx<R>* C, int64_t ldc, cudaStream_t st,
-          DevBuf<cplx<R>>* ws = nullptr, const char* tag = "k_gemm");
+          DevBuf<cplx<R>>* ws = nullptr, const char* tag = "k_gemm", bool lower = false);
 
 // ---------------------------------------------------------------- tensor cores (gemm_tc.cu)
 // D (M x N, FP32 column-major) = alpha A B + beta C with A (M x K) and B (K x N) K-major
@@ -94,6 +103,8 @@ void scale_sym(int64_t n, double2* A, int64_t lda, const double* d, cudaStream_t
 void scale_rows(int64_t n, int64_t m, double2* X, int64_t ldx, const double* d, cudaStream_t st);
 // A <- (A + A^H) / 2
 void hermitize(int64_t n, double2* A, int64_t lda, cudaStream_t st);
+// upper triangle <- conjugate of the lower triangle, diagonal made real
+void mirror_lower(int64_t n, double2* A, int64_t lda, cudaStream_t st);
 // max over an array (device scalar out)
 void reduce_max(int64_t n, const double* x, double* out, cudaStream_t st);
 // y = D x for a real matrix D (n x n) applied to complex block x: used for Q p
