@@ -214,6 +214,10 @@ CONFIGS = {
                   degree=10, sweeps=8, seed=1002),
     "paw96": dict(L=40.0, grid=96, ecut=7.275, natoms=256, nlmn=8, nbands=2048, paw=True,
                   degree=4, sweeps=4, seed=1003),
+    # same spacing and atom density at 72^3: a mid-size case for detailed profiles whose
+    # wavefunction block (512 bands) still exceeds the L2 cache
+    "paw72": dict(L=30.0, grid=72, ecut=7.275, natoms=108, nlmn=8, nbands=512, paw=True,
+                  degree=4, sweeps=4, seed=1006),
 }
 
 
