@@ -303,15 +303,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) mbar_arrive(&acc_empty[acc]);
       }
       if (ok && m < args.M) {
+        // C may be D itself: read every C value of the row first (no store in between, so
+        // the loads can all be in flight together), then store
+        const int nvalid = min(BN, args.N - n0);
+        if (args.beta != 0.f) {
+          const float* c = args.C + (int64_t)m + (int64_t)n0 * args.ldc;
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
-          const int n = n0 + j;
-          if (n < args.N) {
-            float o = args.alpha * racc[j];
-            if (args.beta != 0.f) o = fmaf(args.beta, args.C[(int64_t)m + (int64_t)n * args.ldc], o);
-            args.D[(int64_t)m + (int64_t)n * args.ldd] = o;
-          }
+          for (int j = 0; j < BN; ++j)
+            if (j < nvalid) racc[j] = fmaf(args.beta, c[(int64_t)j * args.ldc], args.alpha * racc[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < BN; ++j) racc[j] *= args.alpha;
         }
+        float* d = args.D + (int64_t)m + (int64_t)n0 * args.ldd;
+#pragma unroll
+        for (int j = 0; j < BN; ++j)
+          if (j < nvalid) d[(int64_t)j * args.ldd] = racc[j];
       }
     }
   }
