@@ -332,3 +332,25 @@ def test_pins_catch_planted_mistakes(monkeypatch, mutation, pins):
     for pin in pins:
         with pytest.raises(AssertionError):
             pin()
+
+
+def test_woodbury_iterative_refinement_reaches_the_direct_solve():
+    """Section 4.1's solve of the reduced system by block-diagonally preconditioned
+    iterative refinement converges to the direct Woodbury result (and hence to S^{-1} x)."""
+    cell = _tiny(N=12, natoms=3)
+    op = pw.PWOperator.from_cell(cell)
+    rng = np.random.default_rng(12)
+    x = rng.normal(size=(cell.npw, 3)) + 1j * rng.normal(size=(cell.npw, 3))
+    y, its = op.apply_Sinv_refined(x, tol=1e-14)
+    assert 1 <= its < 200
+    np.testing.assert_allclose(y, op.apply_Sinv(x), atol=1e-12)
+    np.testing.assert_allclose(op.apply_S(y), x, atol=1e-11)
+    # the update count follows the contraction factor: the residual shrinks by about rho
+    # per update, so reaching 1e-14 takes about log(1e-14)/log(rho) updates
+    rho, kappa = op.refinement_diagnostics()
+    assert 0.0 < rho < 1.0 and kappa >= 1.0
+    assert its <= np.ceil(np.log(1e-14) / np.log(rho)) + 8
+    # a tolerance of 1 is met before any update; maxit = 0 makes no update either
+    assert op.apply_Sinv_refined(x, tol=1.0)[1] == 0
+    y0, its0 = op.apply_Sinv_refined(x, tol=1e-14, maxit=0)
+    assert its0 == 0 and np.allclose(y0, x)
