@@ -34,6 +34,27 @@ WORKLOAD = "paw96"
 DEGREE = 4
 
 
+def _traffic(tag: str):
+    """DRAM bytes per launch of a kernel at the benchmark workload, from the ncu capture
+    recorded in profiles/traffic_paw96.md, or None when the kernel's source has changed
+    since (the record names the file and its SHA-1) or there is no record."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_paw96.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if not line.startswith("traffic:"):
+            continue
+        f = dict(kv.split("=", 1) for kv in line.split()[1:])
+        if f.get("tag") != tag:
+            continue
+        src = os.path.join(ROOT, f["file"])
+        if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != f["sha1"]:
+            return None
+        return float(f["bytes_per_launch"])
+    return None
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -156,6 +177,78 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ extra measurements
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        fn()
+    b_.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b_) / steps
+
+
+def run_extra(args):
+    """backward: the filter backward (gY0, gV, gD) at the differentiation workload (48^3 grid,
+    8025 plane waves, 32 atoms x 8 projectors, PAW, 128 bands, degree 8), FP64 and FP32 forms;
+    unit = band-steps of the adjoint recurrence per second (bands x degree / time).
+    refine: S^{-1} by Section 4.1's iterative refinement against the direct Woodbury form on
+    the benchmark workload's first 256 bands."""
+    import numpy as np
+    import torch
+    from paper_1406_4350_gb300 import build as b
+    from paper_1406_4350_gb300 import F32, F64, BOUND_RIGOROUS
+    from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    from synth import config_cell
+    b.build()
+    torch.cuda.set_device(0)
+    if args.task == "backward":
+        cell = config_cell("paw48", nbands=128)
+        deg = 8
+        g = ChebFI.from_cell(cell)
+        hi = g.upper_bound(BOUND_RIGOROUS)
+        Y = fortran(cell.Y0)
+        lo = float(g.rayleigh_quotients(Y).max().item())
+        rng = np.random.default_rng(8)
+        W = fortran(rng.normal(size=cell.Y0.shape) + 1j * rng.normal(size=cell.Y0.shape))
+        out = {}
+        for name, p in (("f64", F64), ("f32", F32)):
+            with Clocks(0) as clk:
+                ms = _timed(lambda: g.cheb_filter_backward(Y, W, deg, lo, hi, cell.vloc.shape, cell.D.size, prec=p),
+                            args.steps, args.warmup)
+                fwd = _timed(lambda: g.cheb_filter(Y.clone(), deg, lo, hi, prec=p), args.steps, args.warmup)
+            out[name] = {"value": cell.nbands * deg / (ms / 1e3), "ms_backward": ms, "ms_forward": fwd,
+                         "backward_over_forward": ms / fwd, "clocks": clk.summary()}
+        line = {"metric": "filter backward band-steps/s (gY0, gV, gD)", "unit": "band-steps/s",
+                "value": out["f64"]["value"], "dtype": "f64", "steps": args.steps, "warmup": args.warmup,
+                "config": {"workload": "paw48: 48^3 grid, %d plane waves, %d bands, %d projectors, PAW, degree %d, "
+                                       "checkpoints every ceil(sqrt(degree))" % (cell.npw, cell.nbands, cell.nproj, deg)},
+                "forms": out}
+    else:
+        cell = config_cell(WORKLOAD, nbands=256)
+        g = ChebFI.from_cell(cell)
+        X = fortran(cell.Y0)
+        res = {}
+        ms_direct = _timed(lambda: g.apply_Sinv(X), args.steps, args.warmup)
+        its = []
+        ms_ref = _timed(lambda: its.append(g.apply_Sinv_refined(X, tol=1e-12)[1]), args.steps, args.warmup)
+        a = g.apply_Sinv(X)
+        r, _ = g.apply_Sinv_refined(X, tol=1e-12)
+        diff = float((a - r).abs().max().item() / X.abs().max().item())
+        line = {"metric": "S^-1 application time, refinement vs direct Woodbury", "unit": "ms",
+                "value": ms_ref, "dtype": "f64", "steps": args.steps, "warmup": args.warmup,
+                "config": {"workload": "paw96: 96^3 grid, %d plane waves, 256 bands, %d projectors, PAW, tol 1e-12"
+                                       % (cell.npw, cell.nproj)},
+                "ms_direct": ms_direct, "iterations": its[-1], "max_rel_diff": diff}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ native arm
 def main():
     ap = argparse.ArgumentParser()
@@ -163,15 +256,20 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--prec", default="f32", choices=["mixed", "f32", "f64"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "f32", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64-form filter calls (0: skip)")
     ap.add_argument("--cpu-bands", type=int, default=16, help="bands in the oracle's timed CPU sample")
     ap.add_argument("--ref-bands", type=int, default=4)
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
+    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine"],
+                    help="filter: the benchmark; backward / refine: the differentiation and the "
+                         "refinement-Woodbury measurements (their own JSON line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.task != "filter":
+        return run_extra(args)
 
     import numpy as np
     import torch
@@ -317,8 +415,9 @@ def main():
             peak, bound, unit, src = peaks.get("hbm_gbs", 6762.3), "hbm", "GB/s", "hbm_gbs (measured)"
         scale = 1e12 if unit == "TFLOP/s" else 1e9
         achieved = work / cnt / avg_s / scale
+        traffic = _traffic(name) if (args.workload == WORKLOAD and args.nbands is None) else None
         return {"bound": bound, "kernel": name, "phase": phase, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
+                "frac": achieved / peak, "traffic": traffic, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
                 "launches_per_step": cnt / args.steps, "work_per_launch": work / cnt}
 
     allk = [(v[0], ph, k) for ph in prof_acc for k, v in prof_acc[ph].items()]

@@ -130,10 +130,39 @@ int chebfi_set_D(chebfi_ctx* ctx, const double* D, int on_device);
 int chebfi_apply_H_backward(chebfi_ctx* ctx, const void* Y, const void* G, void* gY, double* gV, double* gD,
                             int64_t nb, int64_t ld, void* stream);
 
+/* Backward of chebfi_cheb_filter (Algorithm 2's inner loop) for a real loss L of its output
+ * Y_n, given gYn = dL/dY_n in PyTorch's convention (dL = Re sum conj(gYn) dY_n).  The adjoint
+ * recurrence L_k = a_k (H S^{-1} L_{k+1} - c L_{k+1}) - L_{k+2} (a_0 = 1/r, a_k = 2/r,
+ * L_n = gYn, L_{n+1} = 0) gives gY0 = L_0; V_loc and D enter only through H, so
+ *   gV(r) = sum_k a_k (1/N^3) Re sum_b conj(u_kb(r)) y_kb(r),   u_k = S^{-1} L_{k+1},
+ *   gD_ij = sum_k a_k Re sum_b conj((P^H u_k)_ib) (P^H Y_k)_jb   (atom blocks),
+ * for the same c, r, lambda_lo, lambda_hi and degree as the forward call.  The iterates Y_k
+ * are recomputed from checkpoints (Y_{j-1}, Y_j) kept every checkpoint_every steps
+ * (0: ceil(sqrt(degree))), so device memory is O(degree / s + s) blocks of npw x nb.
+ * Y0, gYn: device complex128 blocks like chebfi_apply_H's Y (same nb, ld).  gY0 (like Y0),
+ * gV (N1*N2*N3 doubles, z fastest) and gD (packed like D) are device outputs, each NULL to
+ * skip; gV and gD are overwritten.  prec: CHEBFI_F64, or CHEBFI_F32 (iterates and operators
+ * in FP32, gradient sums in FP64); CHEBFI_MIXED is rejected with CHEBFI_ERR_ARG.  The V_loc
+ * and D of the context are the point of differentiation. */
+int chebfi_cheb_filter_backward(chebfi_ctx* ctx, const void* Y0, const void* gYn, void* gY0, double* gV,
+                                double* gD, int64_t nb, int64_t ld, int degree, double lambda_lo,
+                                double lambda_hi, int prec, int checkpoint_every, void* stream);
+
 /* Algorithm 1: SY = S Y = Y + P Q P^H Y (FP64). */
 int chebfi_apply_S(chebfi_ctx* ctx, const void* Y, void* SY, int64_t nb, int64_t ld, void* stream);
 /* Section 4.1 (Woodbury): out = S^{-1} X = X - P M P^H X (FP64). */
 int chebfi_apply_Sinv(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int64_t ld, void* stream);
+
+/* Section 4.1's own solve of the Woodbury reduced system (FP64): out = S^{-1} X = X - P q with
+ * A q = P^H X, A = D_S^{-1} + P^H P, found by iterative refinement q <- q + B^{-1}(P^H X - A q)
+ * from q = 0, B = the atom-diagonal blocks of A.  It stops when every column has
+ * ||P^H x - A q|| <= tol ||P^H x||, or after maxit updates; *iterations (nullable) receives the
+ * number of updates.  Needs every D_S block invertible (CHEBFI_ERR_ARG otherwise; the direct
+ * chebfi_apply_Sinv has no such limit).  Returns CHEBFI_ERR_NO_CONVERGENCE, with out written,
+ * when the tolerance is not met.  A and B^{-1} are formed on the first call.  S = I: out = X.
+ * Synchronises. */
+int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int64_t ld, double tol,
+                              int maxit, int* iterations, void* stream);
 
 /* Algorithm 2's inner loop, in place on Y: psi^1 = (S^{-1}H psi^0 - c psi^0)/r,
  * psi^i = 2/r (S^{-1}H psi^{i-1} - c psi^{i-1}) - psi^{i-2}, i = 2..degree, with

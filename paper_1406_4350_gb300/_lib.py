@@ -40,6 +40,10 @@ SIGNATURES = {
     "chebfi_set_D": (c_int, [c_void_p, c_void_p, c_int]),
     "chebfi_apply_H_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
                                         c_int64, c_void_p]),
+    "chebfi_apply_Sinv_refined": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_double, c_int,
+                                          c_void_p, c_void_p]),
+    "chebfi_cheb_filter_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
+                                            c_int64, c_int, c_double, c_double, c_int, c_int, c_void_p]),
     "chebfi_apply_S": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_apply_Sinv": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_cheb_filter": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_double, c_double,

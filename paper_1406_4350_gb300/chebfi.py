@@ -176,6 +176,28 @@ class ChebFI:
         self._check(self.lib.chebfi_apply_H_backward(self.h, y, g, ptr(gY), ptr(gV), ptr(gD), nb, ld, _stream()))
         return gY, gV, gD
 
+    def cheb_filter_backward(self, Y0, gYn, degree: int, lambda_lo: float, lambda_hi: float, grid, nD,
+                             prec: int = F64, checkpoint_every: int = 0, want_Y=True, want_V=True, want_D=True):
+        """Gradients of a real loss through the filter Y_n = cheb_filter(Y0) given gYn = dL/dY_n
+        (PyTorch convention): returns (gY0, gV on the grid, gD packed like D); entries not
+        wanted are None.  The iterates are recomputed from checkpoints every
+        ``checkpoint_every`` steps (0: ceil(sqrt(degree)))."""
+        y, nb, ld = _block(Y0)
+        g, nbg, ldg = _block(gYn)
+        if nbg != nb or ldg != ld:
+            raise ValueError("Y0 and gYn must have the same shape and leading dimension")
+        gY = None
+        if want_Y:
+            gY = self._out_like(Y0)
+            if _block(gY)[2] != ld:
+                gY = torch.empty((nb, ld), dtype=torch.complex128, device=Y0.device).T[: Y0.shape[0]]
+        gV = torch.empty(tuple(int(x) for x in grid), dtype=torch.float64, device=Y0.device) if want_V else None
+        gD = torch.empty(int(nD), dtype=torch.float64, device=Y0.device) if want_D else None
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self.lib.chebfi_cheb_filter_backward(self.h, y, g, ptr(gY), ptr(gV), ptr(gD), nb, ld, degree,
+                                                         lambda_lo, lambda_hi, prec, checkpoint_every, _stream()))
+        return gY, gV, gD
+
     def apply_S(self, Y, out=None):
         out = self._out_like(Y) if out is None else out
         y, nb, ld = _block(Y)
@@ -189,6 +211,17 @@ class ChebFI:
         o, _, _ = _block(out)
         self._check(self.lib.chebfi_apply_Sinv(self.h, x, o, nb, ld, _stream()))
         return out
+
+    def apply_Sinv_refined(self, X, tol: float = 1e-12, maxit: int = 200, out=None):
+        """S^{-1} X with the Woodbury reduced system solved by preconditioned iterative
+        refinement; returns (out, iterations)."""
+        out = self._out_like(X) if out is None else out
+        x, nb, ld = _block(X)
+        o, _, _ = _block(out)
+        its = ctypes.c_int(0)
+        self._check(self.lib.chebfi_apply_Sinv_refined(self.h, x, o, nb, ld, tol, maxit, ctypes.byref(its),
+                                                       _stream()))
+        return out, its.value
 
     def cheb_filter(self, Y, degree: int, lambda_lo: float, lambda_hi: float, prec: int = F64):
         """In place on Y; returns Y."""

@@ -11,6 +11,7 @@
 #include <numeric>
 #include <stdexcept>
 #include <vector>
+#include <complex>
 
 #include "internal.cuh"
 #include "kernels.cuh"
@@ -143,6 +144,10 @@ template <> struct Ops<double> {
   static const double2* M(const chebfi_ctx* c) { return c->d_M.p; }
   static const double* D(const chebfi_ctx* c) { return c->d_Dblk.p; }
   static DevBuf<double2>* ws(chebfi_ctx* c) { return &c->w.splitk; }
+  static DevBuf<double2>& pool(chebfi_ctx* c) { return c->w.gpool; }
+  static DevBuf<double2>& T(chebfi_ctx* c) { return c->w.T1; }
+  static DevBuf<double2>& pa(chebfi_ctx* c) { return c->w.pz; }
+  static DevBuf<double2>& pb(chebfi_ctx* c) { return c->w.pw; }
 };
 template <> struct Ops<float> {
   static const float2* P(const chebfi_ctx* c) { return c->d_Pf.p; }
@@ -150,6 +155,10 @@ template <> struct Ops<float> {
   static const float2* M(const chebfi_ctx* c) { return c->d_Mf.p; }
   static const float* D(const chebfi_ctx* c) { return c->d_Dblkf.p; }
   static DevBuf<float2>* ws(chebfi_ctx* c) { return &c->w.fsplitk; }
+  static DevBuf<float2>& pool(chebfi_ctx* c) { return c->w.fgpool; }
+  static DevBuf<float2>& T(chebfi_ctx* c) { return c->w.fT1; }
+  static DevBuf<float2>& pa(chebfi_ctx* c) { return c->w.fpz; }
+  static DevBuf<float2>& pb(chebfi_ctx* c) { return c->w.fpw; }
 };
 
 // H Y (FP64 or FP32) with the projections p = P^H Y returned; sorted order, ld = npw.
@@ -519,6 +528,255 @@ double rigorous_bound(chebfi_ctx* ctx) {
   return ctx->bound_rigorous;
 }
 
+
+// ---------------------------------------------------------------- Woodbury by refinement
+// Section 4.1 solves the reduced system A q = P^H x, A = D_S^{-1} + P^H P, by iterative
+// refinement preconditioned with the atom-diagonal blocks B of A:
+//   q <- q + B^{-1} (P^H x - A q),  starting from q = 0,
+// then S^{-1} x = x - P q.  A and B^{-1} are formed on first use.
+
+// In-place Gauss-Jordan inverse with partial pivoting of an n x n column-major matrix;
+// false if a pivot is zero or tiny relative to the largest entry.
+template <typename T> bool gj_inverse(int n, std::vector<T>& a) {
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  double amax = 0.0;
+  for (const T& v : a) amax = std::max(amax, (double)std::abs(v));
+  if (amax == 0.0) return false;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::abs(a[i + k * n]) > std::abs(a[piv + k * n])) piv = i;
+    if (std::abs(a[piv + k * n]) <= 1e-14 * amax) return false;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) std::swap(a[k + j * n], a[piv + j * n]);
+      std::swap(perm[k], perm[piv]);
+    }
+    const T inv = T(1) / a[k + k * n];
+    a[k + k * n] = T(1);
+    for (int j = 0; j < n; ++j) a[k + j * n] *= inv;
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const T f = a[i + k * n];
+      if (f == T(0)) continue;
+      a[i + k * n] = T(0);
+      for (int j = 0; j < n; ++j) a[i + j * n] -= f * a[k + j * n];
+    }
+  }
+  // undo the row interchanges as column interchanges of the inverse
+  std::vector<T> out(a.size());
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) out[i + perm[j] * n] = a[i + j * n];
+  a.swap(out);
+  return true;
+}
+
+void ensure_refine(chebfi_ctx* ctx, cudaStream_t st) {
+  if (ctx->refine_ready) return;
+  const int64_t nq = ctx->nproj;
+  const int natoms = ctx->natoms;
+  std::vector<double> dinv(ctx->h_Qblk.size());
+  std::vector<int64_t> cblk(natoms);
+  int64_t off = 0, coff = 0;
+  for (int a = 0; a < natoms; ++a) {
+    const int o = ctx->offs[a], na = ctx->offs[a + 1] - o;
+    std::vector<double> blk(ctx->h_Qblk.begin() + off, ctx->h_Qblk.begin() + off + (int64_t)na * na);
+    CHEBFI_REQUIRE(gj_inverse(na, blk), CHEBFI_ERR_ARG,
+                   "the D_S (Q) block of atom " + std::to_string(a) +
+                       " is singular: the refinement needs D_S^{-1}; use chebfi_apply_Sinv");
+    // Q blocks are symmetric, so the row-major packing of the inverse equals its column-major one
+    std::copy(blk.begin(), blk.end(), dinv.begin() + off);
+    cblk[a] = coff;
+    off += (int64_t)na * na;
+    coff += (int64_t)na * na;
+  }
+  DevBuf<double> dd;
+  dd.upload(dinv.data(), dinv.size(), st);
+  ctx->d_Aref.alloc((size_t)nq * nq);
+  CHEBFI_LAUNCH("k_dense_from_blocks", st, k_dense_from_blocks<<<nblk(nq * nq), 256, 0, st>>>(nq, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p, dd.p, ctx->d_Aref.p));
+  axpby<double>(nq, nq, 1.0, ctx->d_G.p, nq, 1.0, ctx->d_Aref.p, nq, ctx->d_Aref.p, nq, st);
+  // B^{-1}: inverses of the atom-diagonal blocks of A = D_S^{-1} + G
+  std::vector<std::complex<double>> binv((size_t)coff);
+  for (int a = 0; a < natoms; ++a) {
+    const int o = ctx->offs[a], na = ctx->offs[a + 1] - o;
+    std::vector<std::complex<double>> blk((size_t)na * na);
+    CHEBFI_CUDA(cudaMemcpy2DAsync(blk.data(), sizeof(double2) * na, ctx->d_Aref.p + o + (int64_t)o * nq,
+                                  sizeof(double2) * nq, sizeof(double2) * na, na, cudaMemcpyDeviceToHost, st));
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+    CHEBFI_REQUIRE(gj_inverse(na, blk), CHEBFI_ERR_ARG,
+                   "the diagonal block of D_S^{-1} + P^H P of atom " + std::to_string(a) + " is singular");
+    std::copy(blk.begin(), blk.end(), binv.begin() + cblk[a]);
+  }
+  ctx->d_Binv.upload(reinterpret_cast<const double2*>(binv.data()), binv.size(), st);
+  ctx->d_cblk_off.upload(cblk.data(), cblk.size(), st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  ctx->refine_ready = true;
+}
+
+// ---------------------------------------------------------------- filter backward
+// The filter of Algorithm 2 is Y_{k+1} = a_k (A - c) Y_k - b_k Y_{k-1} with A = S^{-1} H,
+// a_0 = 1/r, a_k = 2/r, b_0 = 0, b_k = 1.  For a real loss L with G_n = dL/dY_n (PyTorch's
+// convention), the adjoint iterates L_k = dL/dY_k obey the same recurrence run backwards with
+// the adjoint operator A^H = H S^{-1} (H and S Hermitian):
+//   L_k = a_k (H S^{-1} L_{k+1} - c L_{k+1}) - L_{k+2},      L_{n+1} = 0,
+// and gY_0 = L_0.  Only the term a_k S^{-1} (dH) Y_k of dY_{k+1} depends on V_loc and D, so
+// their gradients are sums over k of the H-gradient of the pair (Y_k, a_k S^{-1} L_{k+1}),
+// the quantity chebfi_apply_H_backward computes for one pair.
+//
+// The iterates Y_k are needed in reverse order.  They are recomputed from checkpoints: a
+// first forward pass keeps (Y_{j-1}, Y_j) at j = 0, s, 2s, ...; each segment [j, j + s) is
+// then recomputed from its checkpoint when the backward sweep reaches it.  Memory is
+// 2 ceil(n/s) + s + 4 blocks (s = ceil(sqrt n) by default) instead of n + 4; the extra work
+// is at most n forward steps.
+
+// S^{-1} X (Section 4.1, Woodbury with the precomputed core M) into out; X itself when S = I.
+template <typename R>
+const cplx<R>* sinv_sorted(chebfi_ctx* ctx, const cplx<R>* X, cplx<R>* out, cplx<R>* pa, cplx<R>* pb, int64_t nb,
+                           cudaStream_t st) {
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  if (!ctx->paw) return X;
+  CHEBFI_CUDA(cudaMemcpyAsync(out, X, sizeof(cplx<R>) * npw * nb, cudaMemcpyDeviceToDevice, st));
+  gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, X, npw, 0.0, pa, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+  gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, pa, nq, 0.0, pb, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+  gemm<R>(false, false, npw, nb, nq, -1.0, Ops<R>::P(ctx), npw, pb, nq, 1.0, out, npw, st, Ops<R>::ws(ctx),
+          "gemm_grad");
+  return out;
+}
+
+template <typename R> struct StepBufs {
+  cplx<R>*HX, *U, *T, *pa, *pb;
+};
+
+// out = a (B X - c X) - bp Xprev with B = S^{-1} H (forward) or B = H S^{-1} (adjoint).
+// out may alias Xprev, not X.  Returns S^{-1} X in the adjoint case (the gradient partner).
+template <typename R>
+const cplx<R>* cheb_step(chebfi_ctx* ctx, bool adjoint, const cplx<R>* X, const cplx<R>* Xprev, cplx<R>* out, double a,
+                         double c, double bp, StepBufs<R> b, int64_t nb, cudaStream_t st) {
+  const int64_t npw = ctx->npw;
+  const cplx<R>* u;
+  const cplx<R>* sx = nullptr;
+  if (!adjoint) {
+    apply_H_sorted<R>(ctx, X, b.HX, b.pa, b.pb, b.T, nb, st, "gemm_grad");
+    u = sinv_sorted<R>(ctx, b.HX, b.U, b.pa, b.pb, nb, st);
+  } else {
+    sx = sinv_sorted<R>(ctx, X, b.U, b.pa, b.pb, nb, st);
+    apply_H_sorted<R>(ctx, sx, b.HX, b.pa, b.pb, b.T, nb, st, "gemm_grad");
+    u = b.HX;
+  }
+  cheb_combine<R>(npw, nb, (R)a, u, npw, (R)c, X, npw, (R)(Xprev ? bp : 0.0), Xprev, npw, out, npw, st);
+  return sx;
+}
+
+// gV += scale * dRe<G, H Y>/dV_loc and gD += scale * dRe<G, H Y>/dD for a sorted FP64 pair.
+void accumulate_pair(chebfi_ctx* ctx, const double2* Y, const double2* G, double scale, int64_t nb, double* gV,
+                     double* gD, cudaStream_t st) {
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  if (gD && nq > 0) {
+    w.pc.alloc((size_t)nq * nb);
+    w.pt.alloc((size_t)nq * nb);
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, G, npw, 0.0, w.pc.p, nq, st, &w.splitk, "gemm_grad");
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, Y, npw, 0.0, w.pt.p, nq, st, &w.splitk, "gemm_grad");
+    block_outer_grad(ctx, w.pc.p, w.pt.p, nq, nb, gD, st, scale, true);
+  }
+  if (gV) vloc_gradient(ctx, Y, G, nb, gV, st, w.T2, w.tmp, w.tmp2, scale, true);
+}
+
+void to_f64(const chebfi_ctx* ctx, const float2* x, double2* y, int64_t nb, cudaStream_t st) {
+  convert(ctx->npw, nb, x, ctx->npw, y, ctx->npw, st);
+}
+template <typename R> void from_f64(const chebfi_ctx* ctx, const double2* x, cplx<R>* y, int64_t nb, cudaStream_t st) {
+  if constexpr (sizeof(R) == 8) {
+    CHEBFI_CUDA(cudaMemcpyAsync(y, x, sizeof(double2) * ctx->npw * nb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    convert(ctx->npw, nb, x, ctx->npw, y, ctx->npw, st);
+  }
+}
+
+// Backward of the degree-n filter on sorted FP64 blocks: Y_0 in w.Ya, G_n in w.Yb; gY_0 is
+// left in w.Ya.  gV and gD (if not null) must be zeroed by the caller; they are accumulated.
+template <typename R>
+void filter_backward(chebfi_ctx* ctx, int64_t nb, int n, double lo, double hi, int s, double* gV, double* gD,
+                     cudaStream_t st) {
+  using C = cplx<R>;
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw;
+  const size_t blk = (size_t)npw * nb, np = (size_t)std::max<int64_t>(ctx->nproj, 1) * nb;
+  const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
+  const int nseg = (n + s - 1) / s, sl = std::max(s, 2);
+  const int nslots = 2 * nseg + sl + 4;
+  DevBuf<C>& pool = Ops<R>::pool(ctx);
+  pool.alloc(blk * nslots);
+  Ops<R>::T(ctx).alloc(local_workspace_elems(ctx, nb));
+  Ops<R>::pa(ctx).alloc(np);
+  Ops<R>::pb(ctx).alloc(np);
+  auto slot = [&](int i) { return pool.p + blk * i; };
+  auto ck = [&](int seg, int which) { return slot(2 * seg + which); };  // which 0: Y_{j-1}, 1: Y_j
+  C* segb = slot(2 * nseg);
+  C* lam1 = slot(2 * nseg + sl);
+  C* lam2 = slot(2 * nseg + sl + 1);
+  StepBufs<R> sb{slot(2 * nseg + sl + 2), slot(2 * nseg + sl + 3), Ops<R>::T(ctx).p, Ops<R>::pa(ctx).p,
+                 Ops<R>::pb(ctx).p};
+  auto alpha = [&](int k) { return (k == 0 ? 1.0 : 2.0) / r; };
+  const size_t bytes = sizeof(C) * blk;
+  if (sizeof(R) == 4) {
+    w.gA.alloc(blk);
+    w.gB.alloc(blk);
+  }
+  from_f64<R>(ctx, w.Ya.p, ck(0, 1), nb, st);
+  from_f64<R>(ctx, w.Yb.p, lam1, nb, st);
+  // forward pass: Y_1 .. Y_{n-1} in two rolling buffers, checkpoints at multiples of s
+  {
+    C* yk = segb;
+    C* ykm1 = nullptr;
+    CHEBFI_CUDA(cudaMemcpyAsync(yk, ck(0, 1), bytes, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k + 1 < n; ++k) {
+      C* out = ykm1 ? ykm1 : segb + blk;  // Y_{k+1} over Y_{k-1}
+      cheb_step<R>(ctx, false, yk, ykm1, out, alpha(k), c, 1.0, sb, nb, st);
+      ykm1 = yk;
+      yk = out;
+      const int j = k + 1;
+      if (j % s == 0) {
+        CHEBFI_CUDA(cudaMemcpyAsync(ck(j / s, 0), ykm1, bytes, cudaMemcpyDeviceToDevice, st));
+        CHEBFI_CUDA(cudaMemcpyAsync(ck(j / s, 1), yk, bytes, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+  }
+  // backward sweep, segment by segment
+  bool have2 = false;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int j = seg * s, e = std::min(j + s, n);
+    CHEBFI_CUDA(cudaMemcpyAsync(segb, ck(seg, 1), bytes, cudaMemcpyDeviceToDevice, st));
+    for (int m = 1; m < e - j; ++m) {
+      const int k = j + m - 1;  // Y_{k+1} from Y_k and Y_{k-1}
+      const C* ykm1 = m >= 2 ? segb + blk * (m - 2) : (j > 0 ? ck(seg, 0) : nullptr);
+      cheb_step<R>(ctx, false, segb + blk * (m - 1), ykm1, segb + blk * m, alpha(k), c, 1.0, sb, nb, st);
+    }
+    for (int k = e - 1; k >= j; --k) {
+      const double a = alpha(k);
+      // L_k = a (H S^{-1} L_{k+1} - c L_{k+1}) - L_{k+2}, written over L_{k+2}
+      const C* u = cheb_step<R>(ctx, true, lam1, have2 ? lam2 : nullptr, lam2, a, c, 1.0, sb, nb, st);
+      const C* yk = segb + blk * (k - j);
+      if (gV || gD) {
+        if constexpr (sizeof(R) == 8) {
+          accumulate_pair(ctx, yk, u, a, nb, gV, gD, st);
+        } else {
+          to_f64(ctx, yk, w.gA.p, nb, st);
+          to_f64(ctx, u, w.gB.p, nb, st);
+          accumulate_pair(ctx, w.gA.p, w.gB.p, a, nb, gV, gD, st);
+        }
+      }
+      std::swap(lam1, lam2);
+      have2 = true;
+    }
+  }
+  if constexpr (sizeof(R) == 8) {
+    CHEBFI_CUDA(cudaMemcpyAsync(w.Ya.p, lam1, bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    to_f64(ctx, lam1, w.Ya.p, nb, st);
+  }
+}
+
 }  // namespace
 }  // namespace chebfi
 
@@ -778,8 +1036,11 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
   ctx->d_Dblk.upload(D, nblkv);
   std::vector<float> Df(D, D + nblkv);
   ctx->d_Dblkf.upload(Df.data(), nblkv);
+  ctx->refine_ready = false;
+  ctx->h_Qblk.clear();
   if (Q) {
     ctx->d_Qblk.upload(Q, nblkv);
+    ctx->h_Qblk.assign(Q, Q + nblkv);
     ctx->paw = true;
   }
   // P in sorted row order
@@ -1149,6 +1410,105 @@ int chebfi_apply_H_backward(chebfi_ctx* ctx, const void* Y, const void* G, void*
     block_outer_grad(ctx, w.pa.p, w.pc.p, nq, nb, gD, st);
   }
   if (gV) vloc_gradient(ctx, w.Ya.p, w.Yb.p, nb, gV, st, w.T2, w.tmp, w.tmp2);
+  API_END(ctx)
+}
+
+int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int64_t ld, double tol,
+                              int maxit, int* iterations, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, X, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || out, CHEBFI_ERR_ARG, "null out");
+  CHEBFI_REQUIRE(tol > 0.0 && std::isfinite(tol) && maxit >= 0, CHEBFI_ERR_ARG, "need tol > 0 and maxit >= 0");
+  if (iterations) *iterations = 0;
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw, nq = ctx->nproj;
+  gather_to_Ya(ctx, X, nb, ld, st);
+  int it = 0;
+  bool converged = true;
+  if (ctx->paw) {
+    ensure_refine(ctx, st);
+    const size_t np = (size_t)nq * nb;
+    w.pa.alloc(np);  // b = P^H x
+    w.pb.alloc(np);  // q
+    w.pc.alloc(np);  // r
+    w.pt.alloc(np);  // B^{-1} r
+    w.dvec1.alloc(nb);
+    w.dvec2.alloc(nb);
+    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk, "gemm_refine");
+    column_dots(nq, nb, w.pa.p, nq, w.pa.p, nq, w.dvec1.p, false, st);
+    std::vector<double> bn(nb), rn(nb);
+    CHEBFI_CUDA(cudaMemcpyAsync(bn.data(), w.dvec1.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    CHEBFI_CUDA(cudaMemsetAsync(w.pb.p, 0, sizeof(double2) * np, st));
+    for (it = 0; it <= maxit; ++it) {
+      // r = b - A q
+      CHEBFI_CUDA(cudaMemcpyAsync(w.pc.p, w.pa.p, sizeof(double2) * np, cudaMemcpyDeviceToDevice, st));
+      if (it > 0)
+        gemm<double>(false, false, nq, nb, nq, -1.0, ctx->d_Aref.p, nq, w.pb.p, nq, 1.0, w.pc.p, nq, st, &w.splitk,
+                     "gemm_refine");
+      column_dots(nq, nb, w.pc.p, nq, w.pc.p, nq, w.dvec2.p, false, st);
+      CHEBFI_CUDA(cudaMemcpyAsync(rn.data(), w.dvec2.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+      CHEBFI_CUDA(cudaStreamSynchronize(st));
+      converged = true;
+      for (int64_t b = 0; b < nb; ++b)
+        if (!(std::sqrt(std::max(rn[b], 0.0)) <= tol * std::sqrt(std::max(bn[b], 0.0)))) converged = false;
+      if (converged || it == maxit) break;
+      // q <- q + B^{-1} r
+      blockdiag_apply_c(ctx, ctx->d_Binv.p, ctx->d_cblk_off.p, w.pc.p, nq, w.pt.p, nq, nb, st);
+      axpby<double>(nq, nb, 1.0, w.pt.p, nq, 1.0, w.pb.p, nq, w.pb.p, nq, st);
+    }
+    // S^{-1} x = x - P q
+    gemm<double>(false, false, npw, nb, nq, -1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk,
+                 "gemm_refine");
+  }
+  scatter_from(ctx, w.Ya.p, out, nb, ld, st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  if (iterations) *iterations = it;
+  CHEBFI_REQUIRE(converged, CHEBFI_ERR_NO_CONVERGENCE,
+                 "iterative refinement did not reach the tolerance in " + std::to_string(maxit) + " iterations");
+  API_END(ctx)
+}
+
+int chebfi_cheb_filter_backward(chebfi_ctx* ctx, const void* Y0, const void* gYn, void* gY0, double* gV, double* gD,
+                                int64_t nb, int64_t ld, int degree, double lambda_lo, double lambda_hi, int prec,
+                                int checkpoint_every, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y0, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || gYn, CHEBFI_ERR_ARG, "null gYn");
+  CHEBFI_REQUIRE(degree >= 0 && degree <= 1000, CHEBFI_ERR_ARG, "degree out of range");
+  CHEBFI_REQUIRE(std::isfinite(lambda_lo) && std::isfinite(lambda_hi) && lambda_hi > lambda_lo, CHEBFI_ERR_ARG,
+                 "need finite lambda_lo < lambda_hi");
+  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32, CHEBFI_ERR_ARG,
+                 "the filter backward runs in the FP64 or the FP32 form");
+  CHEBFI_REQUIRE(checkpoint_every >= 0, CHEBFI_ERR_ARG, "negative checkpoint interval");
+  cudaStream_t st = S(stream);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw;
+  int64_t nblkv = 0;
+  for (int a = 0; a < ctx->natoms; ++a) {
+    const int64_t na = ctx->offs[a + 1] - ctx->offs[a];
+    nblkv += na * na;
+  }
+  if (gV) CHEBFI_CUDA(cudaMemsetAsync(gV, 0, sizeof(double) * ctx->grid[0] * ctx->grid[1] * ctx->grid[2], st));
+  if (gD && nblkv > 0) CHEBFI_CUDA(cudaMemsetAsync(gD, 0, sizeof(double) * nblkv, st));
+  if (nb == 0) return CHEBFI_OK;
+  w.Ya.alloc((size_t)npw * nb);
+  w.Yb.alloc((size_t)npw * nb);
+  gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y0, ld, w.Ya.p, npw, st);
+  gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)gYn, ld, w.Yb.p, npw, st);
+  if (degree == 0) {  // the filter is the identity
+    if (gY0) scatter_from(ctx, w.Yb.p, gY0, nb, ld, st);
+    return CHEBFI_OK;
+  }
+  int s = checkpoint_every;
+  if (s == 0) s = (int)std::ceil(std::sqrt((double)degree));
+  s = std::max(1, std::min(s, degree));
+  if (prec == CHEBFI_F64) filter_backward<double>(ctx, nb, degree, lambda_lo, lambda_hi, s, gV, gD, st);
+  else filter_backward<float>(ctx, nb, degree, lambda_lo, lambda_hi, s, gV, gD, st);
+  if (gY0) scatter_from(ctx, w.Ya.p, gY0, nb, ld, st);
   API_END(ctx)
 }
 

@@ -179,10 +179,31 @@ __global__ void k_hermitize(int64_t n, double2* A, int64_t lda) {
   A[j + i * lda] = make_double2(h.x, -h.y);
 }
 
+// one thread per (projector i, band b): out_ib = sum_j B_a[i - o, j - o] p_jb over i's atom block
+__global__ void k_blockdiag_apply_c(int64_t nproj, int64_t nb, const int32_t* __restrict__ atom_of,
+                                    const int32_t* __restrict__ offs, const int64_t* __restrict__ cblk_off,
+                                    const double2* __restrict__ B, const double2* __restrict__ p, int64_t ldp,
+                                    double2* __restrict__ out, int64_t ldo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nproj * nb) return;
+  const int64_t i = idx % nproj, b = idx / nproj;
+  const int a = atom_of[i];
+  const int o = offs[a], na = offs[a + 1] - o;
+  const double2* Ba = B + cblk_off[a];
+  double re = 0.0, im = 0.0;
+  for (int jl = 0; jl < na; ++jl) {
+    const double2 m = Ba[(i - o) + (int64_t)jl * na], v = p[o + jl + b * ldp];
+    re += m.x * v.x - m.y * v.y;
+    im += m.x * v.y + m.y * v.x;
+  }
+  out[i + b * ldo] = make_double2(re, im);
+}
+
 // one thread per (projector i, position j within i's atom block)
 __global__ void k_block_outer_grad(int64_t nproj, const int32_t* __restrict__ atom_of, const int32_t* __restrict__ offs,
                                    const int64_t* __restrict__ blk_off, const double2* __restrict__ q,
-                                   const double2* __restrict__ p, int64_t ldp, int64_t nb, double* __restrict__ gD) {
+                                   const double2* __restrict__ p, int64_t ldp, int64_t nb, double* __restrict__ gD,
+                                   double scale, int accumulate) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nproj * 64) return;
   const int64_t i = idx / 64;
@@ -196,7 +217,8 @@ __global__ void k_block_outer_grad(int64_t nproj, const int32_t* __restrict__ at
     const double2 u = q[i + b * ldp], v = p[j + b * ldp];
     acc += u.x * v.x + u.y * v.y;
   }
-  gD[blk_off[a] + (i - o) * na + jl] = acc;
+  double* g = gD + blk_off[a] + (i - o) * na + jl;
+  *g = scale * acc + (accumulate ? *g : 0.0);
 }
 
 __global__ void k_mirror_lower(int64_t n, double2* A, int64_t lda) {
@@ -314,11 +336,20 @@ void hermitize(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
   CHEBFI_LAUNCH("k_hermitize", st, k_hermitize<<<nblocks(n * n), 256, 0, st>>>(n, A, lda));
 }
 void block_outer_grad(const chebfi_ctx* ctx, const double2* q, const double2* p, int64_t ldp, int64_t nb, double* gD,
-                      cudaStream_t st) {
+                      cudaStream_t st, double scale, bool accumulate) {
   if (ctx->nproj == 0) return;
   CHEBFI_LAUNCH("k_block_outer_grad", st,
                 k_block_outer_grad<<<nblocks(ctx->nproj * 64), 256, 0, st>>>(ctx->nproj, ctx->d_atom_of.p, ctx->d_offs.p,
-                                                                          ctx->d_blk_off.p, q, p, ldp, nb, gD));
+                                                                          ctx->d_blk_off.p, q, p, ldp, nb, gD,
+                                                                          scale, accumulate ? 1 : 0));
+}
+void blockdiag_apply_c(const chebfi_ctx* ctx, const double2* Bblk, const int64_t* cblk_off, const double2* p,
+                       int64_t ldp, double2* out, int64_t ldo, int64_t nb, cudaStream_t st) {
+  if (ctx->nproj == 0 || nb == 0) return;
+  CHEBFI_LAUNCH("k_blockdiag_apply_c", st,
+                k_blockdiag_apply_c<<<nblocks(ctx->nproj * nb), 256, 0, st>>>(ctx->nproj, nb, ctx->d_atom_of.p,
+                                                                            ctx->d_offs.p, cblk_off, Bblk, p, ldp,
+                                                                            out, ldo));
 }
 void mirror_lower(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
   if (n == 0) return;

@@ -16,6 +16,7 @@
 
 #include "fft_core.cuh"
 #include "fft_fast.cuh"
+#include "fft_fast_kernels.cuh"
 #include "internal.cuh"
 #include "kernels.cuh"
 
@@ -233,107 +234,23 @@ __global__ void k_density_accum(int n1, int n2, int n3, int64_t nbc, const cplx<
 }
 
 // ---------------------------------------------------------------- compile-time-length path
-// Same three passes with two-pass register codelets (fft_fast.cuh): the inverse transforms
-// leave real space in split order and the forward transforms read it back, so the z index
-// of the column buffer and the plane's (x, y) are split positions; V_loc is stored in the
-// same order.  Sphere points and columns are addressed at natural indices.
-constexpr int kCBF = 32;  // columns per z-pass block
-
-struct FastArgs {
-  int ncol, nxa, pitch, zpitch, ncolp;
-  int64_t ldt;
-  const int32_t* col_start;
-  const int32_t* pw_line;
-  const int32_t* pw_z;      // natural z of each sorted sphere point
-  const int32_t* col_off;   // natural x * pitch + y of each column
-  const int32_t* row_off;   // natural x * pitch of each active x
-};
-
-template <typename R, int N>
-__device__ __forceinline__ void load_tw(cplx<R>* s, const cplx<R>* g) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s[i] = g[i];
-}
+// The pass bodies live in fft_fast_kernels.cuh; here each block finds its columns or plane
+// from its grid position.
+using fk::FastArgs;
+using fk::kCBF;
 
 template <typename R, int N3>
 __global__ void __launch_bounds__(kThreads) k_zinv_f(const cplx<R>* __restrict__ Y, int64_t ldy,
                                                      cplx<R>* __restrict__ T, FastArgs fa, const cplx<R>* __restrict__ twz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* lines = tw + N3;
-  load_tw<R, N3>(tw, twz);
-  const int c0 = blockIdx.x * kCBF;
-  const int nc = min(kCBF, fa.ncol - c0);
-  const int64_t b = blockIdx.y;
-  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
-  for (int i = threadIdx.x; i < kCBF * fa.zpitch; i += blockDim.x) lines[i] = zero;
-  __syncthreads();
-  const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
-  const cplx<R>* y = Y + b * ldy;
-  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
-    lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]] = y[j];
-  __syncthreads();
-  LineMap lm;
-  lm.stride = fa.zpitch;
-  fast::lines_F<N3, +1>(lines, nc, lm, 1, tw);
-  cplx<R>* t = T + b * fa.ldt + c0;
-  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
-    const int z = i / nc, l = i - z * nc;
-    t[(int64_t)z * fa.ncolp + l] = lines[l * fa.zpitch + z];
-  }
+  fk::zinv_body<R, N3>(Y, ldy, T, fa, twz, blockIdx.x * kCBF, blockIdx.y, smem_raw);
 }
 
 template <typename R, int N>
 __global__ void __launch_bounds__(kThreads) k_plane_f(cplx<R>* __restrict__ T, const R* __restrict__ Vs, FastArgs fa,
                                                       const cplx<R>* __restrict__ twxy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* plane = tw + N;
-  load_tw<R, N>(tw, twxy);
-  const int z = blockIdx.x;
-  const int64_t b = blockIdx.y;
-  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
-  for (int i = threadIdx.x; i < N * fa.pitch; i += blockDim.x) plane[i] = zero;
-  __syncthreads();
-  cplx<R>* t = T + b * fa.ldt + (int64_t)z * fa.ncolp;
-  for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) plane[fa.col_off[c]] = t[c];
-  __syncthreads();
-  LineMap rows;
-  rows.off = fa.row_off;
-  LineMap cols;
-  cols.stride = 1;
-  fast::lines_F<N, +1>(plane, fa.nxa, rows, 1, tw);       // along y on the rows that hold columns
-  // along x on every y: F's pass A; then, per contiguous group, F's pass B, the multiply by
-  // V_loc and G's pass B in registers; then G's pass A
-  fast::F_passA<N, +1>(plane, N, cols, fa.pitch, tw, threadIdx.x, blockDim.x);
-  __syncthreads();
-  {
-    constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB;
-    const R* v = Vs + (int64_t)z * N * N;
-    for (int t = threadIdx.x; t < N * NA; t += blockDim.x) {
-      const int ka = t / N, yy = t - ka * N;
-      cplx<R>* a = plane + yy + NB * ka * fa.pitch;
-      const R* vv = v + (NB * ka) * N + yy;
-      cplx<R> u[NB];
-#pragma unroll
-      for (int nb = 0; nb < NB; ++nb) u[nb] = a[nb * fa.pitch];
-      fast::dft<NB, +1>(u);
-#pragma unroll
-      for (int kb = 0; kb < NB; ++kb) {
-        const R s = vv[kb * N];
-        u[kb].x *= s;
-        u[kb].y *= s;
-      }
-      fast::dft<NB, -1>(u);
-#pragma unroll
-      for (int nb = 0; nb < NB; ++nb)
-        a[nb * fa.pitch] = (ka == 0 || nb == 0) ? u[nb] : u[nb] * fast::twN<-1>(tw, nb * ka);
-    }
-  }
-  __syncthreads();
-  fast::G_passA<N, -1>(plane, N, cols, fa.pitch, threadIdx.x, blockDim.x);
-  __syncthreads();
-  fast::lines_G<N, -1>(plane, fa.nxa, rows, 1, tw);       // along y on the needed rows
-  for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) t[c] = plane[fa.col_off[c]];
+  fk::plane_body<R, N>(T, Vs, fa, twxy, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 template <typename R, int N3>
@@ -341,50 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_zfwd_f(const cplx<R>* __restrict__
                                                      const cplx<R>* __restrict__ twz, const R* __restrict__ K,
                                                      LocalEpi<R> ep) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* lines = tw + N3;
-  load_tw<R, N3>(tw, twz);
-  const int c0 = blockIdx.x * kCBF;
-  const int nc = min(kCBF, fa.ncol - c0);
-  const int64_t b = blockIdx.y;
-  const cplx<R>* t = T + b * fa.ldt + c0;
-  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
-    const int z = i / nc, l = i - z * nc;
-    lines[l * fa.zpitch + z] = t[(int64_t)z * fa.ncolp + l];
-  }
-  __syncthreads();
-  LineMap lm;
-  lm.stride = fa.zpitch;
-  fast::lines_G<N3, -1>(lines, nc, lm, 1, tw);
-  const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
-  const cplx<R>* y = ep.Y + b * ep.ldy;
-  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-    const cplx<R> v = lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]];
-    const cplx<R> yj = y[j];
-    const R k = K[j];
-    cplx<R> zj;
-    zj.x = v.x * ep.inv_n3 + k * yj.x;
-    zj.y = v.y * ep.inv_n3 + k * yj.y;
-    if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
-    if (ep.Zhi) {
-      const float zr = (float)zj.x, zi = (float)zj.y;
-      const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi);
-      __nv_bfloat16* ph = ep.Zhi + b * ep.ldzb + 2 * j;
-      __nv_bfloat16* pl = ep.Zlo + b * ep.ldzb + 2 * j;
-      ph[0] = hr;
-      ph[1] = hi_;
-      pl[0] = __float2bfloat16_rn(zr - __bfloat162float(hr));
-      pl[1] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
-    }
-    if (ep.T) {
-      cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
-      if (ep.Yprev) tp = ep.Yprev[b * ep.ldt + j];
-      cplx<R> o;
-      o.x = ep.a * (zj.x - ep.c * yj.x) - ep.bprev * tp.x;
-      o.y = ep.a * (zj.y - ep.c * yj.y) - ep.bprev * tp.y;
-      ep.T[b * ep.ldt + j] = o;
-    }
-  }
+  fk::zfwd_body<R, N3>(T, fa, twz, K, ep, blockIdx.x * kCBF, blockIdx.y, smem_raw);
 }
 
 template <typename R> void set_smem(const void* f, size_t bytes) {
@@ -540,11 +414,11 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
 }
 
 void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_t nb, double* gV, cudaStream_t st,
-                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb) {
+                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb, double scale, bool accumulate) {
   const SphereFFT& s = ctx->sph;
   const int n1 = s.n1, n2 = s.n2, n3 = s.n3;
   const int64_t n = (int64_t)n1 * n2 * n3;
-  CHEBFI_CUDA(cudaMemsetAsync(gV, 0, sizeof(double) * n, st));
+  if (!accumulate) CHEBFI_CUDA(cudaMemsetAsync(gV, 0, sizeof(double) * n, st));
   if (nb <= 0) return;
   SphArgs sa;
   sa.ncol = s.ncol;
@@ -589,7 +463,7 @@ void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_
     }
     CHEBFI_LAUNCH("k_density_accum", st,
                   k_density_accum<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n1, n2, n3, nbc, Rb.p, Gb.p,
-                                                                                    1.0 / (double)n, gV));
+                                                                                    scale / (double)n, gV));
   }
 }
 

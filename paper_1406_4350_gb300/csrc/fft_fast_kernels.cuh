@@ -1,0 +1,170 @@
+// Bodies of the compile-time-length FFT passes of the local-potential operator (Section
+// 2.1, Algorithm 1's V_loc psi): the z pass from the sphere to the column buffer, the plane
+// pass (x and y transforms with the multiply by V_loc between them) and the z pass back to
+// the sphere with the fused epilogue.  Shared by the single-problem kernels (fft.cu) and the
+// batched k-point kernels (batch.cu), which differ only in how a block finds its problem.
+//
+// The inverse transforms leave real space in split order and the forward transforms read it
+// back, so the z index of the column buffer and the plane's (x, y) are split positions; V_loc
+// is stored in the same order.  Sphere points and columns are addressed at natural indices.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "fft_fast.cuh"
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace chebfi {
+namespace fk {
+
+constexpr int kThreadsF = 256;
+constexpr int kCBF = 32;  // columns per z-pass block
+
+struct FastArgs {
+  int ncol, nxa, pitch, zpitch, ncolp;
+  int64_t ldt;
+  const int32_t* col_start;
+  const int32_t* pw_line;
+  const int32_t* pw_z;      // natural z of each sorted sphere point
+  const int32_t* col_off;   // natural x * pitch + y of each column
+  const int32_t* row_off;   // natural x * pitch of each active x
+};
+
+template <typename R, int N>
+__device__ __forceinline__ void load_tw(cplx<R>* s, const cplx<R>* g) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s[i] = g[i];
+}
+
+// sphere block b, columns [c0, c0 + kCBF) -> inverse z transform -> column buffer T
+template <typename R, int N3>
+__device__ __forceinline__ void zinv_body(const cplx<R>* __restrict__ Y, int64_t ldy, cplx<R>* __restrict__ T,
+                                          const FastArgs& fa, const cplx<R>* __restrict__ twz, int c0, int64_t b,
+                                          unsigned char* smem_raw) {
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* lines = tw + N3;
+  load_tw<R, N3>(tw, twz);
+  const int nc = min(kCBF, fa.ncol - c0);
+  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
+  for (int i = threadIdx.x; i < kCBF * fa.zpitch; i += blockDim.x) lines[i] = zero;
+  __syncthreads();
+  const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
+  const cplx<R>* y = Y + b * ldy;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+    lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]] = y[j];
+  __syncthreads();
+  LineMap lm;
+  lm.stride = fa.zpitch;
+  fast::lines_F<N3, +1>(lines, nc, lm, 1, tw);
+  cplx<R>* t = T + b * fa.ldt + c0;
+  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
+    const int z = i / nc, l = i - z * nc;
+    t[(int64_t)z * fa.ncolp + l] = lines[l * fa.zpitch + z];
+  }
+}
+
+// plane z of block b: inverse y and x transforms, multiply by V_loc, forward x and y
+template <typename R, int N>
+__device__ __forceinline__ void plane_body(cplx<R>* __restrict__ T, const R* __restrict__ Vs, const FastArgs& fa,
+                                           const cplx<R>* __restrict__ twxy, int z, int64_t b,
+                                           unsigned char* smem_raw) {
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* plane = tw + N;
+  load_tw<R, N>(tw, twxy);
+  const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
+  for (int i = threadIdx.x; i < N * fa.pitch; i += blockDim.x) plane[i] = zero;
+  __syncthreads();
+  cplx<R>* t = T + b * fa.ldt + (int64_t)z * fa.ncolp;
+  for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) plane[fa.col_off[c]] = t[c];
+  __syncthreads();
+  LineMap rows;
+  rows.off = fa.row_off;
+  LineMap cols;
+  cols.stride = 1;
+  fast::lines_F<N, +1>(plane, fa.nxa, rows, 1, tw);       // along y on the rows that hold columns
+  // along x on every y: F's pass A; then, per contiguous group, F's pass B, the multiply by
+  // V_loc and G's pass B in registers; then G's pass A
+  fast::F_passA<N, +1>(plane, N, cols, fa.pitch, tw, threadIdx.x, blockDim.x);
+  __syncthreads();
+  {
+    constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB;
+    const R* v = Vs + (int64_t)z * N * N;
+    for (int it = threadIdx.x; it < N * NA; it += blockDim.x) {
+      const int ka = it / N, yy = it - ka * N;
+      cplx<R>* a = plane + yy + NB * ka * fa.pitch;
+      const R* vv = v + (NB * ka) * N + yy;
+      cplx<R> u[NB];
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb) u[nb] = a[nb * fa.pitch];
+      fast::dft<NB, +1>(u);
+#pragma unroll
+      for (int kb = 0; kb < NB; ++kb) {
+        const R s = vv[kb * N];
+        u[kb].x *= s;
+        u[kb].y *= s;
+      }
+      fast::dft<NB, -1>(u);
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb)
+        a[nb * fa.pitch] = (ka == 0 || nb == 0) ? u[nb] : u[nb] * fast::twN<-1>(tw, nb * ka);
+    }
+  }
+  __syncthreads();
+  fast::G_passA<N, -1>(plane, N, cols, fa.pitch, threadIdx.x, blockDim.x);
+  __syncthreads();
+  fast::lines_G<N, -1>(plane, fa.nxa, rows, 1, tw);       // along y on the needed rows
+  for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) t[c] = plane[fa.col_off[c]];
+}
+
+// columns [c0, c0 + kCBF) of block b: forward z transform, back to the sphere, + K psi and
+// the epilogue (Z, its bf16 pair, and the Chebyshev combination T = a (Z - c Y) - b Yprev)
+template <typename R, int N3>
+__device__ __forceinline__ void zfwd_body(const cplx<R>* __restrict__ T, const FastArgs& fa,
+                                          const cplx<R>* __restrict__ twz, const R* __restrict__ K,
+                                          const LocalEpi<R>& ep, int c0, int64_t b, unsigned char* smem_raw) {
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* lines = tw + N3;
+  load_tw<R, N3>(tw, twz);
+  const int nc = min(kCBF, fa.ncol - c0);
+  const cplx<R>* t = T + b * fa.ldt + c0;
+  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
+    const int z = i / nc, l = i - z * nc;
+    lines[l * fa.zpitch + z] = t[(int64_t)z * fa.ncolp + l];
+  }
+  __syncthreads();
+  LineMap lm;
+  lm.stride = fa.zpitch;
+  fast::lines_G<N3, -1>(lines, nc, lm, 1, tw);
+  const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
+  const cplx<R>* y = ep.Y + b * ep.ldy;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const cplx<R> v = lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]];
+    const cplx<R> yj = y[j];
+    const R k = K[j];
+    cplx<R> zj;
+    zj.x = v.x * ep.inv_n3 + k * yj.x;
+    zj.y = v.y * ep.inv_n3 + k * yj.y;
+    if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
+    if (ep.Zhi) {
+      const float zr = (float)zj.x, zi = (float)zj.y;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi);
+      __nv_bfloat16* ph = ep.Zhi + b * ep.ldzb + 2 * j;
+      __nv_bfloat16* pl = ep.Zlo + b * ep.ldzb + 2 * j;
+      ph[0] = hr;
+      ph[1] = hi_;
+      pl[0] = __float2bfloat16_rn(zr - __bfloat162float(hr));
+      pl[1] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
+    }
+    if (ep.T) {
+      cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
+      if (ep.Yprev) tp = ep.Yprev[b * ep.ldt + j];
+      cplx<R> o;
+      o.x = ep.a * (zj.x - ep.c * yj.x) - ep.bprev * tp.x;
+      o.y = ep.a * (zj.y - ep.c * yj.y) - ep.bprev * tp.y;
+      ep.T[b * ep.ldt + j] = o;
+    }
+  }
+}
+
+}  // namespace fk
+}  // namespace chebfi

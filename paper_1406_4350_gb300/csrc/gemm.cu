@@ -25,14 +25,17 @@ template <typename R, bool CA, bool CB>
 __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, R alpha, const cplx<R>* __restrict__ A,
                                               int64_t lda, const cplx<R>* __restrict__ B, int64_t ldb, R beta,
                                               cplx<R>* __restrict__ Cm, int64_t ldc, int64_t kchunk,
-                                              cplx<R>* __restrict__ ws, int lower) {
+                                              cplx<R>* __restrict__ ws, int lower, int n_fastest) {
   using C = cplx<R>;
-  if (lower && blockIdx.x < blockIdx.y) return;  // tile strictly above the diagonal
+  // n_fastest: blockIdx.x walks the column tiles, so CTAs launched together share a row
+  // tile of A (the large operand when M >> N) in L2
+  const int64_t tile_i = n_fastest ? blockIdx.y : blockIdx.x, tile_j = n_fastest ? blockIdx.x : blockIdx.y;
+  if (lower && tile_i < tile_j) return;  // tile strictly above the diagonal
   __shared__ C As[BK][BM + 1];
   __shared__ C Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+  const int64_t i0 = tile_i * BM, j0 = tile_j * BN;
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   const int64_t kend = min(K, kbeg + kchunk);
   R accr[4][4], acci[4][4];
@@ -142,17 +145,19 @@ void launch(int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A, int
   kchunk = (kchunk + BK - 1) / BK * BK;
   splits = (int)((K + kchunk - 1) / kchunk);
   if (K == 0) { splits = 1; kchunk = BK; }
-  CHEBFI_REQUIRE(tn <= 65535, CHEBFI_ERR_ARG, "GEMM N too large");
+
   cplx<R>* wsp = nullptr;
   if (splits > 1) {
     ws->alloc((size_t)splits * M * N);
     wsp = ws->p;
   }
-  dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)splits);
+  const bool n_fastest = tm > 4 * tn;
+  CHEBFI_REQUIRE((n_fastest ? tm : tn) <= 65535, CHEBFI_ERR_ARG, "GEMM too large");
+  dim3 grid(n_fastest ? (unsigned)tn : (unsigned)tm, n_fastest ? (unsigned)tm : (unsigned)tn, (unsigned)splits);
   const double tiles_done = lower ? (double)(tm * (tm + 1) / 2) / (double)(tm * tn) : 1.0;
   CHEBFI_LAUNCH_W(tag, st, 8.0 * (double)M * (double)N * (double)K * tiles_done,
                   k_gemm<R, CA, CB><<<grid, 256, 0, st>>>(M, N, K, (R)alpha, A, lda, B, ldb, (R)beta, Cm, ldc, kchunk,
-                                                          wsp, lower ? 1 : 0));
+                                                          wsp, lower ? 1 : 0, n_fastest ? 1 : 0));
   if (splits > 1) {
     const int64_t tot = M * N;
     CHEBFI_LAUNCH("k_splitk_reduce", st, k_splitk_reduce<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, wsp, (R)beta, Cm, ldc));

@@ -173,6 +173,8 @@ struct Work {
   DevBuf<double2> splitk;
   DevBuf<float2> fsplitk;
   SplitBF16Buf Zb, Sb;  // bf16 pairs of Z (or Y) and of the projection-space operands
+  DevBuf<double2> gpool, gA, gB;  // filter backward: checkpoints, segment, adjoint iterates
+  DevBuf<float2> fgpool;
 };
 
 }  // namespace chebfi
@@ -230,6 +232,10 @@ struct chebfi_ctx {
   int natoms = 0;
   bool paw = false;
   std::vector<int32_t> offs;
+  std::vector<double> h_Qblk;                 // host copy of the D_S (Q) blocks
+  bool refine_ready = false;                  // A and B^{-1} of the iterative Woodbury solve
+  chebfi::DevBuf<double2> d_Aref, d_Binv;     // A = D_S^{-1} + P^H P (dense), packed B^{-1} blocks
+  chebfi::DevBuf<int64_t> d_cblk_off;         // atom -> offset of its complex block in d_Binv
   chebfi::DevBuf<int32_t> d_offs;
   chebfi::DevBuf<int32_t> d_atom_of;          // projector -> atom
   chebfi::DevBuf<double> d_Dblk, d_Qblk;      // packed blocks (row-major per atom)

@@ -31,10 +31,11 @@ size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb);
 // output is g: gV(x, y, z) = (1/N^3) sum_b Re(conj(g_b(r)) psi_b(r)) with psi_b, g_b the
 // real-space values of sorted-order sphere blocks Ys, Gs (ld = npw).  FP64.
 void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_t nb, double* gV, cudaStream_t st,
-                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb);
-// gD[entry (i, j) of atom block a] = sum_b Re(conj(q_ib) p_jb)
+                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb, double scale = 1.0,
+                   bool accumulate = false);
+// gD[entry (i, j) of atom block a] = scale * sum_b Re(conj(q_ib) p_jb)  (+= if accumulate)
 void block_outer_grad(const chebfi_ctx* ctx, const double2* q, const double2* p, int64_t ldp, int64_t nb, double* gD,
-                      cudaStream_t st);
+                      cudaStream_t st, double scale = 1.0, bool accumulate = false);
 // the two-pass FFT kernels cover cubic grids of a few compiled sizes; split_index(n, p) is
 // the natural index held at position p of their split order
 bool fast_fft_supported(int n1, int n2, int n3);
@@ -70,6 +71,9 @@ void split_block(int64_t m, int64_t nb, const float2* x, int64_t ldx, SplitBF16B
 template <typename R>
 void blockdiag_apply(const chebfi_ctx* ctx, const R* Dblk, const cplx<R>* p, int64_t ldp, cplx<R>* out,
                      int64_t ldo, int64_t nb, cudaStream_t st);
+// out = Bbd p with complex per-atom blocks (column-major, block a at cblk_off[a])
+void blockdiag_apply_c(const chebfi_ctx* ctx, const double2* Bblk, const int64_t* cblk_off, const double2* p,
+                       int64_t ldp, double2* out, int64_t ldo, int64_t nb, cudaStream_t st);
 // out = a (u - c x) - b y   (elementwise on an m x nb block; y may be null, out may alias y)
 template <typename R>
 void cheb_combine(int64_t m, int64_t nb, R a, const cplx<R>* u, int64_t ldu, R c, const cplx<R>* x,

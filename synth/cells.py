@@ -37,7 +37,7 @@ from typing import Optional
 
 import numpy as np
 
-__all__ = ["Cell", "make_cell", "CONFIGS", "config_cell", "random_block"]
+__all__ = ["Cell", "make_cell", "CONFIGS", "config_cell", "random_block", "kpoint_cells"]
 
 
 @dataclasses.dataclass
@@ -254,3 +254,25 @@ def config_cell(name: str, nbands: Optional[int] = None, cache: bool = True) -> 
     if nbands is not None:
         cell.Y0 = np.asfortranarray(cell.Y0[:, :nbands])
     return cell
+
+
+def kpoint_cells(nk: int = 64, nbands: int = 128, seed: int = 1004, npw_range=(3000, 12000), L: float = 20.0,
+                 grid: int = 48, natoms: int = 32, nlmn: int = 8):
+    """The batched k-point workload: one PAW cell (the atoms, V_loc, D and Q of
+    ``make_cell(L, grid, ., natoms, nlmn, ., True, seed)``) sampled at ``nk`` Bloch vectors k
+    drawn uniformly in the first Brillouin zone, each with its own E_cut so that its G-sphere
+    size is drawn uniformly in ``npw_range`` (sizes from the free-electron count
+    N_pw ~ L^3 (2 E_cut)^{3/2} / (6 pi^2)).  Q is the most-halved of the per-k admissible
+    draws, so every k-point sees the same S coefficients.  Returns a list of Cells."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 7]))
+    target = rng.uniform(npw_range[0], npw_range[1], size=nk)
+    kpts = rng.uniform(-np.pi / L, np.pi / L, size=(nk, 3))
+    cells = []
+    for i in range(nk):
+        ecut = 0.5 * (target[i] * 6.0 * np.pi ** 2 / L ** 3) ** (2.0 / 3.0)
+        cells.append(make_cell(L, grid, ecut, natoms, nlmn, nbands, True, seed, kpt=kpts[i], name="k%d" % i))
+    h = max(c.q_halvings for c in cells)
+    for c in cells:
+        c.Q = c.Q * 0.5 ** (h - c.q_halvings)
+        c.q_halvings = h
+    return cells

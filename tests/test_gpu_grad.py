@@ -124,3 +124,147 @@ def test_autograd_function_matches_backward():
     dm[e] -= h
     fd = (_loss_oracle(cell, W.cpu().numpy(), D=dp) - _loss_oracle(cell, W.cpu().numpy(), D=dm)) / (2 * h)
     assert abs(D.grad[e].item() - fd) <= 1e-9 * max(1.0, abs(fd))
+
+
+# ----------------------------------------------------------------------------- filter backward
+def _interval(cell):
+    from oracle import chebyshev as ch
+    op = PWOperator.from_cell(cell)
+    lo, hi, _, _ = ch.bounds(op, cell.Y0, mode="rigorous")
+    return lo, hi
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+@pytest.mark.parametrize("paw", [True, False])
+@pytest.mark.parametrize("every", [0, 1, 2, 5])
+def test_filter_backward_matches_oracle(paw, every):
+    """chebfi_cheb_filter_backward (FP64) against the oracle's adjoint recurrence, element by
+    element, for every checkpoint interval (1: every iterate kept; 5 = degree: one segment)."""
+    from oracle.gradients import filter_backward
+    from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    cell = _cell(nb=3, paw=paw)
+    deg = 5
+    lo, hi = _interval(cell)
+    rng = np.random.default_rng(4)
+    W = rng.normal(size=cell.Y0.shape) + 1j * rng.normal(size=cell.Y0.shape)
+    g = ChebFI.from_cell(cell)
+    gY, gV, gD = g.cheb_filter_backward(fortran(cell.Y0), fortran(W), deg, lo, hi, cell.vloc.shape, cell.D.size,
+                                        checkpoint_every=every)
+    torch.cuda.synchronize()
+    rY, rV, rD = filter_backward(PWOperator.from_cell(cell), cell.Y0, W, deg, lo, hi)
+    assert _rel(gY.cpu().numpy(), rY) <= 1e-11
+    assert _rel(gV.cpu().numpy(), rV) <= 1e-11
+    assert _rel(gD.cpu().numpy(), rD) <= 1e-11
+
+
+def test_filter_backward_degree_zero_and_one():
+    from oracle.gradients import filter_backward
+    from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    cell = _cell(nb=2)
+    lo, hi = _interval(cell)
+    rng = np.random.default_rng(5)
+    W = rng.normal(size=cell.Y0.shape) + 1j * rng.normal(size=cell.Y0.shape)
+    g = ChebFI.from_cell(cell)
+    for deg in (0, 1):
+        gY, gV, gD = g.cheb_filter_backward(fortran(cell.Y0), fortran(W), deg, lo, hi, cell.vloc.shape, cell.D.size)
+        torch.cuda.synchronize()
+        rY, rV, rD = filter_backward(PWOperator.from_cell(cell), cell.Y0, W, deg, lo, hi)
+        assert _rel(gY.cpu().numpy(), rY) <= 1e-11
+        assert np.abs(gV.cpu().numpy() - rV).max() <= 1e-11 * max(np.abs(rV).max(), 1.0)
+        assert np.abs(gD.cpu().numpy() - rD).max() <= 1e-11 * max(np.abs(rD).max(), 1.0)
+
+
+def test_filter_backward_rejects_mixed_and_bad_arguments():
+    from paper_1406_4350_gb300.chebfi import ChebFI, ChebFIError, fortran
+    cell = _cell(nb=1)
+    g = ChebFI.from_cell(cell)
+    Y = fortran(cell.Y0)
+    with pytest.raises(ChebFIError):
+        g.cheb_filter_backward(Y, Y, 3, 0.0, 1.0, cell.vloc.shape, cell.D.size, prec=2)
+    with pytest.raises(ChebFIError):
+        g.cheb_filter_backward(Y, Y, 3, 1.0, 0.0, cell.vloc.shape, cell.D.size)
+    with pytest.raises(ChebFIError):
+        g.cheb_filter_backward(Y, Y, 3, 0.0, 1.0, cell.vloc.shape, cell.D.size, checkpoint_every=-1)
+
+
+def test_filter_backward_eigenvector_closed_form():
+    """Y_0 = psi_n (S-normalised exact eigenvector), gY_n = S psi_n: the filter acts as the
+    scalar p(lambda_n) = T_n((lambda_n - c)/r), so gY_0 = p S psi_n and gV = p' |psi_n(r)|^2/N^3
+    with p' = n U_{n-1}((lambda_n - c)/r)/r (numpy's Chebyshev derivative)."""
+    from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    cell = _cell(nb=1, seed=5)
+    op = PWOperator.from_cell(cell)
+    w, Psi = exact_eigs(op, vectors=True)
+    n = 3
+    psi = np.asfortranarray(Psi[:, n:n + 1])
+    deg, lo, hi = 7, w[6], float(w[-1]) + 1.0
+    c, r = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    Tn = np.polynomial.chebyshev.Chebyshev.basis(deg)
+    x = (w[n] - c) / r
+    p, dp = Tn(x), Tn.deriv()(x) / r
+    Spsi = op.apply_S(psi)
+    g = ChebFI.from_cell(cell)
+    gY, gV, _ = g.cheb_filter_backward(fortran(psi), fortran(Spsi), deg, lo, hi, cell.vloc.shape, cell.D.size,
+                                       want_D=False)
+    torch.cuda.synchronize()
+    assert np.abs(gY.cpu().numpy() - p * Spsi).max() <= 1e-10 * abs(p)
+    grid = np.zeros(op.grid, dtype=np.complex128)
+    grid[tuple(op.miller[:, i] % op.grid[i] for i in range(3))] = psi[:, 0]
+    dens = np.abs(np.fft.ifftn(grid) * op.vloc.size) ** 2 / op.vloc.size
+    assert np.abs(gV.cpu().numpy() - dp * dens).max() <= 1e-9 * abs(dp) * dens.max()
+
+
+@pytest.fixture(scope="module")
+def _cfg5():
+    """The differentiation workload: 48^3 grid, 8025 plane waves, 32 atoms x 8 projectors (PAW),
+    128 bands, degree 8, with the oracle's gradients of L = Re <W, Y_8>."""
+    from oracle.gradients import filter_backward
+    from synth import config_cell
+    cell = config_cell("paw48", nbands=128)
+    lo, hi = _interval(cell)
+    rng = np.random.default_rng(8)
+    W = np.asfortranarray(rng.normal(size=cell.Y0.shape) + 1j * rng.normal(size=cell.Y0.shape))
+    ref = filter_backward(PWOperator.from_cell(cell), cell.Y0, W, 8, lo, hi)
+    return cell, lo, hi, W, ref
+
+
+@pytest.mark.parametrize("prec, tol", [(0, 1e-10), (1, 2e-4)])
+def test_filter_backward_differentiation_workload(_cfg5, prec, tol):
+    """FP64 and FP32 forms at the differentiation workload against the oracle, every element of
+    gY_0, gV and gD (the FP32 tolerance covers FP32 iterates amplified by the degree-8 filter)."""
+    from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    cell, lo, hi, W, (rY, rV, rD) = _cfg5
+    g = ChebFI.from_cell(cell)
+    gY, gV, gD = g.cheb_filter_backward(fortran(cell.Y0), fortran(W), 8, lo, hi, cell.vloc.shape, cell.D.size,
+                                        prec=prec)
+    torch.cuda.synchronize()
+    assert _rel(gY.cpu().numpy(), rY) <= tol
+    assert _rel(gV.cpu().numpy(), rV) <= tol
+    assert _rel(gD.cpu().numpy(), rD) <= tol
+
+
+def test_autograd_filter_matches_oracle():
+    from oracle.gradients import filter_backward
+    from paper_1406_4350_gb300.autograd import cheb_filter
+    from paper_1406_4350_gb300.chebfi import ChebFI
+    from oracle import chebyshev as ch
+    cell = _cell(nb=2)
+    lo, hi = _interval(cell)
+    g = ChebFI.from_cell(cell)
+    Y = torch.tensor(cell.Y0, dtype=torch.complex128, device="cuda", requires_grad=True)
+    V = torch.tensor(cell.vloc, dtype=torch.float64, device="cuda", requires_grad=True)
+    D = torch.tensor(cell.D, dtype=torch.float64, device="cuda", requires_grad=True)
+    rng = np.random.default_rng(6)
+    W = rng.normal(size=cell.Y0.shape) + 1j * rng.normal(size=cell.Y0.shape)
+    out = cheb_filter(g, Y, V, D, 4, lo, hi)
+    ref = ch.filter_plain(PWOperator.from_cell(cell), cell.Y0, 4, lo, hi)
+    assert _rel(out.detach().cpu().numpy(), ref) <= 1e-11
+    loss = (torch.conj(torch.tensor(W, device="cuda")) * out).real.sum()
+    loss.backward()
+    rY, rV, rD = filter_backward(PWOperator.from_cell(cell), cell.Y0, W, 4, lo, hi)
+    assert _rel(Y.grad.cpu().numpy(), rY) <= 1e-11
+    assert _rel(V.grad.cpu().numpy(), rV) <= 1e-11
+    assert _rel(D.grad.cpu().numpy(), rD) <= 1e-11

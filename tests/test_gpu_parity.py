@@ -332,3 +332,40 @@ def test_paw48_forms_agree_after_convergence():
     assert res[:k].max() < 1e-7, res[:k].max()
     for prec in (1, 2):
         assert np.abs(evs[prec][0][:k] - ref[:k]).max() <= 1e-8, (prec, np.abs(evs[prec][0][:k] - ref[:k]).max())
+
+
+# ----------------------------------------------------------------------------- Woodbury by refinement
+def test_apply_Sinv_refined_matches_oracle_and_direct():
+    """Section 4.1's iterative refinement on the device: the same S^{-1} x as the direct
+    Woodbury form, in the same number of updates as the oracle's refinement."""
+    from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    cell = config_cell("paw48", nbands=16)
+    op = PWOperator.from_cell(cell)
+    g = ChebFI.from_cell(cell)
+    X = fortran(cell.Y0)
+    out, its = g.apply_Sinv_refined(X, tol=1e-12)
+    torch.cuda.synchronize()
+    ref, its_ref = op.apply_Sinv_refined(cell.Y0, tol=1e-12)
+    got = out.cpu().numpy()
+    scale = np.abs(cell.Y0).max()
+    assert np.abs(got - ref).max() <= TOL64 * scale
+    assert np.abs(got - op.apply_Sinv(cell.Y0)).max() <= TOL64 * scale
+    assert abs(its - its_ref) <= 1 and 1 <= its <= 30
+    # too few updates for the tolerance: an error, with the partial result written
+    from paper_1406_4350_gb300.chebfi import ChebFIError
+    with pytest.raises(ChebFIError):
+        g.apply_Sinv_refined(X, tol=1e-12, maxit=2)
+
+
+def test_apply_Sinv_refined_norm_conserving_and_singular_Q():
+    from paper_1406_4350_gb300.chebfi import ChebFI, ChebFIError, fortran
+    cell = make_cell(8.0, 16, 3.0, 3, 8, 2, True, 21)
+    g = ChebFI.from_cell(dataclasses.replace(cell, Q=None))
+    out, its = g.apply_Sinv_refined(fortran(cell.Y0))
+    torch.cuda.synchronize()
+    assert its == 0 and np.abs(out.cpu().numpy() - cell.Y0).max() == 0.0
+    Q = cell.Q.copy()
+    Q[:64] = 0.0  # first atom's D_S block is zero: no D_S^{-1}
+    g = ChebFI.from_cell(dataclasses.replace(cell, Q=Q))
+    with pytest.raises(ChebFIError):
+        g.apply_Sinv_refined(fortran(cell.Y0))
