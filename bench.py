@@ -198,7 +198,9 @@ def run_extra(args):
     8025 plane waves, 32 atoms x 8 projectors, PAW, 128 bands, degree 8), FP64 and FP32 forms;
     unit = band-steps of the adjoint recurrence per second (bands x degree / time).
     refine: S^{-1} by Section 4.1's iterative refinement against the direct Woodbury form on
-    the benchmark workload's first 256 bands."""
+    the benchmark workload's first 256 bands.
+    kpoints: the batched k-point filter (64 k-points of a 48^3 PAW cell, spheres of 3000 to
+    12000 plane waves, 128 bands each, FP32, degree 8) against one filter call per k-point."""
     import numpy as np
     import torch
     from paper_1406_4350_gb300 import build as b
@@ -229,6 +231,37 @@ def run_extra(args):
                 "config": {"workload": "paw48: 48^3 grid, %d plane waves, %d bands, %d projectors, PAW, degree %d, "
                                        "checkpoints every ceil(sqrt(degree))" % (cell.npw, cell.nbands, cell.nproj, deg)},
                 "forms": out}
+    elif args.task == "kpoints":
+        from paper_1406_4350_gb300.chebfi import ChebFIBatch
+        from synth import kpoint_cells
+        cells = kpoint_cells()
+        deg = 8
+        ctxs = [ChebFI.from_cell(c) for c in cells]
+        bt = ChebFIBatch(ctxs, cells[0].nbands)
+        Ys = [fortran(c.Y0) for c in cells]
+        his = [g_.upper_bound(BOUND_RIGOROUS) for g_ in ctxs]
+        los = [float(g_.rayleigh_quotients(Y).max().item()) for g_, Y in zip(ctxs, Ys)]
+        shapes, tune = bt.autotune(F32)
+        work = [Y.clone() for Y in Ys]
+        l0 = bt.kernel_launches
+        with Clocks(0) as clk:
+            ms_b = _timed(lambda: bt.cheb_filter(work, deg, los, his, prec=F32), args.steps, args.warmup)
+        launches = (bt.kernel_launches - l0) // (args.steps + args.warmup)
+
+        def loop():
+            for g_, Y, l, h in zip(ctxs, work, los, his):
+                g_.cheb_filter(Y, deg, l, h, prec=F32)
+        ms_l = _timed(loop, args.steps, args.warmup)
+        units = sum(c.nbands for c in cells) * deg
+        line = {"metric": "batched k-point filter band-H-applies/s", "unit": "band-H-applies/s",
+                "value": units / (ms_b / 1e3), "dtype": "f32", "steps": args.steps, "warmup": args.warmup,
+                "config": {"workload": "64 k-points of a 48^3 PAW cell (L = 20 bohr, 32 atoms x 8 projectors), "
+                                       "spheres %d..%d plane waves, %d bands each, degree %d, one graph replay "
+                                       "per step" % (min(c.npw for c in cells), max(c.npw for c in cells),
+                                                     cells[0].nbands, deg)},
+                "ms_batched": ms_b, "ms_per_kpoint_loop": ms_l, "speedup_over_loop": ms_l / ms_b,
+                "gpu_launches_per_call": launches, "autotuned_shapes": shapes,
+                "autotune_ms": tune.round(4).tolist(), "clocks": clk.summary()}
     else:
         cell = config_cell(WORKLOAD, nbands=256)
         g = ChebFI.from_cell(cell)
@@ -262,7 +295,7 @@ def main():
     ap.add_argument("--ref-bands", type=int, default=4)
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
-    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine"],
+    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints"],
                     help="filter: the benchmark; backward / refine: the differentiation and the "
                          "refinement-Woodbury measurements (their own JSON line)")
     args = ap.parse_args()

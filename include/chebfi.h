@@ -232,6 +232,41 @@ int chebfi_profile_count(chebfi_ctx* ctx);
 int chebfi_profile_entry(chebfi_ctx* ctx, int i, char* name, int name_len, double* ms, int64_t* launches,
                          double* work);
 
+/* ---------------------------------------------------------------- batched k-points
+ * Section 2.1: sampling the Brillouin zone gives one eigenproblem per Bloch vector k; they
+ * share the cell, grid, V_loc and atoms (D, Q) and differ in the G-sphere, the kinetic
+ * diagonal and P_k.  A batch runs Algorithm 2's filter for all of them at once: every stage
+ * is one grouped launch over all k-points (the projector GEMMs are persistent kernels that
+ * take (k, tile) items from a device work queue), and the whole degree-n filter is captured
+ * in a CUDA graph on first use and replayed afterwards.  Tile shapes of the grouped GEMMs are
+ * chosen by timing every candidate on the batch (chebfi_batch_autotune; run implicitly by
+ * the first filter call of each form). */
+typedef struct chebfi_batch chebfi_batch;
+
+/* kctx: nk fully set-up contexts (set_cell/sphere/vloc/projectors) on one device, with the
+ * same cubic grid of a compiled size (24, 32, 48, 64, 72 or 96), the same V_loc, atoms, D and
+ * Q (checked; CHEBFI_ERR_ARG otherwise), any k and sphere.  nb bands per k-point,
+ * nk * nb <= 65535.  The batch keeps the pointers: the contexts must outlive it and stay
+ * unchanged.  Synchronises.  *out is NULL on error. */
+int chebfi_batch_create(chebfi_batch** out, chebfi_ctx* const* kctx, int nk, int64_t nb);
+int chebfi_batch_destroy(chebfi_batch* batch);
+const char* chebfi_batch_last_error(const chebfi_batch* batch);
+/* Kernels launched by the batch so far (each graph replay counts its kernel nodes). */
+int64_t chebfi_batch_kernel_launches(const chebfi_batch* batch);
+/* Time the candidate tile shapes (16TM x 16TN with (TM, TN) = (4,4), (2,4), (4,2), (8,4)) of
+ * the three grouped GEMM classes (0: P_k^H Z_k, 1: G_k / M_k products, 2: P_k W_k) in form
+ * prec (CHEBFI_F64 or CHEBFI_F32) and keep the fastest.  shapes (3 ints, nullable) receives
+ * the chosen shape index per class; ms (3 x 4 doubles, nullable) the measured times.
+ * Overwrites the batch's workspaces; a no-op after the first call for a form.  Synchronises. */
+int chebfi_batch_autotune(chebfi_batch* batch, int prec, int* shapes, double* ms);
+/* In place on Y[k] (device, complex128, npw_k x nb column-major, leading dimension ld[k],
+ * caller's plane-wave order) for k = 0..nk-1: Algorithm 2's filter of the given degree on
+ * [lambda_lo[k], lambda_hi[k]] (host arrays of nk doubles), exactly as chebfi_cheb_filter
+ * computes it per k-point, in the FP64 or FP32 form.  Stream-ordered on `stream`; the first
+ * call of a (form, degree) pair tunes and captures, later calls replay the graph. */
+int chebfi_batch_cheb_filter(chebfi_batch* batch, void* const* Y, const int64_t* ld, int degree,
+                             const double* lambda_lo, const double* lambda_hi, int prec, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,12 @@ SIGNATURES = {
     "chebfi_set_D": (c_int, [c_void_p, c_void_p, c_int]),
     "chebfi_apply_H_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
                                         c_int64, c_void_p]),
+    "chebfi_batch_create": (c_int, [c_void_p, c_void_p, c_int, c_int64]),
+    "chebfi_batch_destroy": (c_int, [c_void_p]),
+    "chebfi_batch_last_error": (c_char_p, [c_void_p]),
+    "chebfi_batch_kernel_launches": (c_int64, [c_void_p]),
+    "chebfi_batch_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "chebfi_batch_cheb_filter": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     "chebfi_apply_Sinv_refined": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_double, c_int,
                                           c_void_p, c_void_p]),
     "chebfi_cheb_filter_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,

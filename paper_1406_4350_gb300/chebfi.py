@@ -13,9 +13,9 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import F64, BOUND_PAPER, Params
+from ._lib import F32, F64, BOUND_PAPER, Params
 
-__all__ = ["ChebFI", "ChebFIError", "fortran"]
+__all__ = ["ChebFI", "ChebFIBatch", "ChebFIError", "fortran"]
 
 
 class ChebFIError(RuntimeError):
@@ -288,3 +288,67 @@ class ChebFI:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.chebfi_kernel_launches(self.h))
+
+
+class ChebFIBatch:
+    """Algorithm 2's filter for many k-points of one cell in grouped launches (libchebfi
+    chebfi_batch_*).  ``contexts``: set-up ChebFI objects sharing grid, V_loc, atoms, D and
+    Q; they are kept alive by the batch."""
+
+    def __init__(self, contexts, nbands: int):
+        self.lib = _lib.load()
+        self.contexts = list(contexts)
+        self.nbands = int(nbands)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.contexts[0].device):
+            rc = self.lib.chebfi_batch_create(ctypes.byref(h), arr, len(self.contexts), self.nbands)
+        if rc != 0:
+            raise ChebFIError(rc, "chebfi_batch_create failed (contexts not compatible or not set up)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.chebfi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise ChebFIError(rc, self.lib.chebfi_batch_last_error(self.h).decode())
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.chebfi_batch_kernel_launches(self.h))
+
+    def autotune(self, prec: int = F32):
+        """Tile shape chosen per GEMM class and the measured ms table (3 x 4)."""
+        shapes = (ctypes.c_int * 3)()
+        ms = (ctypes.c_double * 12)()
+        self._check(self.lib.chebfi_batch_autotune(self.h, prec, shapes, ms))
+        return list(shapes), np.array(ms[:]).reshape(3, 4)
+
+    def cheb_filter(self, Ys, degree: int, lambda_lo, lambda_hi, prec: int = F32):
+        """In place on every block of ``Ys`` (one complex128 column-major tensor per k-point);
+        returns Ys."""
+        nk = len(self.contexts)
+        if len(Ys) != nk:
+            raise ValueError("one block per k-point")
+        ptrs, lds = [], []
+        for Y, c in zip(Ys, self.contexts):
+            y, nb, ld = _block(Y)
+            if nb != self.nbands or Y.shape[0] != c.npw:
+                raise ValueError("block shape does not match its k-point")
+            ptrs.append(y.value)
+            lds.append(ld)
+        P = (ctypes.c_void_p * nk)(*ptrs)
+        L = (ctypes.c_int64 * nk)(*lds)
+        lo = (ctypes.c_double * nk)(*[float(x) for x in lambda_lo])
+        hi = (ctypes.c_double * nk)(*[float(x) for x in lambda_hi])
+        self._check(self.lib.chebfi_batch_cheb_filter(self.h, P, L, degree, lo, hi, prec, _stream()))
+        return Ys
