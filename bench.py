@@ -197,7 +197,7 @@ def run_extra(args):
     """backward: the filter backward (gY0, gV, gD) at the differentiation workload (48^3 grid,
     8025 plane waves, 32 atoms x 8 projectors, PAW, 128 bands, degree 8), FP64 and FP32 forms;
     unit = band-steps of the adjoint recurrence per second (bands x degree / time).
-    refine: S^{-1} by Section 4.1's iterative refinement against the direct Woodbury form on
+    refine: S^{-1} by Section 5.1's iterative refinement against the direct Woodbury form on
     the benchmark workload's first 256 bands.
     kpoints: the batched k-point filter (64 k-points of a 48^3 PAW cell, spheres of 3000 to
     12000 plane waves, 128 bands each, FP32, degree 8) against one filter call per k-point."""

@@ -1,7 +1,7 @@
 /*
  * chebfi.h -- C ABI of the GB300 (sm_103a) Chebyshev-filtered subspace iteration for the
  * plane-wave Kohn-Sham eigenproblem H psi = lambda S psi (Levitt & Torrent, arXiv:1406.4350,
- * Eq. (KS) of Section 2.1; Algorithm 2 of Section 3.2; Section 4.1 for S^{-1}).
+ * Eq. (KS) of Section 2.1; Algorithm 2 of Section 4.2; Section 5.1 for S^{-1}).
  *
  * Operators (Section 2.1):
  *   H = K + V_loc + P D P^H       K diagonal |k+G|^2/2, V_loc multiplication in real space
@@ -45,7 +45,7 @@ typedef enum {
                        bf16 (hi + lo) operands and FP32 accumulation */
 } chebfi_prec;
 
-/* Upper end lambda_+ of the filtered interval (Section 4.3, "Choice of the polynomial"). */
+/* Upper end lambda_+ of the filtered interval (Section 5.3, "Choice of the polynomial"). */
 typedef enum {
   CHEBFI_BOUND_PAPER = 0,    /* E_cut: the largest |k+G|^2/2 of the sphere (not a proven bound) */
   CHEBFI_BOUND_RIGOROUS = 1  /* max(0, max K + max V + l_max(L^H D L)) / (1 + min(0, l_min(L^H Q L)))
@@ -100,13 +100,13 @@ int chebfi_set_vloc(chebfi_ctx* ctx, const double* vloc, int on_device);
  *     block sizes 1..64.
  *  D: host, the per-atom symmetric blocks of D_V concatenated, each n_a x n_a row-major.
  *  Q: host, same layout for D_S; NULL for S = I (norm-conserving).
- * Precomputes G = P^H P and the Woodbury core M = Q (I + G Q)^{-1} (Section 4.1) on the
+ * Precomputes G = P^H P and the Woodbury core M = Q (I + G Q)^{-1} (Section 5.1) on the
  * device.  Synchronises; returns CHEBFI_ERR_NOT_SPD if S is not positive definite. */
 int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t ldP,
                           int P_on_device, int natoms, const int32_t* proj_offsets,
                           const double* D, const double* Q);
 
-/* Section 4.3: lambda_+ for the filter.  Synchronises. */
+/* Section 5.3: lambda_+ for the filter.  Synchronises. */
 int chebfi_upper_bound(chebfi_ctx* ctx, int mode, double* lambda_hi);
 
 /* Algorithm 1: HY = H Y for nb bands.  prec selects FP64 or FP32 arithmetic (MIXED acts
@@ -150,10 +150,10 @@ int chebfi_cheb_filter_backward(chebfi_ctx* ctx, const void* Y0, const void* gYn
 
 /* Algorithm 1: SY = S Y = Y + P Q P^H Y (FP64). */
 int chebfi_apply_S(chebfi_ctx* ctx, const void* Y, void* SY, int64_t nb, int64_t ld, void* stream);
-/* Section 4.1 (Woodbury): out = S^{-1} X = X - P M P^H X (FP64). */
+/* Section 5.1 (Woodbury): out = S^{-1} X = X - P M P^H X (FP64). */
 int chebfi_apply_Sinv(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int64_t ld, void* stream);
 
-/* Section 4.1's own solve of the Woodbury reduced system (FP64): out = S^{-1} X = X - P q with
+/* Section 5.1's own solve of the Woodbury reduced system (FP64): out = S^{-1} X = X - P q with
  * A q = P^H X, A = D_S^{-1} + P^H P, found by iterative refinement q <- q + B^{-1}(P^H X - A q)
  * from q = 0, B = the atom-diagonal blocks of A.  It stops when every column has
  * ||P^H x - A q|| <= tol ||P^H x||, or after maxit updates; *iterations (nullable) receives the
@@ -167,7 +167,7 @@ int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t
 /* Algorithm 2's inner loop, in place on Y: psi^1 = (S^{-1}H psi^0 - c psi^0)/r,
  * psi^i = 2/r (S^{-1}H psi^{i-1} - c psi^{i-1}) - psi^{i-2}, i = 2..degree, with
  * c = (lambda_hi + lambda_lo)/2, r = (lambda_hi - lambda_lo)/2 and the projection-reuse
- * identity of Section 4.1.  Requires lambda_hi > lambda_lo. */
+ * identity of Section 5.1.  Requires lambda_hi > lambda_lo. */
 int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree,
                        double lambda_lo, double lambda_hi, int prec, void* stream);
 

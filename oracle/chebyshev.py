@@ -2,19 +2,19 @@
 
 Test infrastructure only.  Everything here follows the paper's order and notation:
 
-* ``cheb_T`` -- the scaled Chebyshev recurrence of Section 3.2:
+* ``cheb_T`` -- the scaled Chebyshev recurrence of Section 4.2:
   ``T_0 = 1``, ``T_1(x) = (x - c)/r``, ``T_{n+1}(x) = 2 (x - c)/r T_n(x) - T_{n-1}(x)``,
   ``c = (a + b)/2``, ``r = (b - a)/2``;
 * ``filter_plain`` -- the inner loop of Algorithm 2 with ``S^{-1} H`` applied as written
-  (``H`` by Algorithm 1, ``S^{-1}`` by the Woodbury formula of Section 4.1);
-* ``filter_reuse`` -- the same loop with the projection-reuse identity of Section 4.1,
+  (``H`` by Algorithm 1, ``S^{-1}`` by the Woodbury formula of Section 5.1);
+* ``filter_reuse`` -- the same loop with the projection-reuse identity of Section 5.1,
   ``P^H S^{-1} psi = P^H psi - (P^H P) q``, so ``P^H`` is applied once, before the loop;
 * ``bounds`` -- the first three steps of Algorithm 2 (maximum Rayleigh quotient for
-  ``lambda_-``; the kinetic upper bound of Section 4.3 for ``lambda_+``, or a rigorous bound);
+  ``lambda_-``; the kinetic upper bound of Section 5.3 for ``lambda_+``, or a rigorous bound);
 * ``rayleigh_ritz`` -- the last three steps of Algorithm 2 (subspace matrices
   ``H_Psi = Psi^H H Psi``, ``S_Psi = Psi^H S Psi``, dense generalized eigenproblem
   ``H_Psi X = S_Psi X Lambda``, rotation ``Psi <- Psi X``) after rescaling the columns
-  (Section 4.3 mentions the rescaling);
+  (Section 5.3 mentions the rescaling);
 * ``solve`` -- Algorithm 2 repeated for a number of sweeps.
 
 Readings of the paper (it leaves these open): degree ``n`` means ``n`` applications of
@@ -35,7 +35,7 @@ __all__ = [
 
 
 def cheb_T(n: int, x, a: float, b: float):
-    """T_n((x - c)/r) on the interval [a, b] by the recurrence of Section 3.2."""
+    """T_n((x - c)/r) on the interval [a, b] by the recurrence of Section 4.2."""
     c = 0.5 * (a + b)
     r = 0.5 * (b - a)
     x = np.asarray(x, dtype=np.float64)
@@ -63,7 +63,7 @@ def filter_plain(op: PWOperator, Y, degree: int, lam_lo: float, lam_hi: float):
 
 
 def _woodbury_reduced(op: PWOperator):
-    """(D_S^{-1} + P^H P): the reduced N_projs x N_projs matrix of Section 4.1."""
+    """(D_S^{-1} + P^H P): the reduced N_projs x N_projs matrix of Section 5.1."""
     sizes = np.diff(op.offsets)
     Dinv = np.zeros_like(op.Ds)
     o = 0
@@ -75,14 +75,14 @@ def _woodbury_reduced(op: PWOperator):
 
 def filter_reuse(op: PWOperator, Y, degree: int, lam_lo: float, lam_hi: float,
                  return_proj: bool = False):
-    """Algorithm 2's inner loop with the projection-reuse identity of Section 4.1.
+    """Algorithm 2's inner loop with the projection-reuse identity of Section 5.1.
 
     For one step with current iterate psi and its carried projections p = P^H psi:
       Z      = K psi + V_loc psi                      (local part of Algorithm 1)
       P^H H psi = P^H Z + G D_V p                     (G = P^H P, precomputed)
       q      = (D_S^{-1} + G)^{-1} P^H H psi          (Woodbury reduced solve)
       S^{-1} H psi = Z + P D_V p - P q
-      P^H S^{-1} H psi = P^H H psi - G q              (the identity of Section 4.1)
+      P^H S^{-1} H psi = P^H H psi - G q              (the identity of Section 5.1)
     and both psi and p follow the Chebyshev recurrence.
     """
     c = 0.5 * (lam_hi + lam_lo)
@@ -127,7 +127,7 @@ def rayleigh_quotients(op: PWOperator, Y):
 def upper_bound(op: PWOperator, mode: str = "paper") -> float:
     """Upper end lambda_+ of the filtered interval.
 
-    ``paper``: the kinetic bound of Section 4.3 (E_cut, here the largest |k+G|^2/2 of the
+    ``paper``: the kinetic bound of Section 5.3 (E_cut, here the largest |k+G|^2/2 of the
     sphere; the paper notes it is not a proven bound).
     ``rigorous``: max(0, max K + max V + max(0, l_max(L^H D_V L))) / (1 + min(0, l_min(L^H D_S L)))
     with P^H P = L L^H.  The nonzero eigenvalues of P X P^H are those of L^H X L, which

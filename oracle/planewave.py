@@ -116,7 +116,7 @@ class PWOperator:
         return Y + self.P @ (self.Ds @ self.projections(Y))
 
     def apply_Sinv(self, X):
-        """S^{-1} x by the Woodbury formula of Section 4.1:
+        """S^{-1} x by the Woodbury formula of Section 5.1:
         S^{-1} = I - P (D_S^{-1} + P^H P)^{-1} P^H.
 
         The reduced system is solved by a dense LU solve (the paper uses iterative
@@ -136,7 +136,7 @@ class PWOperator:
         return X - self.P @ q
 
     def apply_Sinv_refined(self, X, tol: float = 1e-12, maxit: int = 200):
-        """S^{-1} x with the reduced system of Section 4.1 solved the paper's way: iterative
+        """S^{-1} x with the reduced system of Section 5.1 solved the paper's way: iterative
         refinement q <- q + B^{-1} (b - A q) from q = 0 on A = D_S^{-1} + P^H P, b = P^H x,
         preconditioned by B = the per-atom diagonal blocks of A; it stops when every column
         has ||b - A q|| <= tol ||b||, or after maxit updates.
@@ -173,7 +173,7 @@ class PWOperator:
         """The convergence figures of the refinement above: (rho, kappa) with rho the spectral
         radius of I - B^{-1} A (the error shrinks by about rho per update; the iteration
         converges when rho < 1) and kappa = |mu|_max / |mu|_min over the eigenvalues mu of
-        B^{-1} A (the preconditioned condition number Section 4.1 reports)."""
+        B^{-1} A (the preconditioned condition number Section 5.1 reports)."""
         if self.Ds is None:
             return 0.0, 1.0
         sizes = np.diff(self.offsets)

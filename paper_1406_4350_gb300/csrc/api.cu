@@ -1,4 +1,4 @@
-// C ABI of libchebfi: context, setup (Section 2.1 operators, Section 4.1 Woodbury core),
+// C ABI of libchebfi: context, setup (Section 2.1 operators, Section 5.1 Woodbury core),
 // and the orchestration of Algorithm 2 (filter, Rayleigh-Ritz, sweeps) on the device.
 //
 // Internally every wavefunction block is kept in "column-sorted" plane-wave order (the
@@ -183,7 +183,7 @@ template <typename R> struct FilterBufs {
   cplx<R>*Ya, *Yb, *Z, *T, *pa, *pb, *pz, *pw, *pq;
 };
 
-// Algorithm 2's inner loop with the projection-reuse identity of Section 4.1, in place on
+// Algorithm 2's inner loop with the projection-reuse identity of Section 5.1, in place on
 // Y (sorted, ld = npw, its buffer is bufs.Ya on entry).  Returns the buffer holding Y_n.
 template <typename R>
 cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb, int degree, double lo, double hi,
@@ -530,7 +530,7 @@ double rigorous_bound(chebfi_ctx* ctx) {
 
 
 // ---------------------------------------------------------------- Woodbury by refinement
-// Section 4.1 solves the reduced system A q = P^H x, A = D_S^{-1} + P^H P, by iterative
+// Section 5.1 solves the reduced system A q = P^H x, A = D_S^{-1} + P^H P, by iterative
 // refinement preconditioned with the atom-diagonal blocks B of A:
 //   q <- q + B^{-1} (P^H x - A q),  starting from q = 0,
 // then S^{-1} x = x - P q.  A and B^{-1} are formed on first use.
@@ -629,7 +629,7 @@ void ensure_refine(chebfi_ctx* ctx, cudaStream_t st) {
 // 2 ceil(n/s) + s + 4 blocks (s = ceil(sqrt n) by default) instead of n + 4; the extra work
 // is at most n forward steps.
 
-// S^{-1} X (Section 4.1, Woodbury with the precomputed core M) into out; X itself when S = I.
+// S^{-1} X (Section 5.1, Woodbury with the precomputed core M) into out; X itself when S = I.
 template <typename R>
 const cplx<R>* sinv_sorted(chebfi_ctx* ctx, const cplx<R>* X, cplx<R>* out, cplx<R>* pa, cplx<R>* pb, int64_t nb,
                            cudaStream_t st) {
@@ -1055,7 +1055,7 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
     CHEBFI_CUDA(cudaMemcpy(ctx->d_P.p, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
   }
   DevBuf<double2>* ws = &ctx->w.splitk;
-  // G = P^H P (Section 4.1, precomputed once)
+  // G = P^H P (Section 5.1, precomputed once)
   ctx->d_G.alloc((size_t)nproj * nproj);
   gemm<double>(true, false, nproj, nproj, npw, 1.0, ctx->d_P.p, npw, ctx->d_P.p, npw, 0.0, ctx->d_G.p, nproj, st, ws);
   hermitize(nproj, ctx->d_G.p, nproj, st);
@@ -1200,7 +1200,7 @@ int chebfi_apply_Sinv(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   gather_to_Ya(ctx, X, nb, ld, st);
   if (ctx->paw) {
-    // S^{-1} x = x - P M P^H x (Section 4.1)
+    // S^{-1} x = x - P M P^H x (Section 5.1)
     const size_t np = (size_t)nq * nb;
     w.pa.alloc(np);
     w.pb.alloc(np);

@@ -492,7 +492,7 @@ template <typename R> void ensure_ws(chebfi_batch* bt) {
 }
 
 // Algorithm 2's filter of degree n for all k-points (the same steps as the single-problem
-// filter with projection reuse, Section 4.1); launches on st.  Counter slots: 6 per step + 1.
+// filter with projection reuse, Section 5.1); launches on st.  Counter slots: 6 per step + 1.
 template <typename R>
 void batch_filter_body(chebfi_batch* bt, int degree, cudaStream_t st) {
   using C = cplx<R>;

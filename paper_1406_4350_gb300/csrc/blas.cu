@@ -1,6 +1,6 @@
 // Elementwise and reduction kernels of the filter and of Rayleigh-Ritz: the
 // block-diagonal coefficient matrices D_V, D_S of Section 2.1, the Chebyshev three-term
-// combination of Section 3.2, reorderings between the caller's plane-wave order and the
+// combination of Section 4.2, reorderings between the caller's plane-wave order and the
 // column-sorted order of the FFT, column dot products and residual norms.
 #include <algorithm>
 

@@ -1,5 +1,5 @@
 // Dense FP64 linear algebra on the device for the Rayleigh-Ritz step of Algorithm 2 and
-// the Woodbury core of Section 4.1: blocked Cholesky, triangular solve, and a cyclic
+// the Woodbury core of Section 5.1: blocked Cholesky, triangular solve, and a cyclic
 // Jacobi eigensolver for complex Hermitian matrices.
 //
 // Jacobi: each rotation removes one off-diagonal entry a_pq = |a_pq| e^{i phi} of the

@@ -1,7 +1,7 @@
 // Complex GEMM on the CUDA cores (FP64 DFMA or FP32 FFMA), C = alpha op(A) op(B) + beta C.
 //
 // Used for the FP64 and FP32 forms of the projector products P^H psi and P W
-// (Algorithm 1, Section 4.1), the Woodbury core products, and the subspace matrices and
+// (Algorithm 1, Section 5.1), the Woodbury core products, and the subspace matrices and
 // rotations of Algorithm 2.  64 x 64 output tiles, 256 threads, 4 x 4 complex outputs per
 // thread; split-K with a deterministic second pass when the output has too few tiles to
 // fill the 152 SMs.

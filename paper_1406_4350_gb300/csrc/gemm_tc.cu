@@ -7,7 +7,7 @@
 // (the lo * lo term is below the FP32 accumulation error), which carries about 16
 // significant bits per operand instead of bf16's 8.  D and C are FP32 column-major.
 //
-// Complex projector products of Section 4.1 map onto it through the real embedding of
+// Complex projector products of Section 5.1 map onto it through the real embedding of
 // interleaved complex data: with z stored as (re, im) pairs, P^H z and P w become real
 // GEMMs whose A matrices (built once from P at setup) hold the 2 x 2 blocks
 // [[Re, Im], [-Im, Re]] and [[Re, -Im], [Im, Re]].

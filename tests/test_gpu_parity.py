@@ -336,7 +336,7 @@ def test_paw48_forms_agree_after_convergence():
 
 # ----------------------------------------------------------------------------- Woodbury by refinement
 def test_apply_Sinv_refined_matches_oracle_and_direct():
-    """Section 4.1's iterative refinement on the device: the same S^{-1} x as the direct
+    """Section 5.1's iterative refinement on the device: the same S^{-1} x as the direct
     Woodbury form, in the same number of updates as the oracle's refinement."""
     from paper_1406_4350_gb300.chebfi import ChebFI, fortran
     cell = config_cell("paw48", nbands=16)

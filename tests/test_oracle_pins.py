@@ -232,7 +232,7 @@ def test_jacobi_degenerate_and_diagonal():
 
 
 def test_filter_reuse_equals_plain_and_projections_track():
-    """The projection-reuse identity of Section 4.1 changes no result: the carried
+    """The projection-reuse identity of Section 5.1 changes no result: the carried
     projections equal freshly computed P^H psi."""
     cell = _tiny(N=12, natoms=3, nb=6)
     op = pw.PWOperator.from_cell(cell)
@@ -335,7 +335,7 @@ def test_pins_catch_planted_mistakes(monkeypatch, mutation, pins):
 
 
 def test_woodbury_iterative_refinement_reaches_the_direct_solve():
-    """Section 4.1's solve of the reduced system by block-diagonally preconditioned
+    """Section 5.1's solve of the reduced system by block-diagonally preconditioned
     iterative refinement converges to the direct Woodbury result (and hence to S^{-1} x)."""
     cell = _tiny(N=12, natoms=3)
     op = pw.PWOperator.from_cell(cell)
