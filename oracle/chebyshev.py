@@ -15,7 +15,10 @@ Test infrastructure only.  Everything here follows the paper's order and notatio
   ``H_Psi = Psi^H H Psi``, ``S_Psi = Psi^H S Psi``, dense generalized eigenproblem
   ``H_Psi X = S_Psi X Lambda``, rotation ``Psi <- Psi X``) after rescaling the columns
   (Section 5.3 mentions the rescaling);
-* ``solve`` -- Algorithm 2 repeated for a number of sweeps.
+* ``solve`` -- Algorithm 2 repeated for a number of sweeps;
+* ``adaptive_degrees`` / ``filter_adaptive`` -- locking with a per-band degree (Section 5.4):
+  the degree of band i is the smallest n with ``||r_i|| / |T_n((lambda_i - c)/r)| <= tol``,
+  0 (locked) when the residual already meets the tolerance.
 
 Readings of the paper (it leaves these open): degree ``n`` means ``n`` applications of
 ``S^{-1} H`` (``psi^1`` uses ``1/r``, later steps ``2/r``); the recurrence is unscaled;
@@ -30,7 +33,8 @@ from .planewave import PWOperator
 
 __all__ = [
     "cheb_T", "filter_plain", "filter_reuse", "rayleigh_quotients", "upper_bound", "bounds",
-    "rayleigh_ritz", "residuals", "residual_bound", "solve",
+    "rayleigh_ritz", "residuals", "residual_bound", "solve", "adaptive_degrees", "filter_adaptive",
+    "solve_locked",
 ]
 
 
@@ -216,3 +220,59 @@ def solve(op: PWOperator, Y0, degree: int, sweeps: int, mode: str = "paper", lam
     if history:
         out["hist"] = hist
     return out
+
+
+def adaptive_degrees(ritz, resid, lam_lo: float, lam_hi: float, tol: float, max_degree: int):
+    """Per-band polynomial degrees for locking (Section 5.4).
+
+    One Chebyshev iteration of degree n scales the eigencomponent of eigenvalue lambda_i by
+    T_n((lambda_i - c)/r) while unwanted components grow by at most 1, so the residual of
+    band i after filter + Rayleigh-Ritz is estimated by ||r_i|| / |T_n((lambda_i - c)/r)|
+    (the paper prints lambda_1 in the argument; the per-band reading lambda_i is the one that
+    gives each band its own degree).  Band i gets the smallest n in 1..max_degree meeting
+    tol, max_degree if none does, and 0 (locked, not filtered) if ||r_i|| <= tol already.
+    T_n is evaluated by the recurrence of Section 4.2 (``cheb_T``).
+    """
+    out = np.zeros(len(ritz), dtype=np.int64)
+    for i, (lam, res) in enumerate(zip(ritz, resid)):
+        if res <= tol:
+            continue
+        n_i = max_degree
+        for n in range(1, max_degree + 1):
+            if res <= tol * abs(float(cheb_T(n, lam, lam_lo, lam_hi))):
+                n_i = n
+                break
+        out[i] = n_i
+    return out
+
+
+def filter_adaptive(op: PWOperator, Y, degrees, lam_lo: float, lam_hi: float):
+    """Algorithm 2's inner loop with band i filtered to its own degree degrees[i]."""
+    Y = np.array(Y, dtype=np.complex128)
+    out = Y.copy()
+    for n in sorted(set(int(d) for d in degrees)):
+        cols = [i for i, d in enumerate(degrees) if int(d) == n]
+        out[:, cols] = filter_plain(op, Y[:, cols], n, lam_lo, lam_hi)
+    return out
+
+
+def solve_locked(op: PWOperator, Y, max_degree: int, sweeps: int, tol: float, mode: str = "paper",
+                 lam_hi=None):
+    """Algorithm 2 with locking (Section 5.4): after the first full-degree sweep, every sweep
+    filters band i to the degree ``adaptive_degrees`` predicts from its Ritz value and
+    residual (the filter interval being that sweep's [lambda_-, lambda_+]).  Returns
+    (Y, eigenvalues, residuals, the degrees used in each sweep)."""
+    _, lam_hi, _, _ = bounds(op, Y, mode, lam_hi)
+    Psi = np.array(Y, dtype=np.complex128)
+    lam_lo = float(rayleigh_quotients(op, Psi).max())
+    degrees = np.full(Psi.shape[1], max_degree, dtype=np.int64)
+    used = []
+    w = res = None
+    for _ in range(sweeps):
+        Psi = filter_adaptive(op, Psi, degrees, lam_lo, lam_hi)
+        used.append(degrees.copy())
+        w, Psi = rayleigh_ritz(op, Psi)
+        res = residuals(op, Psi, w)
+        lam_lo = float(w.max())
+        degrees = adaptive_degrees(w, res, lam_lo, lam_hi, tol, max_degree)
+    return Psi, w, res, used
