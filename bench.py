@@ -200,7 +200,10 @@ def run_extra(args):
     refine: S^{-1} by Section 5.1's iterative refinement against the direct Woodbury form on
     the benchmark workload's first 256 bands.
     kpoints: the batched k-point filter (64 k-points of a 48^3 PAW cell, spheres of 3000 to
-    12000 plane waves, 128 bands each, FP32, degree 8) against one filter call per k-point."""
+    12000 plane waves, 128 bands each, FP32, degree 8) against one filter call per k-point.
+    locking: the 48^3 PAW cell (8025 plane waves, 256 bands), 20 sweeps with and without
+    locking: FP64 form at degree 10 and residual 1e-9, mixed form at degree 8 (degree 10 trips
+    its overflow guard there) and residual 3e-5, above its floor; time, band-applies."""
     import numpy as np
     import torch
     from paper_1406_4350_gb300 import build as b
@@ -231,6 +234,36 @@ def run_extra(args):
                 "config": {"workload": "paw48: 48^3 grid, %d plane waves, %d bands, %d projectors, PAW, degree %d, "
                                        "checkpoints every ceil(sqrt(degree))" % (cell.npw, cell.nbands, cell.nproj, deg)},
                 "forms": out}
+    elif args.task == "locking":
+        from paper_1406_4350_gb300 import MIXED
+        cell = config_cell("paw48")
+        g = ChebFI.from_cell(cell)
+        hi = g.upper_bound(BOUND_RIGOROUS)
+        k75 = (3 * cell.nbands) // 4
+        forms = {}
+        # (form, degree, lock tolerance): the tolerance sits above each form's residual floor
+        for fname, p, deg, tol in (("f64", F64, 10, 1e-9), ("mixed", MIXED, 8, 3e-5)):
+            res = {}
+            for name, t in (("full_degree", 0.0), ("locking", tol)):
+                Y = fortran(cell.Y0)
+                g.solve(Y.clone(), degree=deg, sweeps=1, prec=p, lambda_hi=hi)  # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ev, rs = g.solve(Y, degree=deg, sweeps=20, prec=p, lambda_hi=hi, lock_tol=t)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                sw, ap = g.solve_stats()
+                res[name] = {"s": dt, "sweeps": sw, "band_applies": ap,
+                             "max_resid_lowest_75pct": float(rs[:k75].max()), "evals": ev.cpu().numpy()}
+            dev = float(np.abs(res["locking"]["evals"][:k75] - res["full_degree"]["evals"][:k75]).max())
+            for v in res.values():
+                v.pop("evals")
+            forms[fname] = {"degree": deg, "lock_tol": tol, "runs": res, "max_eval_diff_lowest_75pct": dev}
+        line = {"metric": "locking: band-H-applications and solve time with and without locking", "unit": "s",
+                "value": forms["f64"]["runs"]["locking"]["s"], "dtype": "f64",
+                "config": {"workload": "paw48: 48^3 grid, %d plane waves, %d bands, PAW, 20 sweeps"
+                                       % (cell.npw, cell.nbands)},
+                "forms": forms}
     elif args.task == "kpoints":
         from paper_1406_4350_gb300.chebfi import ChebFIBatch
         from synth import kpoint_cells
@@ -295,7 +328,7 @@ def main():
     ap.add_argument("--ref-bands", type=int, default=4)
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
-    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints"],
+    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking"],
                     help="filter: the benchmark; backward / refine: the differentiation and the "
                          "refinement-Woodbury measurements (their own JSON line)")
     args = ap.parse_args()

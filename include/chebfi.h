@@ -69,6 +69,8 @@ typedef struct {
   int prec;            /* chebfi_prec of the filter */
   int bound_mode;      /* chebfi_bound_mode, used when lambda_hi <= lambda_lo estimate */
   double lambda_hi;    /* > 0: fixed lambda_+; <= 0: take it from bound_mode */
+  double tol;          /* locking tolerance on ||H y - lambda S y|| (used when lock != 0) */
+  int lock;            /* 1: locking with per-band degrees after the first sweep (Section 5.4) */
 } chebfi_params;
 
 /* Create a context on CUDA device `device` (made current on the calling thread).
@@ -171,6 +173,26 @@ int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t
 int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree,
                        double lambda_lo, double lambda_hi, int prec, void* stream);
 
+/* Locking (Section 5.4), in place on Y: band j filtered to its own degree degrees[j] (host
+ * array of nb ints in 0..1000; 0 leaves the band as it is) on [lambda_lo, lambda_hi], i.e.
+ * chebfi_cheb_filter applied band by band.  Bands are reordered internally by decreasing
+ * degree so each Chebyshev step runs on the still-active prefix of the block. */
+int chebfi_cheb_filter_adaptive(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, const int32_t* degrees,
+                                double lambda_lo, double lambda_hi, int prec, void* stream);
+
+/* Section 5.4's a-priori degree (host arrays, no context): the residual of band i after one
+ * filter of degree n and Rayleigh-Ritz is estimated as resid[i] / |T_n((ritz[i] - c)/r)|,
+ * c, r from [lambda_lo, lambda_hi]; degrees[i] = the smallest n in 1..max_degree with the
+ * estimate <= tol (T_n by the three-term recurrence), max_degree if none, 0 if
+ * resid[i] <= tol.  The paper prints lambda_1 in T_n's argument; each band's own Ritz
+ * value is used so that each band gets its own degree. */
+int chebfi_adaptive_degrees(const double* ritz, const double* resid, int64_t nb, double lambda_lo,
+                            double lambda_hi, double tol, int max_degree, int32_t* degrees);
+
+/* Sweeps performed by the last chebfi_solve on ctx and the band-H-applications of its
+ * filters (sum over sweeps of the bands' degrees). */
+int chebfi_solve_stats(const chebfi_ctx* ctx, int* sweeps_done, int64_t* band_applies);
+
 /* S-orthonormalisation by Cholesky-QR (FP64): G_Y = Y^H S Y = L L^H, Y <- Y L^{-H}.
  * Synchronises; CHEBFI_ERR_NOT_SPD if G_Y is not positive definite. */
 int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream);
@@ -189,7 +211,11 @@ int chebfi_rayleigh_quotients(chebfi_ctx* ctx, const void* Y, double* rq, int64_
 
 /* Algorithm 2 repeated params->sweeps times on Y (in place): lambda_- = max Rayleigh
  * quotient, lambda_+ from params, filter, Rayleigh-Ritz.  evals/resid as in
- * chebfi_rayleigh_ritz.  Synchronises. */
+ * chebfi_rayleigh_ritz.  With params->lock (Section 5.4), the first sweep uses
+ * params->degree for every band and each later sweep gives band i the degree
+ * chebfi_adaptive_degrees predicts for params->tol from its Ritz value and residual (at
+ * most params->degree; 0 = locked, not filtered, still in the Rayleigh-Ritz space); the
+ * solve stops early when every band is locked.  Synchronises. */
 int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb, int64_t ld,
                  const chebfi_params* params, void* stream);
 

@@ -22,7 +22,7 @@ BOUND_PAPER, BOUND_RIGOROUS = 0, 1
 
 class Params(ctypes.Structure):
     _fields_ = [("degree", c_int), ("sweeps", c_int), ("prec", c_int), ("bound_mode", c_int),
-                ("lambda_hi", c_double)]
+                ("lambda_hi", c_double), ("tol", c_double), ("lock", c_int)]
 
 
 SIGNATURES = {
@@ -46,6 +46,10 @@ SIGNATURES = {
     "chebfi_batch_kernel_launches": (c_int64, [c_void_p]),
     "chebfi_batch_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "chebfi_batch_cheb_filter": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
+    "chebfi_cheb_filter_adaptive": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_double, c_double,
+                                            c_int, c_void_p]),
+    "chebfi_adaptive_degrees": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_double, c_double, c_int, c_void_p]),
+    "chebfi_solve_stats": (c_int, [c_void_p, c_void_p, c_void_p]),
     "chebfi_apply_Sinv_refined": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_double, c_int,
                                           c_void_p, c_void_p]),
     "chebfi_cheb_filter_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,

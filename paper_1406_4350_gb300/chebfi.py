@@ -252,15 +252,46 @@ class ChebFI:
         return rq
 
     def solve(self, Y, degree: int, sweeps: int, prec: int = F64, bound_mode: int = BOUND_PAPER,
-              lambda_hi: float = 0.0):
-        """Algorithm 2 repeated `sweeps` times in place on Y; returns (evals, residual norms)."""
+              lambda_hi: float = 0.0, lock_tol: float = 0.0):
+        """Algorithm 2 repeated `sweeps` times in place on Y; returns (evals, residual norms).
+        lock_tol > 0 turns on locking with per-band degrees (Section 5.4)."""
         y, nb, ld = _block(Y)
         ev = torch.empty(nb, dtype=torch.float64, device=Y.device)
         rs = torch.empty(nb, dtype=torch.float64, device=Y.device)
-        p = Params(degree, sweeps, prec, bound_mode, float(lambda_hi))
+        p = Params(degree, sweeps, prec, bound_mode, float(lambda_hi), float(lock_tol), 1 if lock_tol > 0 else 0)
         self._check(self.lib.chebfi_solve(self.h, y, ctypes.c_void_p(ev.data_ptr()), ctypes.c_void_p(rs.data_ptr()),
                                           nb, ld, ctypes.byref(p), _stream()))
         return ev, rs
+
+    def solve_stats(self):
+        """(sweeps performed, band-H-applications of the filters) of the last solve."""
+        sw = ctypes.c_int(0)
+        ap = ctypes.c_int64(0)
+        self._check(self.lib.chebfi_solve_stats(self.h, ctypes.byref(sw), ctypes.byref(ap)))
+        return sw.value, ap.value
+
+    def cheb_filter_adaptive(self, Y, degrees, lambda_lo: float, lambda_hi: float, prec: int = F64):
+        """In place on Y: band j filtered to degree degrees[j] (Section 5.4); returns Y."""
+        y, nb, ld = _block(Y)
+        d = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32))
+        if d.shape != (nb,):
+            raise ValueError("one degree per band")
+        self._check(self.lib.chebfi_cheb_filter_adaptive(self.h, y, nb, ld, ctypes.c_void_p(d.ctypes.data),
+                                                         lambda_lo, lambda_hi, prec, _stream()))
+        return Y
+
+    @staticmethod
+    def adaptive_degrees(ritz, resid, lambda_lo: float, lambda_hi: float, tol: float, max_degree: int):
+        """Section 5.4's per-band degree for a residual tolerance (host computation)."""
+        lib = _lib.load()
+        r = np.ascontiguousarray(np.asarray(ritz, dtype=np.float64))
+        s_ = np.ascontiguousarray(np.asarray(resid, dtype=np.float64))
+        out = np.zeros(r.shape[0], dtype=np.int32)
+        rc = lib.chebfi_adaptive_degrees(ctypes.c_void_p(r.ctypes.data), ctypes.c_void_p(s_.ctypes.data), r.shape[0],
+                                         lambda_lo, lambda_hi, tol, max_degree, ctypes.c_void_p(out.ctypes.data))
+        if rc != 0:
+            raise ChebFIError(rc, "chebfi_adaptive_degrees: bad arguments")
+        return out
 
     def sync_status(self):
         self._check(self.lib.chebfi_sync_status(self.h))

@@ -179,6 +179,15 @@ void apply_H_sorted(chebfi_ctx* ctx, const cplx<R>* Y, cplx<R>* HY, cplx<R>* p, 
   }
 }
 
+// Locking (Section 5.4): bands [m_next, m) have reached their own degree; their iterate, in
+// the buffer `cur`, goes to its column of the result buffer, which later steps leave alone.
+template <typename R>
+void keep_finished(int64_t npw, const cplx<R>* cur, cplx<R>* result, int64_t m_next, int64_t m, cudaStream_t st) {
+  if (cur == result || m <= m_next) return;
+  CHEBFI_CUDA(cudaMemcpyAsync(result + m_next * npw, cur + m_next * npw, sizeof(cplx<R>) * npw * (m - m_next),
+                              cudaMemcpyDeviceToDevice, st));
+}
+
 template <typename R> struct FilterBufs {
   cplx<R>*Ya, *Yb, *Z, *T, *pa, *pb, *pz, *pw, *pq;
 };
@@ -186,15 +195,16 @@ template <typename R> struct FilterBufs {
 // Algorithm 2's inner loop with the projection-reuse identity of Section 5.1, in place on
 // Y (sorted, ld = npw, its buffer is bufs.Ya on entry).  Returns the buffer holding Y_n.
 template <typename R>
-cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb, int degree, double lo, double hi,
-                       cudaStream_t st) {
+cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb0, int degree, double lo, double hi,
+                       cudaStream_t st, const int64_t* active = nullptr) {
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
   cplx<R>*cur = b.Ya, *prev = b.Yb, *pcur = b.pa, *pprev = b.pb;
   if (nq > 0)
-    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st, Ops<R>::ws(ctx),
-            "gemm_PhY");
+    gemm<R>(true, false, nq, active ? active[0] : nb0, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st,
+            Ops<R>::ws(ctx), "gemm_PhY");
   for (int k = 0; k < degree; ++k) {
+    const int64_t nb = active ? active[k] : nb0;  // bands still being filtered (a prefix)
     const double a = (k == 0 ? 1.0 : 2.0) / r;
     const double bp = k == 0 ? 0.0 : 1.0;
     // Z = (K + V_loc) Y_k and T = a (Z - c Y_k) - bp Y_{k-1}, T written over Y_{k-1}
@@ -233,8 +243,9 @@ cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb, int degree,
     }
     std::swap(cur, prev);
     std::swap(pcur, pprev);
+    if (active) keep_finished<R>(npw, cur, b.Ya, k + 1 < degree ? active[k + 1] : 0, nb, st);
   }
-  return cur;
+  return active ? b.Ya : cur;
 }
 
 // bf16 (hi, lo) embeddings of P^H, P, G and M for the tensor-core GEMMs (first use only).
@@ -251,8 +262,9 @@ void ensure_tc(chebfi_ctx* ctx, cudaStream_t st) {
 // Mixed form of the filter: FP32 iterates and FFT, projector GEMMs on the tensor cores
 // with split bf16 operands.  Same steps as filter_sorted; Y_0 and the result are the FP32
 // buffers b.Ya / returned pointer.
-float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb, int degree, double lo, double hi,
-                     cudaStream_t st) {
+float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb0, int degree, double lo, double hi,
+                     cudaStream_t st, const int64_t* active = nullptr) {
+  const int64_t nb = active ? active[0] : nb0;
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
   Work& w = ctx->w;
@@ -268,6 +280,7 @@ float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb, int degre
             "tc_gemm_PhY");
   }
   for (int k = 0; k < degree; ++k) {
+    const int64_t nb = active ? active[k] : nb0;  // bands still being filtered (a prefix)
     const double a = (k == 0 ? 1.0 : 2.0) / r;
     const double bp = k == 0 ? 0.0 : 1.0;
     LocalEpi<float> ep;
@@ -311,8 +324,9 @@ float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb, int degre
     }
     std::swap(cur, prev);
     std::swap(pcur, pprev);
+    if (active) keep_finished<float>(npw, cur, b.Ya, k + 1 < degree ? active[k + 1] : 0, nb, st);
   }
-  return cur;
+  return active ? b.Ya : cur;
 }
 
 void ensure_filter_ws(chebfi_ctx* ctx, int64_t nb, int prec) {
@@ -357,6 +371,68 @@ void filter_on_Ya(chebfi_ctx* ctx, int64_t nb, int degree, double lo, double hi,
     float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lo, hi, st)
                                        : filter_sorted<float>(ctx, b, nb, degree, lo, hi, st);
     convert(npw, nb, out, npw, w.Ya.p, npw, st);
+  }
+}
+
+
+// Locking (Section 5.4): band j of the sorted FP64 block w.Ya filtered to its own degree
+// deg[j].  Bands are reordered by decreasing degree so that the bands still filtered at
+// step k form a prefix of the block; each step then runs on that prefix only.
+void filter_on_Ya_adaptive(chebfi_ctx* ctx, int64_t nb, const std::vector<int>& deg, double lo, double hi, int prec,
+                           cudaStream_t st) {
+  const int dmax = nb ? *std::max_element(deg.begin(), deg.end()) : 0;
+  if (dmax == 0) return;
+  std::vector<int32_t> order(nb);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
+  std::vector<int64_t> active(dmax, 0);
+  for (int k = 0; k < dmax; ++k)
+    for (int64_t j = 0; j < nb; ++j) active[k] += deg[j] > k ? 1 : 0;
+  ensure_filter_ws(ctx, nb, prec);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw;
+  w.Yc.alloc((size_t)npw * nb);
+  w.order.upload(order.data(), nb, st);
+  permute_cols(npw, nb, w.order.p, w.Ya.p, w.Yc.p, false, st);
+  if (prec == CHEBFI_F64) {
+    FilterBufs<double> b{w.Yc.p, w.Yb.p, w.Z.p, w.T1.p, w.pa.p, w.pb.p, w.pz.p, w.pw.p, w.pq.p};
+    filter_sorted<double>(ctx, b, nb, dmax, lo, hi, st, active.data());
+  } else {
+    convert(npw, nb, w.Yc.p, npw, w.fYa.p, npw, st);
+    FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
+    if (prec == CHEBFI_MIXED) filter_mixed(ctx, b, nb, dmax, lo, hi, st, active.data());
+    else filter_sorted<float>(ctx, b, nb, dmax, lo, hi, st, active.data());
+    // only the filtered prefix comes back: locked bands keep their FP64 values untouched
+    convert(npw, active[0], w.fYa.p, npw, w.Yc.p, npw, st);
+  }
+  permute_cols(npw, nb, w.order.p, w.Yc.p, w.Ya.p, true, st);
+}
+
+// Section 5.4's degree estimate: the smallest n in 1..max_degree with
+// ||r_i|| <= tol |T_n((lambda_i - c)/r)|, max_degree if none, 0 when ||r_i|| <= tol.
+void degrees_for_tolerance(const double* ritz, const double* resid, int64_t nb, double lo, double hi, double tol,
+                           int max_degree, int* deg) {
+  const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
+  for (int64_t i = 0; i < nb; ++i) {
+    if (resid[i] <= tol) {
+      deg[i] = 0;
+      continue;
+    }
+    const double x = (ritz[i] - c) / r;
+    double t_prev = 1.0, t = x;  // T_0, T_1 by the recurrence of Section 4.2
+    int n_i = max_degree;
+    for (int n = 1; n <= max_degree; ++n) {
+      if (n > 1) {
+        const double t_next = 2.0 * x * t - t_prev;
+        t_prev = t;
+        t = t_next;
+      }
+      if (resid[i] <= tol * std::fabs(t)) {
+        n_i = n;
+        break;
+      }
+    }
+    deg[i] = n_i;
   }
 }
 
@@ -1229,6 +1305,46 @@ int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int deg
   API_END(ctx)
 }
 
+int chebfi_cheb_filter_adaptive(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, const int32_t* degrees,
+                                double lambda_lo, double lambda_hi, int prec, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || degrees, CHEBFI_ERR_ARG, "null degrees");
+  CHEBFI_REQUIRE(std::isfinite(lambda_lo) && std::isfinite(lambda_hi) && lambda_hi > lambda_lo, CHEBFI_ERR_ARG,
+                 "need finite lambda_lo < lambda_hi");
+  CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
+  std::vector<int> deg(nb);
+  for (int64_t j = 0; j < nb; ++j) {
+    CHEBFI_REQUIRE(degrees[j] >= 0 && degrees[j] <= 1000, CHEBFI_ERR_ARG, "degree out of range");
+    deg[j] = degrees[j];
+  }
+  if (nb == 0 || *std::max_element(deg.begin(), deg.end()) == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  filter_on_Ya_adaptive(ctx, nb, deg, lambda_lo, lambda_hi, prec, st);
+  scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  API_END(ctx)
+}
+
+int chebfi_adaptive_degrees(const double* ritz, const double* resid, int64_t nb, double lambda_lo, double lambda_hi,
+                            double tol, int max_degree, int32_t* degrees) {
+  if (nb < 0 || (nb > 0 && (!ritz || !resid || !degrees)) || !(tol > 0.0) || max_degree < 1 ||
+      !(lambda_hi > lambda_lo) || !std::isfinite(lambda_lo) || !std::isfinite(lambda_hi))
+    return CHEBFI_ERR_ARG;
+  std::vector<int> d(nb);
+  degrees_for_tolerance(ritz, resid, nb, lambda_lo, lambda_hi, tol, max_degree, d.data());
+  for (int64_t i = 0; i < nb; ++i) degrees[i] = d[i];
+  return CHEBFI_OK;
+}
+
+int chebfi_solve_stats(const chebfi_ctx* ctx, int* sweeps_done, int64_t* band_applies) {
+  if (!ctx) return CHEBFI_ERR_ARG;
+  if (sweeps_done) *sweeps_done = ctx->last_sweeps;
+  if (band_applies) *band_applies = ctx->last_applies;
+  return CHEBFI_OK;
+}
+
 int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream) {
   API_BEGIN(ctx)
   require_ready(ctx);
@@ -1298,17 +1414,43 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
   rq_sorted(ctx, ctx->w.Ya.p, nb, ctx->w.dvec3.p, st);
   double lo = host_max(ctx, ctx->w.dvec3.p, nb, st);
   double l1 = host_max(ctx, ctx->w.dvec3.p, nb, st, true);
-  for (int s = 0; s < params->sweeps; ++s) {
+  // locking (Section 5.4): after a full-degree sweep, each band gets the degree its residual
+  // estimate needs for params->tol; converged bands are not filtered
+  const bool lock = params->lock != 0;
+  CHEBFI_REQUIRE(!lock || params->tol > 0.0, CHEBFI_ERR_ARG, "locking needs tol > 0");
+  std::vector<int> deg(nb, params->degree);
+  double* res = resid;
+  if (lock && !res) {
+    ctx->w.dvec2.alloc(nb);
+    res = ctx->w.dvec2.p;
+  }
+  int dmax = params->degree;
+  int sweeps_done = 0;
+  int64_t applies = 0;
+  for (int s = 0; s < params->sweeps && dmax > 0; ++s) {
     CHEBFI_REQUIRE(hi > lo, CHEBFI_ERR_ARG, "upper bound below the largest Rayleigh quotient");
     const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
-    if (cheb_T_abs(params->degree, (l1 - c) / r) >= 1.0 / (100.0 * eps))
+    if (cheb_T_abs(dmax, (l1 - c) / r) >= 1.0 / (100.0 * eps))
       throw Error{CHEBFI_ERR_FILTER_OVERFLOW, "T_n((lambda_1 - c)/r) exceeds 1/(100 eps) of the filter precision"};
-    filter_on_Ya(ctx, nb, params->degree, lo, hi, params->prec, st);
+    if (lock && s > 0) filter_on_Ya_adaptive(ctx, nb, deg, lo, hi, params->prec, st);
+    else filter_on_Ya(ctx, nb, params->degree, lo, hi, params->prec, st);
+    for (int64_t j = 0; j < nb; ++j) applies += (lock && s > 0) ? deg[j] : params->degree;
+    sweeps_done = s + 1;
     ctx->w.tmp.alloc(ctx->w.Ya.n);
-    rr_on_Ya(ctx, nb, evals, resid, st);
+    rr_on_Ya(ctx, nb, evals, res, st);
     lo = host_max(ctx, evals, nb, st);
     l1 = host_max(ctx, evals, nb, st, true);
+    if (lock) {
+      std::vector<double> he(nb), hr(nb);
+      CHEBFI_CUDA(cudaMemcpyAsync(he.data(), evals, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+      CHEBFI_CUDA(cudaMemcpyAsync(hr.data(), res, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+      CHEBFI_CUDA(cudaStreamSynchronize(st));
+      degrees_for_tolerance(he.data(), hr.data(), nb, lo, hi, params->tol, params->degree, deg.data());
+      dmax = *std::max_element(deg.begin(), deg.end());
+    }
   }
+  ctx->last_sweeps = sweeps_done;
+  ctx->last_applies = applies;
   scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
   CHEBFI_CUDA(cudaStreamSynchronize(st));
   API_END(ctx)

@@ -179,6 +179,16 @@ __global__ void k_hermitize(int64_t n, double2* A, int64_t lda) {
   A[j + i * lda] = make_double2(h.x, -h.y);
 }
 
+__global__ void k_permute_cols(int64_t m, const int32_t* __restrict__ order, const double2* __restrict__ src,
+                               double2* __restrict__ dst, int inverse) {
+  const int64_t j = blockIdx.y;
+  const int64_t o = order[j];
+  const double2* s = src + (inverse ? j : o) * m;
+  double2* d = dst + (inverse ? o : j) * m;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
 // one thread per (projector i, band b): out_ib = sum_j B_a[i - o, j - o] p_jb over i's atom block
 __global__ void k_blockdiag_apply_c(int64_t nproj, int64_t nb, const int32_t* __restrict__ atom_of,
                                     const int32_t* __restrict__ offs, const int64_t* __restrict__ cblk_off,
@@ -350,6 +360,13 @@ void blockdiag_apply_c(const chebfi_ctx* ctx, const double2* Bblk, const int64_t
                 k_blockdiag_apply_c<<<nblocks(ctx->nproj * nb), 256, 0, st>>>(ctx->nproj, nb, ctx->d_atom_of.p,
                                                                             ctx->d_offs.p, cblk_off, Bblk, p, ldp,
                                                                             out, ldo));
+}
+void permute_cols(int64_t m, int64_t nb, const int32_t* order, const double2* src, double2* dst, bool inverse,
+                  cudaStream_t st) {
+  if (m == 0 || nb == 0) return;
+  CHEBFI_REQUIRE(nb <= 65535, CHEBFI_ERR_ARG, "at most 65535 columns to permute");
+  const unsigned gx = (unsigned)std::min<int64_t>((m + 255) / 256, 64);
+  CHEBFI_LAUNCH("k_permute_cols", st, (k_permute_cols<<<dim3(gx, (unsigned)nb), 256, 0, st>>>(m, order, src, dst, inverse ? 1 : 0)));
 }
 void mirror_lower(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
   if (n == 0) return;

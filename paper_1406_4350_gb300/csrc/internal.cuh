@@ -174,6 +174,7 @@ struct Work {
   DevBuf<float2> fsplitk;
   SplitBF16Buf Zb, Sb;  // bf16 pairs of Z (or Y) and of the projection-space operands
   DevBuf<double2> gpool, gA, gB;  // filter backward: checkpoints, segment, adjoint iterates
+  DevBuf<int32_t> order;          // band order of the locking filter
   DevBuf<float2> fgpool;
 };
 
@@ -249,4 +250,6 @@ struct chebfi_ctx {
   chebfi::SplitBF16Buf tcA1, tcA2, tcAG, tcAM;
   chebfi::Work w;
   double bound_rigorous = -1.0;
+  int last_sweeps = 0;            // sweeps performed by the last chebfi_solve
+  int64_t last_applies = 0;       // band-H-applications of its filters
 };

@@ -82,6 +82,9 @@ void cheb_combine(int64_t m, int64_t nb, R a, const cplx<R>* u, int64_t ldu, R c
 template <typename R>
 void axpby(int64_t m, int64_t nb, R alpha, const cplx<R>* x, int64_t ldx, R beta, const cplx<R>* y, int64_t ldy,
            cplx<R>* out, int64_t ldo, cudaStream_t st);
+// column permutation of an m x nb block: dst[:, j] = src[:, order[j]] (inverse: dst[:, order[j]] = src[:, j])
+void permute_cols(int64_t m, int64_t nb, const int32_t* order, const double2* src, double2* dst, bool inverse,
+                  cudaStream_t st);
 // copy with precision conversion
 void convert(int64_t m, int64_t nb, const double2* x, int64_t ldx, float2* y, int64_t ldy, cudaStream_t st);
 void convert(int64_t m, int64_t nb, const float2* x, int64_t ldx, double2* y, int64_t ldy, cudaStream_t st);

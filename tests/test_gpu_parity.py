@@ -369,3 +369,41 @@ def test_apply_Sinv_refined_norm_conserving_and_singular_Q():
     g = ChebFI.from_cell(dataclasses.replace(cell, Q=Q))
     with pytest.raises(ChebFIError):
         g.apply_Sinv_refined(fortran(cell.Y0))
+
+
+# ----------------------------------------------------------------------------- locking (Section 5.4)
+@pytest.mark.parametrize("prec, tol", [(0, TOL64), (1, TOL32), (2, TOLMIX)])
+def test_cheb_filter_adaptive_matches_oracle(prec, tol):
+    """Band j filtered to its own degree (0 = left alone), against the oracle band by band."""
+    cell = _tiny_paw(nb=7, seed=9)
+    op = PWOperator.from_cell(cell)
+    hi = ch.upper_bound(op, "rigorous")
+    lo = float(ch.rayleigh_quotients(op, cell.Y0).max())
+    deg = np.array([4, 0, 7, 1, 4, 2, 0], dtype=np.int32)
+    g = _ctx(cell)
+    Y = _F(cell.Y0)
+    g.cheb_filter_adaptive(Y, deg, lo, hi, prec=prec)
+    ref = ch.filter_adaptive(op, cell.Y0, deg, lo, hi)
+    got = _np(Y)
+    for j in range(len(deg)):
+        scale = np.abs(ref[:, j]).max()
+        assert np.abs(got[:, j] - ref[:, j]).max() <= tol * scale, (j, deg[j])
+    assert np.array_equal(got[:, 1], cell.Y0[:, 1]) and np.array_equal(got[:, 6], cell.Y0[:, 6])
+
+
+@pytest.mark.parametrize("prec, lock_tol", [(0, 1e-7), (2, 3e-6)])
+def test_locked_solve_nc24_reaches_exact_eigenvalues_with_less_work(prec, lock_tol):
+    """Locking: after the first sweep each band gets the degree its residual estimate needs
+    for the tolerance; the lowest 75 % still reach 1e-8 Ha of the exact eigenvalues (oracle
+    O1) while the filters apply fewer band-H-applications than full-degree sweeps."""
+    cell = config_cell("nc24")
+    exact = _golden("nc24")
+    g = _ctx(cell)
+    Y = _F(cell.Y0)
+    ev, rs = g.solve(Y, degree=8, sweeps=12, prec=prec, lock_tol=lock_tol)
+    sweeps, applies = g.solve_stats()
+    ev = _np(ev)
+    k = (3 * cell.nbands) // 4
+    assert np.abs(ev[:k] - exact[:k]).max() <= 1e-8
+    assert applies < 0.8 * 8 * cell.nbands * sweeps
+    assert _np(rs)[:k].max() <= 10 * lock_tol
