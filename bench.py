@@ -276,7 +276,7 @@ def run_extra(args):
         Ys = [fortran(c.Y0) for c in cells]
         his = [g_.upper_bound(BOUND_RIGOROUS) for g_ in ctxs]
         los = [float(g_.rayleigh_quotients(Y).max().item()) for g_, Y in zip(ctxs, Ys)]
-        shapes, tune = bt.autotune(F32)
+        shapes, split, tune, split_ms = bt.autotune(F32)
         work = [Y.clone() for Y in Ys]
         l0 = bt.kernel_launches
         with Clocks(0) as clk:
@@ -295,8 +295,9 @@ def run_extra(args):
                                        "per step" % (min(c.npw for c in cells), max(c.npw for c in cells),
                                                      cells[0].nbands, deg)},
                 "ms_batched": ms_b, "ms_per_kpoint_loop": ms_l, "speedup_over_loop": ms_l / ms_b,
-                "gpu_launches_per_call": launches, "autotuned_shapes": shapes,
-                "autotune_ms": tune.round(4).tolist(), "clocks": clk.summary()}
+                "gpu_launches_per_call": launches, "autotuned_shapes": shapes, "split_k_PhY": split,
+                "autotune_ms": tune.round(4).tolist(), "split_ms": split_ms.round(4).tolist(),
+                "clocks": clk.summary()}
     else:
         cell = config_cell(WORKLOAD, nbands=256)
         g = ChebFI.from_cell(cell)

@@ -281,10 +281,17 @@ const char* chebfi_batch_last_error(const chebfi_batch* batch);
 int64_t chebfi_batch_kernel_launches(const chebfi_batch* batch);
 /* Time the candidate tile shapes (16TM x 16TN with (TM, TN) = (4,4), (2,4), (4,2), (8,4)) of
  * the three grouped GEMM classes (0: P_k^H Z_k, 1: G_k / M_k products, 2: P_k W_k) in form
- * prec (CHEBFI_F64 or CHEBFI_F32) and keep the fastest.  shapes (3 ints, nullable) receives
- * the chosen shape index per class; ms (3 x 4 doubles, nullable) the measured times.
- * Overwrites the batch's workspaces; a no-op after the first call for a form.  Synchronises. */
+ * prec (CHEBFI_F64 or CHEBFI_F32), and for class 0 also the split-K factors 1, 2, 4, 8 of its
+ * long inner dimension (chunks summed by a deterministic second pass); keep the fastest.
+ * shapes (4 ints, nullable) receives the chosen shape index per class and the split factor;
+ * ms (16 doubles, nullable) the times per (class, shape) with split 1, then the best time per
+ * split factor.  Overwrites the batch's workspaces; a no-op after the first call for a form.
+ * Synchronises. */
 int chebfi_batch_autotune(chebfi_batch* batch, int prec, int* shapes, double* ms);
+/* Override the autotuner: tile shape index per GEMM class (3 ints, 0..3) and the split-K
+ * factor of P_k^H Z_k (1, 2, 4 or 8) for form prec; graphs captured with other tiles are
+ * dropped and recaptured on the next call.  Synchronises. */
+int chebfi_batch_set_tiles(chebfi_batch* batch, int prec, const int* shapes, int split);
 /* In place on Y[k] (device, complex128, npw_k x nb column-major, leading dimension ld[k],
  * caller's plane-wave order) for k = 0..nk-1: Algorithm 2's filter of the given degree on
  * [lambda_lo[k], lambda_hi[k]] (host arrays of nk doubles), exactly as chebfi_cheb_filter

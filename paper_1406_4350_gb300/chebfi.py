@@ -358,11 +358,18 @@ class ChebFIBatch:
         return int(self.lib.chebfi_batch_kernel_launches(self.h))
 
     def autotune(self, prec: int = F32):
-        """Tile shape chosen per GEMM class and the measured ms table (3 x 4)."""
-        shapes = (ctypes.c_int * 3)()
-        ms = (ctypes.c_double * 12)()
+        """(tile shape per GEMM class, split-K factor of P^H Z, ms per (class, shape) at split 1
+        (3 x 4), best ms per split factor 1, 2, 4, 8)."""
+        shapes = (ctypes.c_int * 4)()
+        ms = (ctypes.c_double * 16)()
         self._check(self.lib.chebfi_batch_autotune(self.h, prec, shapes, ms))
-        return list(shapes), np.array(ms[:]).reshape(3, 4)
+        m = np.array(ms[:])
+        return list(shapes[:3]), int(shapes[3]), m[:12].reshape(3, 4), m[12:]
+
+    def set_tiles(self, shapes, split: int, prec: int = F32):
+        """Override the autotuner's tile shapes (3 indices) and P^H Z split-K factor."""
+        arr = (ctypes.c_int * 3)(*[int(x) for x in shapes])
+        self._check(self.lib.chebfi_batch_set_tiles(self.h, prec, arr, int(split)))
 
     def cheb_filter(self, Ys, degree: int, lambda_lo, lambda_hi, prec: int = F32):
         """In place on every block of ``Ys`` (one complex128 column-major tensor per k-point);

@@ -144,7 +144,6 @@ __global__ void k_bcombine(const KDesc<R>* __restrict__ ks, int64_t per_k, int64
 
 // ---------------------------------------------------------------- grouped GEMM
 enum BOp : int { OP_PHY = 0, OP_G = 1, OP_M = 2, OP_GNEG = 3, OP_PW = 4 };
-constexpr int BKg = 8;
 
 // One problem of the group: C = alpha op(A) B + beta C, complex, column-major.
 template <typename R> struct Prob {
@@ -177,14 +176,30 @@ __device__ __forceinline__ Prob<R> make_prob(const KDesc<R>& d, int op, int firs
 
 // Persistent CTAs take (k, tile) items from the queue until it is empty.  Tile BM x BN with
 // BM = 16 TM, BN = 16 TN; 256 threads, TM x TN complex outputs per thread.  CA: op(A) = A^H.
+// The K loop is double-buffered: the next BKb-deep slices of A and B are fetched into
+// registers while the current ones are multiplied from shared memory (one barrier per slice).
+// With nsplit > 1 (the P^H Z class, whose inner dimension is a whole sphere) an item is
+// (k, tile * nsplit + chunk): it sums one K-chunk into its own slice of ws, and
+// k_bsplit_reduce adds the slices in chunk order (deterministic).
+constexpr int BKb = 16;
+
+template <typename R, int TM, int TN>
+constexpr size_t bgemm_smem() {
+  return (size_t)2 * BKb * (16 * TM + 1 + 16 * TN + 1) * sizeof(cplx<R>);
+}
+
 template <typename R, int TM, int TN, bool CA>
 __global__ void __launch_bounds__(256) k_bgemm(const KDesc<R>* __restrict__ ks, int op, int first, int64_t nq,
                                                int64_t nb, const int2* __restrict__ items, int nitems,
-                                               int* __restrict__ counter, const cplx<R>* Bb, cplx<R>* Cb) {
+                                               int* __restrict__ counter, const cplx<R>* Bb, cplx<R>* Cb,
+                                               int nsplit, cplx<R>* __restrict__ ws) {
   using C = cplx<R>;
   constexpr int BM = 16 * TM, BN = 16 * TN;
-  __shared__ C As[BKg][BM + 1];
-  __shared__ C Bs[BKg][BN + 1];
+  constexpr int LA = BM * BKb / 256, LB = BN * BKb / 256;
+  static_assert(LA * 256 == BM * BKb && LB * 256 == BN * BKb, "tile slices must split evenly over 256 threads");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* As = reinterpret_cast<C*>(smem_raw);  // [2][BKb][BM + 1]
+  C* Bs = As + 2 * BKb * (BM + 1);         // [2][BKb][BN + 1]
   __shared__ int s_item;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const C zero = cmake<C>(0.0, 0.0);
@@ -195,43 +210,83 @@ __global__ void __launch_bounds__(256) k_bgemm(const KDesc<R>* __restrict__ ks, 
     __syncthreads();
     if (item >= nitems) break;
     const int2 it = items[item];
-    const Prob<R> p = make_prob<R>(ks[it.x], op, first, it.x, nq, nb, Bb, Cb);
+    Prob<R> p = make_prob<R>(ks[it.x], op, first, it.x, nq, nb, Bb, Cb);
+    const int tile = it.y / nsplit, chunk = it.y - tile * nsplit;
+    int64_t klo = 0, khi = p.K;
+    if (nsplit > 1) {
+      const int64_t kc = ((p.K + nsplit - 1) / nsplit + BKb - 1) / BKb * BKb;
+      klo = min(p.K, (int64_t)chunk * kc);
+      khi = min(p.K, klo + kc);
+      p.C = ws + ((int64_t)it.x * nsplit + chunk) * p.M * p.N;
+      p.ldc = p.M;
+      p.alpha = 1;
+      p.beta = 0;
+    }
     const int64_t tm = (p.M + BM - 1) / BM;
-    const int64_t i0 = (int64_t)(it.y % tm) * BM, j0 = (int64_t)(it.y / tm) * BN;
+    const int64_t i0 = (int64_t)(tile % tm) * BM, j0 = (int64_t)(tile / tm) * BN;
     R accr[TM][TN], acci[TM][TN];
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
       for (int b = 0; b < TN; ++b) accr[a][b] = acci[a][b] = (R)0;
-    for (int64_t k0 = 0; k0 < p.K; k0 += BKg) {
+    C ra[LA], rb[LB];
+    auto fetch = [&](int64_t k0) {
 #pragma unroll
-      for (int e0 = 0; e0 < BM * BKg; e0 += 256) {
-        const int e = e0 + tid;
+      for (int l = 0; l < LA; ++l) {
+        const int e = l * 256 + tid;
         int i, k;
-        if (!CA) { i = e % BM; k = e / BM; } else { k = e % BKg; i = e / BKg; }
+        if (!CA) { i = e % BM; k = e / BM; } else { k = e % BKb; i = e / BKb; }
         const int64_t gi = i0 + i, gk = k0 + k;
         C v = zero;
-        if (gi < p.M && gk < p.K) {
+        if (gi < p.M && gk < khi) {
           v = CA ? p.A[gk + gi * p.lda] : p.A[gi + gk * p.lda];
           if (CA) v.y = -v.y;
         }
-        As[k][i] = v;
+        ra[l] = v;
       }
 #pragma unroll
-      for (int e0 = 0; e0 < BN * BKg; e0 += 256) {
-        const int e = e0 + tid;
-        const int k = e % BKg, j = e / BKg;
+      for (int l = 0; l < LB; ++l) {
+        const int e = l * 256 + tid;
+        const int k = e % BKb, j = e / BKb;
         const int64_t gj = j0 + j, gk = k0 + k;
-        Bs[k][j] = (gj < p.N && gk < p.K) ? p.B[gk + gj * p.ldb] : zero;
+        rb[l] = (gj < p.N && gk < khi) ? p.B[gk + gj * p.ldb] : zero;
       }
-      __syncthreads();
+    };
+    auto stash = [&](int buf) {
+      C* as = As + buf * BKb * (BM + 1);
+      C* bs = Bs + buf * BKb * (BN + 1);
 #pragma unroll
-      for (int k = 0; k < BKg; ++k) {
+      for (int l = 0; l < LA; ++l) {
+        const int e = l * 256 + tid;
+        int i, k;
+        if (!CA) { i = e % BM; k = e / BM; } else { k = e % BKb; i = e / BKb; }
+        as[k * (BM + 1) + i] = ra[l];
+      }
+#pragma unroll
+      for (int l = 0; l < LB; ++l) {
+        const int e = l * 256 + tid;
+        const int k = e % BKb, j = e / BKb;
+        bs[k * (BN + 1) + j] = rb[l];
+      }
+    };
+    if (klo < khi) {
+      fetch(klo);
+      stash(0);
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = klo; k0 < khi; k0 += BKb) {
+      const bool more = k0 + BKb < khi;
+      if (more) fetch(k0 + BKb);  // in flight while the current slice is multiplied
+      const C* as = As + buf * BKb * (BM + 1);
+      const C* bs = Bs + buf * BKb * (BN + 1);
+#pragma unroll
+      for (int k = 0; k < BKb; ++k) {
         C av[TM], bv[TN];
 #pragma unroll
-        for (int a = 0; a < TM; ++a) av[a] = As[k][tx + 16 * a];
+        for (int a = 0; a < TM; ++a) av[a] = as[k * (BM + 1) + tx + 16 * a];
 #pragma unroll
-        for (int b = 0; b < TN; ++b) bv[b] = Bs[k][ty + 16 * b];
+        for (int b = 0; b < TN; ++b) bv[b] = bs[k * (BN + 1) + ty + 16 * b];
 #pragma unroll
         for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -242,7 +297,9 @@ __global__ void __launch_bounds__(256) k_bgemm(const KDesc<R>* __restrict__ ks, 
             acci[a][b] = fma(av[a].y, bv[b].x, acci[a][b]);
           }
       }
+      if (more) stash(buf ^ 1);  // that buffer was last read before the previous barrier
       __syncthreads();
+      buf ^= 1;
     }
 #pragma unroll
     for (int b = 0; b < TN; ++b) {
@@ -266,10 +323,36 @@ __global__ void __launch_bounds__(256) k_bgemm(const KDesc<R>* __restrict__ ks, 
   }
 }
 
+// C_k = sum over chunks of the split-K slices (per = M x N elements of one problem)
+template <typename R>
+__global__ void k_bsplit_reduce(int64_t n, int64_t per, int nsplit, const cplx<R>* __restrict__ ws,
+                                cplx<R>* __restrict__ C) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t k = i / per, e = i - k * per;
+  cplx<R> acc = ws[(k * nsplit) * per + e];
+  for (int c = 1; c < nsplit; ++c) {
+    const cplx<R> v = ws[(k * nsplit + c) * per + e];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  C[i] = acc;
+}
+
 // tile shapes the autotuner chooses from: (TM, TN) -> BM x BN = 16 TM x 16 TN
 constexpr int kNumShapes = 4;
+constexpr int kMaxSplit = 8;  // split-K factors tried for P^H Z: 1, 2, 4, 8
 constexpr int kShapeTM[kNumShapes] = {4, 2, 4, 8};
 constexpr int kShapeTN[kNumShapes] = {4, 4, 2, 4};
+
+template <typename R> size_t bgemm_smem_of(int shape) {
+  switch (shape) {
+    case 0: return bgemm_smem<R, 4, 4>();
+    case 1: return bgemm_smem<R, 2, 4>();
+    case 2: return bgemm_smem<R, 4, 2>();
+    default: return bgemm_smem<R, 8, 4>();
+  }
+}
 
 template <typename R, bool CA> const void* bgemm_fn(int shape) {
   switch (shape) {
@@ -307,12 +390,14 @@ struct chebfi_batch {
   std::vector<KDesc<double>> h64;
   std::vector<KDesc<float>> h32;
   // workspaces
-  DevBuf<double2> Y64[2], Z64, T64, p64[5];
-  DevBuf<float2> Y32[2], Z32, T32, p32[5];
+  DevBuf<double2> Y64[2], Z64, T64, p64[5], ws64;
+  DevBuf<float2> Y32[2], Z32, T32, p32[5], ws32;
   DevBuf<int> counters;
   // autotuned tile shape per (form, GEMM class); -1 = not tuned yet
   int shape[2][GC_N] = {{-1, -1, -1}, {-1, -1, -1}};
+  int split[2] = {1, 1};  // split-K factor of the P^H Z class
   double tune_ms[2][GC_N][kNumShapes] = {};
+  double split_ms[2][4] = {};
   // work-queue items per (GEMM class, shape)
   std::map<std::pair<int, int>, DevBuf<int2>*> items;
   std::map<std::pair<int, int>, int> nitems;
@@ -340,6 +425,7 @@ template <> struct BatchOps<double> {
   static DevBuf<double2>& Z(chebfi_batch* b) { return b->Z64; }
   static DevBuf<double2>& T(chebfi_batch* b) { return b->T64; }
   static DevBuf<double2>* p(chebfi_batch* b) { return b->p64; }
+  static DevBuf<double2>& ws(chebfi_batch* b) { return b->ws64; }
   static const double* K(chebfi_ctx* c) { return c->d_K.p; }
   static const double2* P(chebfi_ctx* c) { return c->d_P.p; }
   static const double2* G(chebfi_ctx* c) { return c->d_G.p; }
@@ -356,6 +442,7 @@ template <> struct BatchOps<float> {
   static DevBuf<float2>& Z(chebfi_batch* b) { return b->Z32; }
   static DevBuf<float2>& T(chebfi_batch* b) { return b->T32; }
   static DevBuf<float2>* p(chebfi_batch* b) { return b->p32; }
+  static DevBuf<float2>& ws(chebfi_batch* b) { return b->ws32; }
   static const float* K(chebfi_ctx* c) { return c->d_Kf.p; }
   static const float2* P(chebfi_ctx* c) { return c->d_Pf.p; }
   static const float2* G(chebfi_ctx* c) { return c->d_Gf.p; }
@@ -382,9 +469,10 @@ FastArgs fast_args(const chebfi_ctx* c) {
   return fa;
 }
 
-// (k, tile) items of a GEMM class for tile shape `shape`, longest problems first
-void build_items(chebfi_batch* bt, int gc, int shape) {
-  const auto key = std::make_pair(gc, shape);
+// (k, tile[, chunk]) items of a GEMM class for tile shape `shape` and split factor
+// `nsplit`, longest problems first
+void build_items(chebfi_batch* bt, int gc, int shape, int nsplit) {
+  const auto key = std::make_pair(gc, shape * 16 + nsplit);
   if (bt->items.count(key)) return;
   const int64_t BM = 16 * kShapeTM[shape], BN = 16 * kShapeTN[shape];
   std::vector<int> order(bt->nk);
@@ -394,7 +482,7 @@ void build_items(chebfi_batch* bt, int gc, int shape) {
   std::vector<int2> v;
   for (int k : order) {
     const int64_t M = gc == GC_PW ? bt->npw[k] : bt->nq;
-    const int64_t tiles = ((M + BM - 1) / BM) * ((bt->nb + BN - 1) / BN);
+    const int64_t tiles = ((M + BM - 1) / BM) * ((bt->nb + BN - 1) / BN) * nsplit;
     for (int64_t t = 0; t < tiles; ++t) v.push_back(make_int2(k, (int)t));
   }
   auto* buf = new DevBuf<int2>();
@@ -404,33 +492,39 @@ void build_items(chebfi_batch* bt, int gc, int shape) {
 }
 
 template <typename R, bool CA>
-void launch_bgemm(chebfi_batch* bt, int shape, int op, int first, const cplx<R>* Bb, cplx<R>* Cb, int* counter,
-                  cudaStream_t st, const char* tag) {
+void launch_bgemm(chebfi_batch* bt, int shape, int nsplit, int op, int first, const cplx<R>* Bb, cplx<R>* Cb,
+                  int* counter, cudaStream_t st, const char* tag) {
   const int gc = op == OP_PHY ? GC_PHY : (op == OP_PW ? GC_PW : GC_SMALL);
-  build_items(bt, gc, shape);
-  const auto key = std::make_pair(gc, shape);
+  build_items(bt, gc, shape, nsplit);
+  const auto key = std::make_pair(gc, shape * 16 + nsplit);
   const int n = bt->nitems[key];
   const int per_sm = std::max(1, bt->grid_per_sm[BatchOps<R>::form][shape]);
   const unsigned grid = (unsigned)std::max(1, std::min(n, bt->nsm * per_sm));
   const KDesc<R>* d = BatchOps<R>::desc(bt).p;
   const int2* it = bt->items[key]->p;
   const int64_t nq = bt->nq, nb = bt->nb;
+  cplx<R>* ws = BatchOps<R>::ws(bt).p;
   switch (shape) {
-    case 0: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 4, 4, CA><<<grid, 256, 0, st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb))); break;
-    case 1: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 2, 4, CA><<<grid, 256, 0, st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb))); break;
-    case 2: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 4, 2, CA><<<grid, 256, 0, st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb))); break;
-    default: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 8, 4, CA><<<grid, 256, 0, st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb))); break;
+    case 0: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 4, 4, CA><<<grid, 256, bgemm_smem<R, 4, 4>(), st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb, nsplit, ws))); break;
+    case 1: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 2, 4, CA><<<grid, 256, bgemm_smem<R, 2, 4>(), st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb, nsplit, ws))); break;
+    case 2: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 4, 2, CA><<<grid, 256, bgemm_smem<R, 4, 2>(), st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb, nsplit, ws))); break;
+    default: CHEBFI_LAUNCH(tag, st, (k_bgemm<R, 8, 4, CA><<<grid, 256, bgemm_smem<R, 8, 4>(), st>>>(d, op, first, nq, nb, it, n, counter, Bb, Cb, nsplit, ws))); break;
+  }
+  if (nsplit > 1) {
+    const int64_t per = nq * nb, tot = (int64_t)bt->nk * per;
+    CHEBFI_LAUNCH("k_bsplit_reduce", st, (k_bsplit_reduce<R><<<nblk(tot), 256, 0, st>>>(tot, per, nsplit, ws, Cb)));
   }
 }
 
 // grouped GEMM of one op with the tuned shape; counter slot `slot`
 template <typename R>
 void bgemm(chebfi_batch* bt, int op, int first, const cplx<R>* Bb, cplx<R>* Cb, int slot, cudaStream_t st) {
+  const int f = BatchOps<R>::form;
   const int gc = op == OP_PHY ? GC_PHY : (op == OP_PW ? GC_PW : GC_SMALL);
-  const int shape = bt->shape[BatchOps<R>::form][gc];
+  const int shape = bt->shape[f][gc];
   int* counter = bt->counters.p + slot;
-  if (op == OP_PHY) launch_bgemm<R, true>(bt, shape, op, first, Bb, Cb, counter, st, "bgemm_PhY");
-  else launch_bgemm<R, false>(bt, shape, op, first, Bb, Cb, counter, st, op == OP_PW ? "bgemm_PW" : "bgemm_small");
+  if (op == OP_PHY) launch_bgemm<R, true>(bt, shape, bt->split[f], op, first, Bb, Cb, counter, st, "bgemm_PhY");
+  else launch_bgemm<R, false>(bt, shape, 1, op, first, Bb, Cb, counter, st, op == OP_PW ? "bgemm_PW" : "bgemm_small");
 }
 
 template <typename R, int N>
@@ -489,6 +583,7 @@ template <typename R> void ensure_ws(chebfi_batch* bt) {
   BatchOps<R>::Z(bt).alloc((size_t)bt->ytot);
   BatchOps<R>::T(bt).alloc((size_t)bt->ttot);
   for (int i = 0; i < 5; ++i) BatchOps<R>::p(bt)[i].alloc(np);
+  BatchOps<R>::ws(bt).alloc(np * kMaxSplit);
 }
 
 // Algorithm 2's filter of degree n for all k-points (the same steps as the single-problem
@@ -544,8 +639,11 @@ void autotune(chebfi_batch* bt, cudaStream_t st) {
   CHEBFI_CUDA(cudaMemsetAsync(Y2, 0, sizeof(C) * bt->ytot, st));
   for (int i = 0; i < 5; ++i) CHEBFI_CUDA(cudaMemsetAsync(pp[i].p, 0, sizeof(C) * pp[i].n, st));
   for (int s = 0; s < kNumShapes; ++s) {
+    const size_t smem = bgemm_smem_of<R>(s);
+    for (const void* fn : {bgemm_fn<R, false>(s), bgemm_fn<R, true>(s)})
+      CHEBFI_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb_per_sm = 0;
-    CHEBFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, bgemm_fn<R, false>(s), 256, 0));
+    CHEBFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, bgemm_fn<R, false>(s), 256, smem));
     bt->grid_per_sm[f][s] = std::max(1, nb_per_sm);
   }
   cudaEvent_t a, b;
@@ -578,6 +676,38 @@ void autotune(chebfi_batch* bt, cudaStream_t st) {
       if (best_ms < bt->tune_ms[f][gc][best]) best = s;
     }
     bt->shape[f][gc] = best;
+  }
+  // split-K factor of P^H Z: every shape again with each factor, keep the fastest pair
+  if (bt->nq > 0) {
+    int best_shape = bt->shape[f][GC_PHY], best_split = 1;
+    float best_all = (float)bt->tune_ms[f][GC_PHY][best_shape];
+    for (int si = 0, sp = 1; sp <= kMaxSplit; sp *= 2, ++si) {
+      float best_sp = 1e30f;
+      for (int s = 0; s < kNumShapes; ++s) {
+        bt->shape[f][GC_PHY] = s;
+        bt->split[f] = sp;
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          CHEBFI_CUDA(cudaMemsetAsync(bt->counters.p, 0, sizeof(int), st));
+          CHEBFI_CUDA(cudaEventRecord(a, st));
+          bgemm<R>(bt, OP_PHY, 0, Y, pp[1].p, 0, st);
+          CHEBFI_CUDA(cudaEventRecord(b, st));
+          CHEBFI_CUDA(cudaEventSynchronize(b));
+          float ms = 0.f;
+          CHEBFI_CUDA(cudaEventElapsedTime(&ms, a, b));
+          if (rep > 0) best_ms = std::min(best_ms, ms);
+        }
+        best_sp = std::min(best_sp, best_ms);
+        if (best_ms < best_all) {
+          best_all = best_ms;
+          best_shape = s;
+          best_split = sp;
+        }
+      }
+      bt->split_ms[f][si] = best_sp;
+    }
+    bt->shape[f][GC_PHY] = best_shape;
+    bt->split[f] = best_split;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -789,6 +919,35 @@ int chebfi_batch_autotune(chebfi_batch* bt, int prec, int* shapes, double* ms) {
     if (shapes) shapes[gc] = bt->shape[f][gc];
     if (ms)
       for (int s = 0; s < kNumShapes; ++s) ms[gc * kNumShapes + s] = bt->tune_ms[f][gc][s];
+  }
+  if (shapes) shapes[GC_N] = bt->split[f];
+  if (ms)
+    for (int i = 0; i < 4; ++i) ms[GC_N * kNumShapes + i] = bt->split_ms[f][i];
+  BAPI_END(bt)
+}
+
+int chebfi_batch_set_tiles(chebfi_batch* bt, int prec, const int* shapes, int split) {
+  BAPI_BEGIN(bt)
+  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32, CHEBFI_ERR_ARG, "the batch runs the FP64 or FP32 form");
+  CHEBFI_REQUIRE(shapes, CHEBFI_ERR_ARG, "null shapes");
+  for (int gc = 0; gc < GC_N; ++gc)
+    CHEBFI_REQUIRE(shapes[gc] >= 0 && shapes[gc] < kNumShapes, CHEBFI_ERR_ARG, "tile shape index out of range");
+  CHEBFI_REQUIRE(split == 1 || split == 2 || split == 4 || split == 8, CHEBFI_ERR_ARG, "split-K factor must be 1, 2, 4 or 8");
+  const int f = prec == CHEBFI_F64 ? 0 : 1;
+  // occupancy and buffers as the autotuner would have set them
+  if (prec == CHEBFI_F64) autotune<double>(bt, 0);
+  else autotune<float>(bt, 0);
+  CHEBFI_CUDA(cudaDeviceSynchronize());
+  for (int gc = 0; gc < GC_N; ++gc) bt->shape[f][gc] = shapes[gc];
+  bt->split[f] = split;
+  // graphs captured with the previous tiles are stale
+  for (auto it = bt->graphs.begin(); it != bt->graphs.end();) {
+    if (it->first.first == f) {
+      cudaGraphExecDestroy(it->second);
+      it = bt->graphs.erase(it);
+    } else {
+      ++it;
+    }
   }
   BAPI_END(bt)
 }

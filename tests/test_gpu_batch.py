@@ -105,11 +105,29 @@ def test_batch_norm_conserving_and_degree_zero():
 def test_batch_autotune_reports_every_shape():
     cells = _small(nk=3, seed=1207)
     bt = _batch(cells)
-    shapes, ms = bt.autotune(1)
-    assert len(shapes) == 3 and all(0 <= s < 4 for s in shapes)
-    assert np.all(np.isfinite(ms)) and np.all(ms > 0)
-    for gc in range(3):
+    shapes, split, ms, split_ms = bt.autotune(1)
+    assert len(shapes) == 3 and all(0 <= s < 4 for s in shapes) and split in (1, 2, 4, 8)
+    assert np.all(np.isfinite(ms)) and np.all(ms > 0) and np.all(split_ms > 0)
+    for gc in (1, 2):
         assert ms[gc, shapes[gc]] == ms[gc].min()
+    # the P^H Z choice is the fastest (shape, split) pair
+    assert split_ms[[1, 2, 4, 8].index(split)] == split_ms.min()
+
+
+@pytest.mark.parametrize("shapes, split", [([0, 1, 2], 1), ([3, 0, 3], 2), ([1, 2, 0], 4), ([2, 3, 1], 8)])
+def test_batch_every_tile_shape_and_split(shapes, split):
+    """Forced tiles (every shape in some class, every split-K factor of P^H Z): FP64 parity."""
+    from paper_1406_4350_gb300.chebfi import fortran
+    cells = _small(nk=4, seed=1209)
+    lo, hi = _intervals(cells)
+    bt = _batch(cells)
+    bt.set_tiles(shapes, split, prec=0)
+    Ys = [fortran(c.Y0) for c in cells]
+    bt.cheb_filter(Ys, 5, lo, hi, prec=0)
+    torch.cuda.synchronize()
+    for c, Y, l, h in zip(cells, Ys, lo, hi):
+        ref = ch.filter_plain(PWOperator.from_cell(c), c.Y0, 5, l, h)
+        assert _rel(Y.cpu().numpy(), ref) <= TOL64
 
 
 def test_batch_rejects_incompatible_contexts():
