@@ -1299,9 +1299,21 @@ int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int deg
   CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
   if (nb == 0 || degree == 0) return CHEBFI_OK;
   cudaStream_t st = S(stream);
-  gather_to_Ya(ctx, Y, nb, ld, st);
-  filter_on_Ya(ctx, nb, degree, lambda_lo, lambda_hi, prec, st);
-  scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  if (prec == CHEBFI_F64) {
+    gather_to_Ya(ctx, Y, nb, ld, st);
+    filter_on_Ya(ctx, nb, degree, lambda_lo, lambda_hi, prec, st);
+    scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  } else {
+    // FP32 iterates straight from and to the caller's FP64 block (reorder and convert in one pass)
+    ensure_filter_ws(ctx, nb, prec);
+    Work& w = ctx->w;
+    const int64_t npw = ctx->npw;
+    gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y, ld, w.fYa.p, npw, st);
+    FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
+    float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lambda_lo, lambda_hi, st)
+                                       : filter_sorted<float>(ctx, b, nb, degree, lambda_lo, lambda_hi, st);
+    scatter_rows(npw, nb, ctx->d_sorted_to_user.p, out, npw, (double2*)Y, ld, st);
+  }
   API_END(ctx)
 }
 

@@ -94,6 +94,25 @@ __global__ void k_scatter(int64_t m, int64_t nb, const int32_t* __restrict__ per
   dst[perm[i] + j * ldd] = src[i + j * lds];
 }
 
+// the same reorderings with the precision change fused in (FP64 caller blocks, FP32 iterates)
+__global__ void k_gather_f32(int64_t m, int64_t nb, const int32_t* __restrict__ perm, const double2* __restrict__ src,
+                             int64_t lds, float2* __restrict__ dst, int64_t ldd) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, j = idx / m;
+  const double2 v = src[perm[i] + j * lds];
+  dst[i + j * ldd] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void k_scatter_f32(int64_t m, int64_t nb, const int32_t* __restrict__ perm, const float2* __restrict__ src,
+                              int64_t lds, double2* __restrict__ dst, int64_t ldd) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int64_t i = idx % m, j = idx / m;
+  const float2 v = src[i + j * lds];
+  dst[perm[i] + j * ldd] = make_double2((double)v.x, (double)v.y);
+}
+
 // one block per column; fixed-order tree reduction (deterministic)
 __global__ void k_column_dots(int64_t m, const double2* __restrict__ x, int64_t ldx, const double2* __restrict__ y,
                               int64_t ldy, double* __restrict__ out, int accumulate) {
@@ -310,6 +329,16 @@ void scatter_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src
                   int64_t ldd, cudaStream_t st) {
   if (m * nb == 0) return;
   CHEBFI_LAUNCH("k_scatter", st, k_scatter<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd));
+}
+void gather_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, float2* dst, int64_t ldd,
+                 cudaStream_t st) {
+  if (m * nb == 0) return;
+  CHEBFI_LAUNCH("k_gather", st, k_gather_f32<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd));
+}
+void scatter_rows(int64_t m, int64_t nb, const int32_t* perm, const float2* src, int64_t lds, double2* dst, int64_t ldd,
+                  cudaStream_t st) {
+  if (m * nb == 0) return;
+  CHEBFI_LAUNCH("k_scatter", st, k_scatter_f32<<<nblocks(m * nb), 256, 0, st>>>(m, nb, perm, src, lds, dst, ldd));
 }
 void column_dots(int64_t m, int64_t nb, const double2* x, int64_t ldx, const double2* y, int64_t ldy, double* out,
                  bool accumulate, cudaStream_t st) {

@@ -93,6 +93,11 @@ void gather_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src,
                  int64_t ldd, cudaStream_t st);
 void scatter_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, double2* dst,
                   int64_t ldd, cudaStream_t st);
+// the same with the conversion to / from FP32 fused in
+void gather_rows(int64_t m, int64_t nb, const int32_t* perm, const double2* src, int64_t lds, float2* dst, int64_t ldd,
+                 cudaStream_t st);
+void scatter_rows(int64_t m, int64_t nb, const int32_t* perm, const float2* src, int64_t lds, double2* dst, int64_t ldd,
+                  cudaStream_t st);
 // out[b] = Re sum_j conj(x_jb) y_jb  (+= if accumulate)
 void column_dots(int64_t m, int64_t nb, const double2* x, int64_t ldx, const double2* y, int64_t ldy,
                  double* out, bool accumulate, cudaStream_t st);
