@@ -193,6 +193,16 @@ int chebfi_adaptive_degrees(const double* ritz, const double* resid, int64_t nb,
  * filters (sum over sweeps of the bands' degrees). */
 int chebfi_solve_stats(const chebfi_ctx* ctx, int* sweeps_done, int64_t* band_applies);
 
+/* chebfi_cheb_filter on a block in HOST memory (complex128, npw x nb column-major, leading
+ * dimension ld, caller's row order; page-locked memory for full copy bandwidth), in place.
+ * Bands are filtered independently, so the block goes through the GPU in nchunks band chunks
+ * (0: 2 chunks from 1024 bands up, else 1): the copy in of chunk c, the filter of chunk c-1
+ * and the copy out of chunk c-2 overlap (two device staging buffers, two copy streams).
+ * Stream-ordered on `stream`: the host block is final once `stream` completes.  The host
+ * block must not be touched until then. */
+int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lambda_lo,
+                            double lambda_hi, int prec, int nchunks, void* stream);
+
 /* S-orthonormalisation by Cholesky-QR (FP64): G_Y = Y^H S Y = L L^H, Y <- Y L^{-H}.
  * Synchronises; CHEBFI_ERR_NOT_SPD if G_Y is not positive definite. */
 int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream);

@@ -47,6 +47,8 @@ SIGNATURES = {
     "chebfi_batch_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "chebfi_batch_set_tiles": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "chebfi_batch_cheb_filter": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
+    "chebfi_cheb_filter_host": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_double, c_double, c_int, c_int,
+                                        c_void_p]),
     "chebfi_cheb_filter_adaptive": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_double, c_double,
                                             c_int, c_void_p]),
     "chebfi_adaptive_degrees": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_double, c_double, c_int, c_void_p]),

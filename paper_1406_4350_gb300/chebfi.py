@@ -230,6 +230,21 @@ class ChebFI:
                                                 _stream()))
         return Y
 
+    def cheb_filter_host(self, Y, degree: int, lambda_lo: float, lambda_hi: float, prec: int = F64,
+                         nchunks: int = 0):
+        """chebfi_cheb_filter on a host block (complex128 CPU tensor, column-major, ideally pinned),
+        in place; the copies overlap the filter of neighbouring band chunks.  Returns Y."""
+        if not (isinstance(Y, torch.Tensor) and not Y.is_cuda and Y.dtype == torch.complex128 and Y.dim() == 2):
+            raise TypeError("expected a 2-D complex128 CPU tensor")
+        if Y.shape[1] > 0 and Y.stride(0) != 1:
+            raise ValueError("host block must be column-major")
+        nb = int(Y.shape[1])
+        ld = int(Y.stride(1)) if nb > 1 else max(int(Y.shape[0]), 1)
+        self._check(self.lib.chebfi_cheb_filter_host(self.h, ctypes.c_void_p(Y.data_ptr() if Y.numel() else 0), nb,
+                                                     max(ld, int(Y.shape[0])), degree, lambda_lo, lambda_hi, prec,
+                                                     nchunks, _stream()))
+        return Y
+
     def orthonormalise(self, Y):
         y, nb, ld = _block(Y)
         self._check(self.lib.chebfi_orthonormalise(self.h, y, nb, ld, _stream()))

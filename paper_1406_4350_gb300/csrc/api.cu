@@ -436,6 +436,7 @@ void degrees_for_tolerance(const double* ritz, const double* resid, int64_t nb, 
   }
 }
 
+
 // Rayleigh quotients of the sorted FP64 block Y.
 void rq_sorted(chebfi_ctx* ctx, const double2* Y, int64_t nb, double* rq, cudaStream_t st) {
   Work& w = ctx->w;
@@ -556,6 +557,28 @@ void gather_to_Ya(chebfi_ctx* ctx, const void* Y, int64_t nb, int64_t ld, cudaSt
 void scatter_from(chebfi_ctx* ctx, const double2* src, void* Y, int64_t nb, int64_t ld, cudaStream_t st) {
   scatter_rows(ctx->npw, nb, ctx->d_sorted_to_user.p, src, ctx->npw, (double2*)Y, ld, st);
 }
+
+// Algorithm 2's filter in place on a caller's device block (caller's row order, leading
+// dimension ld), stream-ordered on st.
+void filter_device_block(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lo, double hi,
+                         int prec, cudaStream_t st) {
+  if (prec == CHEBFI_F64) {
+    gather_to_Ya(ctx, Y, nb, ld, st);
+    filter_on_Ya(ctx, nb, degree, lo, hi, prec, st);
+    scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+    return;
+  }
+  // FP32 iterates straight from and to the caller's FP64 block (reorder and convert in one pass)
+  ensure_filter_ws(ctx, nb, prec);
+  Work& w = ctx->w;
+  const int64_t npw = ctx->npw;
+  gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y, ld, w.fYa.p, npw, st);
+  FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
+  float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lo, hi, st)
+                                     : filter_sorted<float>(ctx, b, nb, degree, lo, hi, st);
+  scatter_rows(npw, nb, ctx->d_sorted_to_user.p, out, npw, (double2*)Y, ld, st);
+}
+
 
 double cheb_T_abs(int n, double x) {  // |T_n(x)| for |x| >= 1 by its cosh form, else <= 1
   const double ax = std::fabs(x);
@@ -1298,22 +1321,7 @@ int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int deg
                  "need finite lambda_lo < lambda_hi");
   CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
   if (nb == 0 || degree == 0) return CHEBFI_OK;
-  cudaStream_t st = S(stream);
-  if (prec == CHEBFI_F64) {
-    gather_to_Ya(ctx, Y, nb, ld, st);
-    filter_on_Ya(ctx, nb, degree, lambda_lo, lambda_hi, prec, st);
-    scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
-  } else {
-    // FP32 iterates straight from and to the caller's FP64 block (reorder and convert in one pass)
-    ensure_filter_ws(ctx, nb, prec);
-    Work& w = ctx->w;
-    const int64_t npw = ctx->npw;
-    gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y, ld, w.fYa.p, npw, st);
-    FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
-    float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lambda_lo, lambda_hi, st)
-                                       : filter_sorted<float>(ctx, b, nb, degree, lambda_lo, lambda_hi, st);
-    scatter_rows(npw, nb, ctx->d_sorted_to_user.p, out, npw, (double2*)Y, ld, st);
-  }
+  filter_device_block(ctx, Y, nb, ld, degree, lambda_lo, lambda_hi, prec, S(stream));
   API_END(ctx)
 }
 
@@ -1355,6 +1363,64 @@ int chebfi_solve_stats(const chebfi_ctx* ctx, int* sweeps_done, int64_t* band_ap
   if (sweeps_done) *sweeps_done = ctx->last_sweeps;
   if (band_applies) *band_applies = ctx->last_applies;
   return CHEBFI_OK;
+}
+
+int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lambda_lo,
+                            double lambda_hi, int prec, int nchunks, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  CHEBFI_REQUIRE(nb >= 0 && (nb == 0 || Y) && ld >= ctx->npw, CHEBFI_ERR_ARG, "bad host block");
+  CHEBFI_REQUIRE(degree >= 0 && degree <= 1000, CHEBFI_ERR_ARG, "degree out of range");
+  CHEBFI_REQUIRE(std::isfinite(lambda_lo) && std::isfinite(lambda_hi) && lambda_hi > lambda_lo, CHEBFI_ERR_ARG,
+                 "need finite lambda_lo < lambda_hi");
+  CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
+  CHEBFI_REQUIRE(nchunks >= 0, CHEBFI_ERR_ARG, "negative chunk count");
+  if (nb == 0 || degree == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  const int64_t npw = ctx->npw;
+  // bands are filtered independently, so the block is processed in band chunks: chunk c is
+  // copied in while chunk c-1 is filtered and chunk c-2 is copied out (two staging buffers)
+  int nc = nchunks > 0 ? nchunks : (nb >= 1024 ? 2 : 1);
+  nc = (int)std::min<int64_t>(nc, nb);
+  const int64_t per = (nb + nc - 1) / nc;
+  if (!ctx->copy_in) {
+    CHEBFI_CUDA(cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
+    CHEBFI_CUDA(cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CHEBFI_CUDA(cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
+      CHEBFI_CUDA(cudaEventCreateWithFlags(&ctx->ev_filt[i], cudaEventDisableTiming));
+      CHEBFI_CUDA(cudaEventCreateWithFlags(&ctx->ev_out[i], cudaEventDisableTiming));
+    }
+  }
+  const int nbuf = nc > 1 ? 2 : 1;
+  for (int i = 0; i < nbuf; ++i) ctx->stage[i].alloc((size_t)npw * per);
+  // the copies start after whatever the caller queued on st before this call
+  CHEBFI_CUDA(cudaEventRecord(ctx->ev_filt[0], st));
+  CHEBFI_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->ev_filt[0], 0));
+  bool used[2] = {false, false};
+  char* host = static_cast<char*>(Y);
+  for (int c = 0; c < nc; ++c) {
+    const int64_t b0 = c * per, nbc = std::min<int64_t>(per, nb - b0);
+    if (nbc <= 0) break;
+    const int k = c % nbuf;
+    double2* dev = ctx->stage[k].p;
+    if (used[k]) CHEBFI_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->ev_out[k], 0));  // chunk c-2 copied out
+    CHEBFI_CUDA(cudaMemcpy2DAsync(dev, sizeof(double2) * npw, host + sizeof(double2) * b0 * ld, sizeof(double2) * ld,
+                                  sizeof(double2) * npw, nbc, cudaMemcpyHostToDevice, ctx->copy_in));
+    CHEBFI_CUDA(cudaEventRecord(ctx->ev_in[k], ctx->copy_in));
+    CHEBFI_CUDA(cudaStreamWaitEvent(st, ctx->ev_in[k], 0));
+    filter_device_block(ctx, dev, nbc, npw, degree, lambda_lo, lambda_hi, prec, st);
+    CHEBFI_CUDA(cudaEventRecord(ctx->ev_filt[k], st));
+    CHEBFI_CUDA(cudaStreamWaitEvent(ctx->copy_out, ctx->ev_filt[k], 0));
+    CHEBFI_CUDA(cudaMemcpy2DAsync(host + sizeof(double2) * b0 * ld, sizeof(double2) * ld, dev, sizeof(double2) * npw,
+                                  sizeof(double2) * npw, nbc, cudaMemcpyDeviceToHost, ctx->copy_out));
+    CHEBFI_CUDA(cudaEventRecord(ctx->ev_out[k], ctx->copy_out));
+    used[k] = true;
+  }
+  // completion on st covers the last copies out
+  for (int k = 0; k < nbuf; ++k)
+    if (used[k]) CHEBFI_CUDA(cudaStreamWaitEvent(st, ctx->ev_out[k], 0));
+  API_END(ctx)
 }
 
 int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream) {

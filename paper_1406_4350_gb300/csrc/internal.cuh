@@ -250,6 +250,19 @@ struct chebfi_ctx {
   chebfi::SplitBF16Buf tcA1, tcA2, tcAG, tcAM;
   chebfi::Work w;
   double bound_rigorous = -1.0;
+  // host-block filter: staging buffers, copy streams and their events (created on first use)
+  chebfi::DevBuf<double2> stage[2];
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_filt[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  ~chebfi_ctx() {
+    for (int i = 0; i < 2; ++i) {
+      if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+      if (ev_filt[i]) cudaEventDestroy(ev_filt[i]);
+      if (ev_out[i]) cudaEventDestroy(ev_out[i]);
+    }
+    if (copy_in) cudaStreamDestroy(copy_in);
+    if (copy_out) cudaStreamDestroy(copy_out);
+  }
   int last_sweeps = 0;            // sweeps performed by the last chebfi_solve
   int64_t last_applies = 0;       // band-H-applications of its filters
 };

@@ -407,3 +407,22 @@ def test_locked_solve_nc24_reaches_exact_eigenvalues_with_less_work(prec, lock_t
     assert np.abs(ev[:k] - exact[:k]).max() <= 1e-8
     assert applies < 0.8 * 8 * cell.nbands * sweeps
     assert _np(rs)[:k].max() <= 10 * lock_tol
+
+
+# ----------------------------------------------------------------------------- host-block filter
+@pytest.mark.parametrize("prec, tol, nchunks", [(0, TOL64, 1), (0, TOL64, 2), (0, TOL64, 3), (2, TOLMIX, 2),
+                                                (1, TOL32, 0)])
+def test_cheb_filter_host_block_in_chunks(prec, tol, nchunks):
+    """The filter on a pinned host block, copied through the GPU in band chunks whose copies
+    overlap the neighbouring chunks' filters, against the oracle (degree 5, 7 bands)."""
+    cell = _tiny_paw(nb=7, seed=14)
+    op = PWOperator.from_cell(cell)
+    hi = ch.upper_bound(op, "rigorous")
+    lo = float(ch.rayleigh_quotients(op, cell.Y0).max())
+    g = _ctx(cell)
+    host = torch.empty((cell.nbands, cell.npw), dtype=torch.complex128, pin_memory=True).T
+    host.copy_(torch.from_numpy(cell.Y0))
+    g.cheb_filter_host(host, 5, lo, hi, prec=prec, nchunks=nchunks)
+    torch.cuda.synchronize()
+    ref = ch.filter_reuse(op, cell.Y0, 5, lo, hi)
+    _close(host.numpy(), ref, tol * 5)
