@@ -766,19 +766,40 @@ const cplx<R>* cheb_step(chebfi_ctx* ctx, bool adjoint, const cplx<R>* X, const 
   return sx;
 }
 
-// gV += scale * dRe<G, H Y>/dV_loc and gD += scale * dRe<G, H Y>/dD for a sorted FP64 pair.
-void accumulate_pair(chebfi_ctx* ctx, const double2* Y, const double2* G, double scale, int64_t nb, double* gV,
+// gV += scale * dRe<G, H Y>/dV_loc and gD += scale * dRe<G, H Y>/dD for a sorted pair, in the
+// pair's precision (the sums over bands and grid points are accumulated in FP64).
+template <typename R> struct GradBufs;
+template <> struct GradBufs<double> {
+  static DevBuf<double2>& q(chebfi_ctx* c) { return c->w.pc; }
+  static DevBuf<double2>& p(chebfi_ctx* c) { return c->w.pt; }
+  static DevBuf<double2>& T(chebfi_ctx* c) { return c->w.T2; }
+  static DevBuf<double2>& Rg(chebfi_ctx* c) { return c->w.tmp; }
+  static DevBuf<double2>& Gg(chebfi_ctx* c) { return c->w.tmp2; }
+};
+template <> struct GradBufs<float> {
+  static DevBuf<float2>& q(chebfi_ctx* c) { return c->w.fpq; }
+  static DevBuf<float2>& p(chebfi_ctx* c) { return c->w.fpt; }
+  static DevBuf<float2>& T(chebfi_ctx* c) { return c->w.fgT; }
+  static DevBuf<float2>& Rg(chebfi_ctx* c) { return c->w.fgR; }
+  static DevBuf<float2>& Gg(chebfi_ctx* c) { return c->w.fgG; }
+};
+
+template <typename R>
+void accumulate_pair(chebfi_ctx* ctx, const cplx<R>* Y, const cplx<R>* G, double scale, int64_t nb, double* gV,
                      double* gD, cudaStream_t st) {
-  Work& w = ctx->w;
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   if (gD && nq > 0) {
-    w.pc.alloc((size_t)nq * nb);
-    w.pt.alloc((size_t)nq * nb);
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, G, npw, 0.0, w.pc.p, nq, st, &w.splitk, "gemm_grad");
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, Y, npw, 0.0, w.pt.p, nq, st, &w.splitk, "gemm_grad");
-    block_outer_grad(ctx, w.pc.p, w.pt.p, nq, nb, gD, st, scale, true);
+    DevBuf<cplx<R>>& q = GradBufs<R>::q(ctx);
+    DevBuf<cplx<R>>& pp = GradBufs<R>::p(ctx);
+    q.alloc((size_t)nq * nb);
+    pp.alloc((size_t)nq * nb);
+    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, G, npw, 0.0, q.p, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, pp.p, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+    block_outer_grad(ctx, q.p, pp.p, nq, nb, gD, st, scale, true);
   }
-  if (gV) vloc_gradient(ctx, Y, G, nb, gV, st, w.T2, w.tmp, w.tmp2, scale, true);
+  if (gV)
+    vloc_gradient<R>(ctx, Y, G, nb, gV, st, GradBufs<R>::T(ctx), GradBufs<R>::Rg(ctx), GradBufs<R>::Gg(ctx), scale,
+                     true);
 }
 
 void to_f64(const chebfi_ctx* ctx, const float2* x, double2* y, int64_t nb, cudaStream_t st) {
@@ -818,10 +839,6 @@ void filter_backward(chebfi_ctx* ctx, int64_t nb, int n, double lo, double hi, i
                  Ops<R>::pb(ctx).p};
   auto alpha = [&](int k) { return (k == 0 ? 1.0 : 2.0) / r; };
   const size_t bytes = sizeof(C) * blk;
-  if (sizeof(R) == 4) {
-    w.gA.alloc(blk);
-    w.gB.alloc(blk);
-  }
   from_f64<R>(ctx, w.Ya.p, ck(0, 1), nb, st);
   from_f64<R>(ctx, w.Yb.p, lam1, nb, st);
   // forward pass: Y_1 .. Y_{n-1} in two rolling buffers, checkpoints at multiples of s
@@ -856,15 +873,7 @@ void filter_backward(chebfi_ctx* ctx, int64_t nb, int n, double lo, double hi, i
       // L_k = a (H S^{-1} L_{k+1} - c L_{k+1}) - L_{k+2}, written over L_{k+2}
       const C* u = cheb_step<R>(ctx, true, lam1, have2 ? lam2 : nullptr, lam2, a, c, 1.0, sb, nb, st);
       const C* yk = segb + blk * (k - j);
-      if (gV || gD) {
-        if constexpr (sizeof(R) == 8) {
-          accumulate_pair(ctx, yk, u, a, nb, gV, gD, st);
-        } else {
-          to_f64(ctx, yk, w.gA.p, nb, st);
-          to_f64(ctx, u, w.gB.p, nb, st);
-          accumulate_pair(ctx, w.gA.p, w.gB.p, a, nb, gV, gD, st);
-        }
-      }
+      if (gV || gD) accumulate_pair<R>(ctx, yk, u, a, nb, gV, gD, st);
       std::swap(lam1, lam2);
       have2 = true;
     }
@@ -1629,7 +1638,7 @@ int chebfi_apply_H_backward(chebfi_ctx* ctx, const void* Y, const void* G, void*
     gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pc.p, nq, st, &w.splitk, "gemm_H");
     block_outer_grad(ctx, w.pa.p, w.pc.p, nq, nb, gD, st);
   }
-  if (gV) vloc_gradient(ctx, w.Ya.p, w.Yb.p, nb, gV, st, w.T2, w.tmp, w.tmp2);
+  if (gV) vloc_gradient<double>(ctx, w.Ya.p, w.Yb.p, nb, gV, st, w.T2, w.tmp, w.tmp2);
   API_END(ctx)
 }
 

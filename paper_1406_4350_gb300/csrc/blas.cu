@@ -229,9 +229,10 @@ __global__ void k_blockdiag_apply_c(int64_t nproj, int64_t nb, const int32_t* __
 }
 
 // one thread per (projector i, position j within i's atom block)
+template <typename C>
 __global__ void k_block_outer_grad(int64_t nproj, const int32_t* __restrict__ atom_of, const int32_t* __restrict__ offs,
-                                   const int64_t* __restrict__ blk_off, const double2* __restrict__ q,
-                                   const double2* __restrict__ p, int64_t ldp, int64_t nb, double* __restrict__ gD,
+                                   const int64_t* __restrict__ blk_off, const C* __restrict__ q,
+                                   const C* __restrict__ p, int64_t ldp, int64_t nb, double* __restrict__ gD,
                                    double scale, int accumulate) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nproj * 64) return;
@@ -243,8 +244,8 @@ __global__ void k_block_outer_grad(int64_t nproj, const int32_t* __restrict__ at
   const int64_t j = o + jl;
   double acc = 0.0;
   for (int64_t b = 0; b < nb; ++b) {
-    const double2 u = q[i + b * ldp], v = p[j + b * ldp];
-    acc += u.x * v.x + u.y * v.y;
+    const C u = q[i + b * ldp], v = p[j + b * ldp];
+    acc += (double)u.x * (double)v.x + (double)u.y * (double)v.y;
   }
   double* g = gD + blk_off[a] + (i - o) * na + jl;
   *g = scale * acc + (accumulate ? *g : 0.0);
@@ -374,14 +375,19 @@ void hermitize(int64_t n, double2* A, int64_t lda, cudaStream_t st) {
   if (n == 0) return;
   CHEBFI_LAUNCH("k_hermitize", st, k_hermitize<<<nblocks(n * n), 256, 0, st>>>(n, A, lda));
 }
-void block_outer_grad(const chebfi_ctx* ctx, const double2* q, const double2* p, int64_t ldp, int64_t nb, double* gD,
+template <typename C>
+void block_outer_grad(const chebfi_ctx* ctx, const C* q, const C* p, int64_t ldp, int64_t nb, double* gD,
                       cudaStream_t st, double scale, bool accumulate) {
   if (ctx->nproj == 0) return;
   CHEBFI_LAUNCH("k_block_outer_grad", st,
-                k_block_outer_grad<<<nblocks(ctx->nproj * 64), 256, 0, st>>>(ctx->nproj, ctx->d_atom_of.p, ctx->d_offs.p,
-                                                                          ctx->d_blk_off.p, q, p, ldp, nb, gD,
-                                                                          scale, accumulate ? 1 : 0));
+                k_block_outer_grad<C><<<nblocks(ctx->nproj * 64), 256, 0, st>>>(ctx->nproj, ctx->d_atom_of.p, ctx->d_offs.p,
+                                                                             ctx->d_blk_off.p, q, p, ldp, nb, gD,
+                                                                             scale, accumulate ? 1 : 0));
 }
+template void block_outer_grad<double2>(const chebfi_ctx*, const double2*, const double2*, int64_t, int64_t, double*,
+                                        cudaStream_t, double, bool);
+template void block_outer_grad<float2>(const chebfi_ctx*, const float2*, const float2*, int64_t, int64_t, double*,
+                                       cudaStream_t, double, bool);
 void blockdiag_apply_c(const chebfi_ctx* ctx, const double2* Bblk, const int64_t* cblk_off, const double2* p,
                        int64_t ldp, double2* out, int64_t ldo, int64_t nb, cudaStream_t st) {
   if (ctx->nproj == 0 || nb == 0) return;

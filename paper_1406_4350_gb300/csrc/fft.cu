@@ -413,8 +413,9 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   }
 }
 
-void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_t nb, double* gV, cudaStream_t st,
-                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb, double scale, bool accumulate) {
+template <typename R>
+void vloc_gradient(chebfi_ctx* ctx, const cplx<R>* Ys, const cplx<R>* Gs, int64_t nb, double* gV, cudaStream_t st,
+                   DevBuf<cplx<R>>& T, DevBuf<cplx<R>>& Rb, DevBuf<cplx<R>>& Gb, double scale, bool accumulate) {
   const SphereFFT& s = ctx->sph;
   const int n1 = s.n1, n2 = s.n2, n3 = s.n3;
   const int64_t n = (int64_t)n1 * n2 * n3;
@@ -440,12 +441,12 @@ void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_
   pa.ncolp = sa.ncolp;
   pa.col_off = s.col_off.p;
   pa.row_off = s.rows_act.p;
-  const FFTPlan<double> px = ctx->ax[0].plan<double>(), py = ctx->ax[1].plan<double>(), pz = ctx->ax[2].plan<double>();
-  const size_t zbytes = (size_t)kCB * s.zpitch * sizeof(double2);
-  const size_t pbytes = (size_t)n1 * s.pitch * sizeof(double2);
+  const FFTPlan<R> px = ctx->ax[0].plan<R>(), py = ctx->ax[1].plan<R>(), pz = ctx->ax[2].plan<R>();
+  const size_t zbytes = (size_t)kCB * s.zpitch * sizeof(cplx<R>);
+  const size_t pbytes = (size_t)n1 * s.pitch * sizeof(cplx<R>);
   CHEBFI_REQUIRE(pbytes <= 227 * 1024, CHEBFI_ERR_ARG, "FFT plane does not fit in shared memory");
-  set_smem<double>((const void*)k_zinv<double>, zbytes);
-  set_smem<double>((const void*)k_plane_real<double>, pbytes);
+  set_smem<R>((const void*)k_zinv<R>, zbytes);
+  set_smem<R>((const void*)k_plane_real<R>, pbytes);
   // bands per chunk: two full grids per band, at most ~512 MB of grids
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nb, ((int64_t)1 << 25) / n));
   T.alloc((size_t)sa.ldt * chunk);
@@ -455,18 +456,22 @@ void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_
     const int nbc = (int)std::min<int64_t>(chunk, nb - b0);
     dim3 gz((s.ncol + kCB - 1) / kCB, nbc);
     for (int which = 0; which < 2; ++which) {
-      const double2* src = (which == 0 ? Ys : Gs) + b0 * ctx->npw;
-      double2* dst = which == 0 ? Rb.p : Gb.p;
-      CHEBFI_LAUNCH("k_zinv", st, k_zinv<double><<<gz, kThreads, zbytes, st>>>(src, ctx->npw, T.p, sa, pz));
+      const cplx<R>* src = (which == 0 ? Ys : Gs) + b0 * ctx->npw;
+      cplx<R>* dst = which == 0 ? Rb.p : Gb.p;
+      CHEBFI_LAUNCH("k_zinv", st, k_zinv<R><<<gz, kThreads, zbytes, st>>>(src, ctx->npw, T.p, sa, pz));
       CHEBFI_LAUNCH("k_plane_real", st,
-                    k_plane_real<double><<<dim3(n3, nbc), kThreads, pbytes, st>>>(T.p, pa, px, py, dst));
+                    k_plane_real<R><<<dim3(n3, nbc), kThreads, pbytes, st>>>(T.p, pa, px, py, dst));
     }
     CHEBFI_LAUNCH("k_density_accum", st,
-                  k_density_accum<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n1, n2, n3, nbc, Rb.p, Gb.p,
+                  k_density_accum<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n1, n2, n3, nbc, Rb.p, Gb.p,
                                                                                     scale / (double)n, gV));
   }
 }
 
+template void vloc_gradient<double>(chebfi_ctx*, const double2*, const double2*, int64_t, double*, cudaStream_t,
+                                    DevBuf<double2>&, DevBuf<double2>&, DevBuf<double2>&, double, bool);
+template void vloc_gradient<float>(chebfi_ctx*, const float2*, const float2*, int64_t, double*, cudaStream_t,
+                                   DevBuf<float2>&, DevBuf<float2>&, DevBuf<float2>&, double, bool);
 template void local_apply<double>(chebfi_ctx*, const double2*, int64_t, int64_t, double2*, LocalEpi<double>, cudaStream_t);
 template void local_apply<float>(chebfi_ctx*, const float2*, int64_t, int64_t, float2*, LocalEpi<float>, cudaStream_t);
 

@@ -30,11 +30,13 @@ size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb);
 // Derivative of (V_loc psi) with respect to V_loc for a real loss whose gradient at the
 // output is g: gV(x, y, z) = (1/N^3) sum_b Re(conj(g_b(r)) psi_b(r)) with psi_b, g_b the
 // real-space values of sorted-order sphere blocks Ys, Gs (ld = npw).  FP64.
-void vloc_gradient(chebfi_ctx* ctx, const double2* Ys, const double2* Gs, int64_t nb, double* gV, cudaStream_t st,
-                   DevBuf<double2>& T, DevBuf<double2>& Rb, DevBuf<double2>& Gb, double scale = 1.0,
+template <typename R>
+void vloc_gradient(chebfi_ctx* ctx, const cplx<R>* Ys, const cplx<R>* Gs, int64_t nb, double* gV, cudaStream_t st,
+                   DevBuf<cplx<R>>& T, DevBuf<cplx<R>>& Rb, DevBuf<cplx<R>>& Gb, double scale = 1.0,
                    bool accumulate = false);
 // gD[entry (i, j) of atom block a] = scale * sum_b Re(conj(q_ib) p_jb)  (+= if accumulate)
-void block_outer_grad(const chebfi_ctx* ctx, const double2* q, const double2* p, int64_t ldp, int64_t nb, double* gD,
+template <typename C>
+void block_outer_grad(const chebfi_ctx* ctx, const C* q, const C* p, int64_t ldp, int64_t nb, double* gD,
                       cudaStream_t st, double scale = 1.0, bool accumulate = false);
 // the two-pass FFT kernels cover cubic grids of a few compiled sizes; split_index(n, p) is
 // the natural index held at position p of their split order
