@@ -19,7 +19,9 @@
  *    is COPIED at the call; the caller may free its copy afterwards.
  *  - Work is enqueued on the given CUDA stream (cudaStream_t passed as void*, NULL =
  *    legacy default stream) and runs asynchronously, except where a function says it
- *    synchronises.  The context is not thread-safe: one host thread at a time.
+ *    synchronises.  The context is not thread-safe: one host thread at a time.  Its
+ *    workspaces are shared by all its calls, so calls on one context must be ordered on
+ *    the device too (one stream, or synchronised between streams).
  *  - Return value 0 = success; negative = error, with a message from chebfi_last_error.
  *    Argument and state errors are detected before any work is enqueued.  Errors found
  *    on the device (a Gram matrix that is not positive definite, a Jacobi sweep limit)
@@ -306,7 +308,9 @@ int chebfi_batch_set_tiles(chebfi_batch* batch, int prec, const int* shapes, int
  * caller's plane-wave order) for k = 0..nk-1: Algorithm 2's filter of the given degree on
  * [lambda_lo[k], lambda_hi[k]] (host arrays of nk doubles), exactly as chebfi_cheb_filter
  * computes it per k-point, in the FP64 or FP32 form.  Stream-ordered on `stream`; the first
- * call of a (form, degree) pair tunes and captures, later calls replay the graph. */
+ * call of a (form, degree) pair tunes and captures, later calls replay the graph.  The
+ * batch's workspaces and per-call descriptor table are shared by its calls: calls on one
+ * batch must be ordered (one stream, or synchronised between streams). */
 int chebfi_batch_cheb_filter(chebfi_batch* batch, void* const* Y, const int64_t* ld, int degree,
                              const double* lambda_lo, const double* lambda_hi, int prec, void* stream);
 
