@@ -1012,7 +1012,7 @@ int chebfi_set_sphere(chebfi_ctx* ctx, int64_t npw, const int32_t* miller) {
       col_start.push_back((int32_t)j);
       const int x = (int)(key[u] / n2), y = (int)(key[u] % n2);
       col_off.push_back(rx[x] * s.pitch + ry[y]);
-      col_nat.push_back(x * s.pitch + y);
+      col_nat.push_back(((x + n1 / 2) % n1) * s.pitch + y);
       xact[x] = 1;
     }
     pw_line[j] = (int32_t)col_start.size() - 1;
@@ -1021,12 +1021,18 @@ int chebfi_set_sphere(chebfi_ctx* ctx, int64_t npw, const int32_t* miller) {
   }
   s.ncol = (int)col_start.size();
   col_start.push_back((int32_t)npw);
+  // The compile-time-length kernels keep plane row x in slot (x + n1/2) mod n1: the rows
+  // holding sphere columns (signed x in [-m, m]) then sit in consecutive slots, so the y
+  // passes over them, one row per thread, meet no bank conflicts at the wrap of x.  A cyclic
+  // relabelling of x only multiplies the real-space values of the x transform by a phase,
+  // which the transform back removes; V_loc is indexed by the transform's own positions.
   std::vector<int32_t> rows, rows_nat;
   for (int x = 0; x < n1; ++x)
-    if (xact[x]) {
-      rows.push_back(rx[x] * s.pitch);
-      rows_nat.push_back(x * s.pitch);
-    }
+    if (xact[x]) rows.push_back(rx[x] * s.pitch);
+  for (int r = 0; r < n1; ++r) {
+    const int x = (r - n1 / 2 + n1) % n1;
+    if (xact[x]) rows_nat.push_back(r * s.pitch);
+  }
   s.nxa = (int)rows.size();
   s.col_start.upload(col_start.data(), col_start.size());
   s.pw_line.upload(pw_line.data(), npw);

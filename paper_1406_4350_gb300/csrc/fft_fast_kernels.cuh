@@ -27,8 +27,8 @@ struct FastArgs {
   const int32_t* col_start;
   const int32_t* pw_line;
   const int32_t* pw_z;      // natural z of each sorted sphere point
-  const int32_t* col_off;   // natural x * pitch + y of each column
-  const int32_t* row_off;   // natural x * pitch of each active x
+  const int32_t* col_off;   // slot(x) * pitch + y of each column (plane rows cyclically shifted)
+  const int32_t* row_off;   // slot(x) * pitch of each active x
 };
 
 template <typename R, int N>

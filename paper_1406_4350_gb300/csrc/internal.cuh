@@ -158,8 +158,8 @@ struct SphereFFT {
   DevBuf<int32_t> rows_act;    // active rows rev(x) of the plane (nxa)
   // natural-index maps of the compile-time-length path
   DevBuf<int32_t> pw_z;        // sorted sphere point -> z
-  DevBuf<int32_t> col_off_nat; // column -> x * pitch + y
-  DevBuf<int32_t> rows_nat;    // active rows x * pitch
+  DevBuf<int32_t> col_off_nat; // column -> slot(x) * pitch + y, slot(x) = (x + n1/2) mod n1
+  DevBuf<int32_t> rows_nat;    // slot(x) * pitch of the active rows, consecutive slots
 };
 
 // Workspace grown on demand (never shrinks while the context lives).
