@@ -720,6 +720,7 @@ void batch_filter(chebfi_batch* bt, void* const* Y, const int64_t* ld, int degre
   autotune<R>(bt, st);
   ensure_ws<R>(bt);
   set_fft_smem_n<R>(bt);
+  fk::init_twiddles();
   // per-call descriptor fields
   auto& h = BatchOps<R>::hdesc(bt);
   for (int k = 0; k < bt->nk; ++k) {

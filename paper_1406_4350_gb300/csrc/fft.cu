@@ -292,6 +292,7 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   const R* Vs = sizeof(R) == 8 ? (const R*)ctx->d_vs.p : (const R*)ctx->d_vsf.p;
   const size_t zbytes = (size_t)(N + kCBF * s.zpitch) * sizeof(cplx<R>);
   const size_t pbytes = (size_t)(N + N * s.pitch) * sizeof(cplx<R>);
+  fk::init_twiddles();
   set_smem<R>((const void*)k_plane_f<R, N>, pbytes);
   set_smem<R>((const void*)k_zinv_f<R, N>, zbytes);
   set_smem<R>((const void*)k_zfwd_f<R, N>, zbytes);

@@ -137,17 +137,24 @@ template <> struct Plan<120> { static constexpr int NA = 12, NB = 10; };
 template <> struct Plan<128> { static constexpr int NA = 16, NB = 8; };
 template <> struct Plan<144> { static constexpr int NA = 12, NB = 12; };
 
-// twiddle w^e = exp(SIGN 2 pi i e / N) from the table tw[e] = exp(-2 pi i e / N)
+// twiddle w^e = exp(SIGN 2 pi i e / N) from the table tw[e] = exp(-2 pi i e / N), held in
+// memory (a pointer) or behind an accessor object tw(e)
 template <int SIGN, typename C> __host__ __device__ __forceinline__ C twN(const C* tw, int e) {
   C w = tw[e];
+  if (SIGN > 0) w.y = -w.y;
+  return w;
+}
+template <int SIGN, typename T>
+__host__ __device__ __forceinline__ auto twN(const T& tw, int e) -> decltype(tw(e)) {
+  auto w = tw(e);
   if (SIGN > 0) w.y = -w.y;
   return w;
 }
 
 // F: natural in, split order out (position NB*ka + kb holds X[ka + NA*kb]).
 // Each pass is a loop over (line, sub-DFT) items of thread `tid` of `nthr`.
-template <int N, int SIGN, typename C>
-__host__ __device__ __forceinline__ void F_passA(C* buf, int nlines, LineMap lm, int es, const C* tw, int tid,
+template <int N, int SIGN, typename C, typename TW>
+__host__ __device__ __forceinline__ void F_passA(C* buf, int nlines, LineMap lm, int es, const TW& tw, int tid,
                                                  int nthr) {
   constexpr int NA = Plan<N>::NA, NB = Plan<N>::NB;
   for (int t = tid; t < nlines * NB; t += nthr) {
@@ -176,8 +183,8 @@ __host__ __device__ __forceinline__ void F_passB(C* buf, int nlines, LineMap lm,
   }
 }
 // G: split order in, natural out (the transpose of F: pass B, twiddles, pass A).
-template <int N, int SIGN, typename C>
-__host__ __device__ __forceinline__ void G_passB(C* buf, int nlines, LineMap lm, int es, const C* tw, int tid,
+template <int N, int SIGN, typename C, typename TW>
+__host__ __device__ __forceinline__ void G_passB(C* buf, int nlines, LineMap lm, int es, const TW& tw, int tid,
                                                  int nthr) {
   constexpr int NA = Plan<N>::NA, NB = Plan<N>::NB;
   for (int t = tid; t < nlines * NA; t += nthr) {
@@ -207,15 +214,15 @@ __host__ __device__ __forceinline__ void G_passA(C* buf, int nlines, LineMap lm,
 }
 
 #ifdef __CUDACC__
-template <int N, int SIGN, typename C>
-__device__ __forceinline__ void lines_F(C* buf, int nlines, LineMap lm, int es, const C* tw) {
+template <int N, int SIGN, typename C, typename TW>
+__device__ __forceinline__ void lines_F(C* buf, int nlines, LineMap lm, int es, const TW& tw) {
   F_passA<N, SIGN>(buf, nlines, lm, es, tw, threadIdx.x, blockDim.x);
   __syncthreads();
   F_passB<N, SIGN>(buf, nlines, lm, es, threadIdx.x, blockDim.x);
   __syncthreads();
 }
-template <int N, int SIGN, typename C>
-__device__ __forceinline__ void lines_G(C* buf, int nlines, LineMap lm, int es, const C* tw) {
+template <int N, int SIGN, typename C, typename TW>
+__device__ __forceinline__ void lines_G(C* buf, int nlines, LineMap lm, int es, const TW& tw) {
   G_passB<N, SIGN>(buf, nlines, lm, es, tw, threadIdx.x, blockDim.x);
   __syncthreads();
   G_passA<N, SIGN>(buf, nlines, lm, es, threadIdx.x, blockDim.x);

@@ -11,6 +11,9 @@
 
 #include <cuda_bf16.h>
 
+#include <cmath>
+#include <vector>
+
 #include "fft_fast.cuh"
 #include "internal.cuh"
 #include "kernels.cuh"
@@ -36,14 +39,58 @@ __device__ __forceinline__ void load_tw(cplx<R>* s, const cplx<R>* g) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) s[i] = g[i];
 }
 
+// Twiddle tables tw[e] = exp(-2 pi i e / N) of the compiled line lengths, in constant memory:
+// a warp of a pass reads one entry (two where it straddles two sub-transforms), which the
+// constant cache broadcasts without using the shared-memory pipe that bounds these kernels.
+// Each translation unit has its own copy, filled by init_twiddles before its first launch.
+template <int N> struct TwOff;
+template <> struct TwOff<24> { static constexpr int v = 0; };
+template <> struct TwOff<32> { static constexpr int v = 24; };
+template <> struct TwOff<48> { static constexpr int v = 56; };
+template <> struct TwOff<64> { static constexpr int v = 104; };
+template <> struct TwOff<72> { static constexpr int v = 168; };
+template <> struct TwOff<96> { static constexpr int v = 240; };
+constexpr int kTwTotal = 336;
+static __constant__ float2 c_twf[kTwTotal];
+static __constant__ double2 c_twd[kTwTotal];
+
+template <typename R, int N> struct ConstTw;
+template <int N> struct ConstTw<float, N> {
+  __device__ __forceinline__ float2 operator()(int e) const { return c_twf[TwOff<N>::v + e]; }
+};
+template <int N> struct ConstTw<double, N> {
+  __device__ __forceinline__ double2 operator()(int e) const { return c_twd[TwOff<N>::v + e]; }
+};
+
+// Fill this translation unit's tables on the current device (once per device; not inside a
+// stream capture).
+static inline void init_twiddles() {
+  static bool done[64] = {false};
+  int dev = 0;
+  CHEBFI_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  const int lens[6] = {24, 32, 48, 64, 72, 96};
+  std::vector<float2> f;
+  std::vector<double2> d;
+  for (int n : lens)
+    for (int k = 0; k < n; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)n;
+      d.push_back(make_double2(std::cos(a), -std::sin(a)));
+      f.push_back(make_float2((float)d.back().x, (float)d.back().y));
+    }
+  CHEBFI_CUDA(cudaMemcpyToSymbol(c_twf, f.data(), sizeof(float2) * f.size()));
+  CHEBFI_CUDA(cudaMemcpyToSymbol(c_twd, d.data(), sizeof(double2) * d.size()));
+  done[dev] = true;
+}
+
 // sphere block b, columns [c0, c0 + kCBF) -> inverse z transform -> column buffer T
 template <typename R, int N3>
 __device__ __forceinline__ void zinv_body(const cplx<R>* __restrict__ Y, int64_t ldy, cplx<R>* __restrict__ T,
                                           const FastArgs& fa, const cplx<R>* __restrict__ twz, int c0, int64_t b,
                                           unsigned char* smem_raw) {
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* lines = tw + N3;
-  load_tw<R, N3>(tw, twz);
+  (void)twz;
+  const ConstTw<R, N3> tw;
+  cplx<R>* lines = reinterpret_cast<cplx<R>*>(smem_raw) + N3;
   const int nc = min(kCBF, fa.ncol - c0);
   const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
   for (int i = threadIdx.x; i < kCBF * fa.zpitch; i += blockDim.x) lines[i] = zero;
@@ -68,9 +115,9 @@ template <typename R, int N>
 __device__ __forceinline__ void plane_body(cplx<R>* __restrict__ T, const R* __restrict__ Vs, const FastArgs& fa,
                                            const cplx<R>* __restrict__ twxy, int z, int64_t b,
                                            unsigned char* smem_raw) {
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* plane = tw + N;
-  load_tw<R, N>(tw, twxy);
+  (void)twxy;
+  const ConstTw<R, N> tw;
+  cplx<R>* plane = reinterpret_cast<cplx<R>*>(smem_raw) + N;
   const cplx<R> zero = cmake<cplx<R>>(0.0, 0.0);
   for (int i = threadIdx.x; i < N * fa.pitch; i += blockDim.x) plane[i] = zero;
   __syncthreads();
@@ -122,9 +169,9 @@ template <typename R, int N3>
 __device__ __forceinline__ void zfwd_body(const cplx<R>* __restrict__ T, const FastArgs& fa,
                                           const cplx<R>* __restrict__ twz, const R* __restrict__ K,
                                           const LocalEpi<R>& ep, int c0, int64_t b, unsigned char* smem_raw) {
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* lines = tw + N3;
-  load_tw<R, N3>(tw, twz);
+  (void)twz;
+  const ConstTw<R, N3> tw;
+  cplx<R>* lines = reinterpret_cast<cplx<R>*>(smem_raw) + N3;
   const int nc = min(kCBF, fa.ncol - c0);
   const cplx<R>* t = T + b * fa.ldt + c0;
   for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
