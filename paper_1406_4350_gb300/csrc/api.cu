@@ -277,7 +277,7 @@ float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb0, int degr
     w.Zb.alloc((size_t)ldzb * nb);
     split_block(npw, nb, cur, npw, w.Zb, st);
     tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)pcur, 2 * nq, status, st,
-            "tc_gemm_PhY");
+            "tc_gemm_PhY", &ctx->w.tcws);
   }
   for (int k = 0; k < degree; ++k) {
     const int64_t nb = active ? active[k] : nb0;  // bands still being filtered (a prefix)
@@ -301,24 +301,24 @@ float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb0, int degr
     if (nq > 0) {
       // P^H H Y_k = P^H Z + G D p_k
       tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)b.pz, 2 * nq, status,
-              st, "tc_gemm_PhY");
+              st, "tc_gemm_PhY", &ctx->w.tcws);
       blockdiag_apply<float>(ctx, ctx->d_Dblkf.p, pcur, nq, b.pw, nq, nb, st);
       split_block(nq, nb, b.pw, nq, w.Sb, st);
       tc_gemm(ctx->tcAG.view(), w.Sb.view(), 2 * nq, nb, 2 * nq, 1.f, 1.f, (float*)b.pz, 2 * nq, (float*)b.pz, 2 * nq,
-              status, st, "tc_gemm_small");
+              status, st, "tc_gemm_small", &ctx->w.tcws);
       if (ctx->paw) {
         split_block(nq, nb, b.pz, nq, w.Sb, st);
         tc_gemm(ctx->tcAM.view(), w.Sb.view(), 2 * nq, nb, 2 * nq, 1.f, 0.f, nullptr, 0, (float*)b.pq, 2 * nq, status,
-                st, "tc_gemm_small");
+                st, "tc_gemm_small", &ctx->w.tcws);
         axpby<float>(nq, nb, 1.f, b.pw, nq, -1.f, b.pq, nq, b.pw, nq, st);
         split_block(nq, nb, b.pq, nq, w.Sb, st);
         tc_gemm(ctx->tcAG.view(), w.Sb.view(), 2 * nq, nb, 2 * nq, -1.f, 1.f, (float*)b.pz, 2 * nq, (float*)b.pz,
-                2 * nq, status, st, "tc_gemm_small");
+                2 * nq, status, st, "tc_gemm_small", &ctx->w.tcws);
       }
       // Y_{k+1} = T + a P W
       split_block(nq, nb, b.pw, nq, w.Sb, st);
       tc_gemm(ctx->tcA2.view(), w.Sb.view(), 2 * npw, nb, 2 * nq, (float)a, 1.f, (float*)prev, 2 * npw, (float*)prev,
-              2 * npw, status, st, "tc_gemm_PW");
+              2 * npw, status, st, "tc_gemm_PW", &ctx->w.tcws);
       cheb_combine<float>(nq, nb, (float)a, b.pz, nq, (float)c, pcur, nq, (float)bp, k == 0 ? nullptr : pprev, nq,
                           pprev, nq, st);
     }
@@ -1267,11 +1267,11 @@ int chebfi_apply_H(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t
       w.Zb.alloc((size_t)w.Zb.ld * nb);
       split_block(npw, nb, w.fYa.p, npw, w.Zb, st);
       tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)w.fpa.p, 2 * nq,
-              ctx->d_status.p, st, "tc_gemm_PhY");
+              ctx->d_status.p, st, "tc_gemm_PhY", &ctx->w.tcws);
       blockdiag_apply<float>(ctx, ctx->d_Dblkf.p, w.fpa.p, nq, w.fpb.p, nq, nb, st);
       split_block(nq, nb, w.fpb.p, nq, w.Sb, st);
       tc_gemm(ctx->tcA2.view(), w.Sb.view(), 2 * npw, nb, 2 * nq, 1.f, 1.f, (float*)w.fZ.p, 2 * npw, (float*)w.fZ.p,
-              2 * npw, ctx->d_status.p, st, "tc_gemm_PW");
+              2 * npw, ctx->d_status.p, st, "tc_gemm_PW", &ctx->w.tcws);
     } else {
       apply_H_sorted<float>(ctx, w.fYa.p, w.fZ.p, w.fpa.p, w.fpb.p, w.fT1.p, nb, st);
     }

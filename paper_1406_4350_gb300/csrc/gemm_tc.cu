@@ -52,6 +52,8 @@ struct Args {
   const float* C;
   int64_t ldc;
   int* status;
+  int splits;  // K split over this many work units per tile (partial sums go to ws)
+  float* ws;   // splits x M x N column-major partial sums when splits > 1
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -175,9 +177,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int num_k = (args.K + BK - 1) / BK;
-  const int num_chunks = (num_k + CHUNK - 1) / CHUNK;
   const int tiles_n = (args.N + BN - 1) / BN;
   const int tiles = tiles_n * ((args.M + BM - 1) / BM);
+  // work unit u: tile u % tiles, k-tiles [kb, ke) of split u / tiles
+  const int units = tiles * args.splits;
+  const int kpt = (num_k + args.splits - 1) / args.splits;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -208,9 +212,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       int g = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int tile = u % tiles, kb = (u / tiles) * kpt, ke = min(num_k, kb + kpt);
         const int n0 = (tile % tiles_n) * BN, m0 = (tile / tiles_n) * BM;
-        for (int kt = 0; kt < num_k; ++kt, ++g) {
+        for (int kt = kb; kt < ke; ++kt, ++g) {
           const int s = g % STAGES;
           const uint32_t par = (g / STAGES) & 1;
           if (g >= STAGES && !mbar_wait(&empty[s], par ^ 1)) {
@@ -233,8 +238,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
       bool ok = true;
       int g = 0, gch = 0;
-      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        int kt = 0;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int kb = (u / tiles) * kpt, ke = min(num_k, kb + kpt);
+        const int num_chunks = (ke - kb + CHUNK - 1) / CHUNK;
+        int kt = kb;
         for (int ch = 0; ch < num_chunks && ok; ++ch, ++gch) {
           const int acc = gch & 1;
           if (gch >= 2 && !mbar_wait(&acc_empty[acc], ((gch >> 1) - 1) & 1)) {
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(acc * BN);
-          const int kend = min(num_k, (ch + 1) * CHUNK);
+          const int kend = min(ke, kb + (ch + 1) * CHUNK);
           for (; kt < kend; ++kt, ++g) {
             const int s = g % STAGES;
             const uint32_t par = (g / STAGES) & 1;
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-            const bool first = kt == ch * CHUNK;
+            const bool first = kt == kb + ch * CHUNK;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               const uint32_t off = kk * 32;  // 16 bf16 along K
@@ -277,7 +284,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int lane_base = 32 * (warp % 4);
     bool ok = true;
     int gch = 0;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      const int tile = u % tiles, split = u / tiles, kb = split * kpt, ke = min(num_k, kb + kpt);
+      const int num_chunks = (ke - kb + CHUNK - 1) / CHUNK;
       const int n0 = (tile % tiles_n) * BN, m0 = (tile / tiles_n) * BM;
       const int m = m0 + lane_base + lane;
       float racc[BN];
@@ -302,7 +311,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[acc]);
       }
-      if (ok && m < args.M) {
+      if (ok && m < args.M && args.splits > 1) {
+        // partial sum of this K split; k_tc_reduce applies alpha and beta
+        const int nvalid = min(BN, args.N - n0);
+        float* w = args.ws + (int64_t)split * args.M * args.N + (int64_t)m + (int64_t)n0 * args.M;
+#pragma unroll
+        for (int j = 0; j < BN; ++j)
+          if (j < nvalid) w[(int64_t)j * args.M] = racc[j];
+      } else if (ok && m < args.M) {
         // C may be D itself: read every C value of the row first (no store in between, so
         // the loads can all be in flight together), then store
         const int nvalid = min(BN, args.N - n0);
@@ -327,6 +343,32 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// D = alpha * (sum of the K-split partial sums, in split order) + beta * C; C may be D
+// (M x N <= 2^26 in split mode, so 32-bit indices; one thread per 4 consecutive rows)
+__global__ void k_tc_reduce(int M, int N, int splits, const float* __restrict__ ws, float alpha, float beta,
+                            const float* C, int64_t ldc, float* D, int64_t ldd) {
+  const int mn = M * N;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= mn) return;
+  const int n = i0 / M;
+  int m = i0 - n * M;
+  const float* c = C + (int64_t)n * ldc;
+  float* d = D + (int64_t)n * ldd;
+  for (int q = 0; q < 4 && i0 + q < mn; ++q, ++m) {
+    if (m == M) {  // the four rows ran into the next column
+      m = 0;
+      c += ldc;
+      d += ldd;
+    }
+    const int i = i0 + q;
+    float acc = ws[i];
+    for (int sp = 1; sp < splits; ++sp) acc += ws[sp * mn + i];
+    float r = alpha * acc;
+    if (beta != 0.f) r = fmaf(beta, c[m], r);
+    d[m] = r;
   }
 }
 
@@ -369,7 +411,8 @@ CUtensorMap make_map(const __nv_bfloat16* base, int64_t k, int64_t rows, int64_t
 }  // namespace tc
 
 void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64_t K, float alpha, float beta,
-             const float* C, int64_t ldc, float* D, int64_t ldd, int* status, cudaStream_t st, const char* tag) {
+             const float* C, int64_t ldc, float* D, int64_t ldd, int* status, cudaStream_t st, const char* tag,
+             DevBuf<float>* ws) {
   if (M <= 0 || N <= 0) return;
   CHEBFI_REQUIRE(K > 0, CHEBFI_ERR_ARG, "tensor-core GEMM with K = 0");
   CHEBFI_REQUIRE(M < (1ll << 31) && N < (1ll << 31) && K < (1ll << 31), CHEBFI_ERR_ARG, "GEMM too large");
@@ -397,8 +440,39 @@ void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64
   }
   const int64_t tiles = ((N + tc::BN - 1) / tc::BN) * ((M + tc::BM - 1) / tc::BM);
   CHEBFI_REQUIRE(tiles < (1ll << 31), CHEBFI_ERR_ARG, "GEMM too large");
-  dim3 grid((unsigned)std::min<int64_t>(tiles, sms));
+  // K split: when the tiles fill the SMs in a whole number of rounds poorly (e.g. 512 tiles
+  // on 148 SMs: 4 rounds, the last half empty), more and shorter work units balance better;
+  // the split with the fewest rounds x k-tiles per unit wins if it saves at least 5 %, each
+  // unit keeping at least one full accumulation chunk, and only for outputs small enough
+  // (at most 2^26 elements) that the extra pass over the partial sums costs little
+  const int64_t num_k = (K + tc::BK - 1) / tc::BK;
+  int splits = 1;
+  if (ws && M * N <= (int64_t(1) << 26)) {
+    const int64_t single = ((tiles + sms - 1) / sms) * num_k;
+    int64_t best = single;
+    for (int sp = 2; sp <= 8; ++sp) {
+      const int64_t kpt = (num_k + sp - 1) / sp;
+      if (kpt < tc::CHUNK || (sp - 1) * kpt >= num_k) break;
+      const int64_t cost = ((tiles * sp + sms - 1) / sms) * kpt;
+      if (cost < best && cost * 20 <= single * 19) {
+        best = cost;
+        splits = sp;
+      }
+    }
+  }
+  a.splits = splits;
+  a.ws = nullptr;
+  if (splits > 1) {
+    ws->alloc((size_t)splits * M * N);
+    a.ws = ws->p;
+  }
+  const int64_t units = tiles * splits;
+  dim3 grid((unsigned)std::min<int64_t>(units, sms));
   CHEBFI_LAUNCH_W(tag, st, 2.0 * (double)M * (double)N * (double)K, tc::k_tc_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(ah, al, bh, bl, a));
+  if (splits > 1) {
+    const int64_t n4 = (M * N + 3) / 4;
+    CHEBFI_LAUNCH("k_tc_reduce", st, tc::k_tc_reduce<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>((int)M, (int)N, splits, a.ws, alpha, beta, C, ldc, D, ldd));
+  }
 }
 
 }  // namespace chebfi

@@ -173,6 +173,7 @@ struct Work {
   DevBuf<double2> splitk;
   DevBuf<float2> fsplitk;
   SplitBF16Buf Zb, Sb;  // bf16 pairs of Z (or Y) and of the projection-space operands
+  DevBuf<float> tcws;   // K-split partial sums of the tensor-core GEMMs
   DevBuf<double2> gpool;          // filter backward: checkpoints, segment, adjoint iterates
   DevBuf<float2> fgT, fgR, fgG;   // FP32 backward: column buffer and real-space grids of the V gradient
   DevBuf<int32_t> order;          // band order of the locking filter

@@ -60,7 +60,8 @@ void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha,
 // D (M x N, FP32 column-major) = alpha A B + beta C with A (M x K) and B (K x N) K-major
 // bf16 pairs; tcgen05 tensor cores with FP32 accumulation.  C may equal D.
 void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64_t K, float alpha, float beta,
-             const float* C, int64_t ldc, float* D, int64_t ldd, int* status, cudaStream_t st, const char* tag);
+             const float* C, int64_t ldc, float* D, int64_t ldd, int* status, cudaStream_t st, const char* tag,
+             DevBuf<float>* ws = nullptr);
 // Real embeddings (bf16 pairs) of complex operators applied to interleaved complex data:
 // embed_ph: the (2 nq) x (2 npw) matrix of x -> P^H x;  embed_n: the (2m) x (2k) matrix of x -> A x.
 void embed_ph(int64_t npw, int64_t nq, const double2* P, int64_t ldp, SplitBF16Buf& out, cudaStream_t st);
