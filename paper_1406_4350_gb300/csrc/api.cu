@@ -1395,7 +1395,7 @@ int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, in
   const int64_t npw = ctx->npw;
   // bands are filtered independently, so the block is processed in band chunks: chunk c is
   // copied in while chunk c-1 is filtered and chunk c-2 is copied out (two staging buffers)
-  int nc = nchunks > 0 ? nchunks : (nb >= 1024 ? 2 : 1);
+  int nc = nchunks > 0 ? nchunks : (nb >= 2048 ? 4 : (nb >= 1024 ? 2 : 1));
   nc = (int)std::min<int64_t>(nc, nb);
   const int64_t per = (nb + nc - 1) / nc;
   if (!ctx->copy_in) {

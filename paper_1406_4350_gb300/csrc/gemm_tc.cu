@@ -14,13 +14,14 @@
 //
 // Persistent kernel, one CTA per SM looping over 128 x 128 tiles: warp 0 issues the TMA
 // loads (128-byte swizzle,
-// three-stage mbarrier ring), warp 1 allocates 256 TMEM columns and issues the MMAs
+// three-stage mbarrier ring), warp 1 allocates all 512 TMEM columns and issues the MMAs
 // (tcgen05.mma cta_group::1 kind::f16, M = 128, N = 128, K = 16), warps 2-5 read the
 // accumulator with tcgen05.ld.  The long contractions of the projector products (K up to
 // 1.2e5) would lose accuracy in one tensor-core accumulator, so K is cut into chunks of
-// 8 k-tiles (96 MMAs): each chunk accumulates in one of two TMEM buffers while the
-// epilogue warps add the other, finished one into FP32 registers; the alpha/beta epilogue
-// writes the register sums.  Every wait on an mbarrier gives up after a fixed time,
+// 8 k-tiles (96 MMAs): each chunk accumulates in one of four TMEM buffers while the
+// epilogue warps add finished ones into FP32 registers; the alpha/beta epilogue writes the
+// register sums.  Four buffers let the MMAs run three chunks ahead while the epilogue
+// reads C and stores D for a finished tile.  Every wait on an mbarrier gives up after a fixed time,
 // records an error code and lets the CTA finish (the TMEM is released on every path).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -41,7 +42,8 @@ constexpr int B_BYTES = BN * BK * 2;                     // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of both: 64 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 2 * BN;                   // two accumulators
+constexpr int NACC = 4;                                  // TMEM accumulators (chunks in flight)
+constexpr uint32_t TMEM_COLS = NACC * BN;                // all 512 columns
 constexpr unsigned long long WAIT_NS = 2000000000ull;    // 2 s per wait
 
 struct Args {
@@ -171,9 +173,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;   // [2]: MMAs of a chunk done
-  uint64_t* acc_empty = acc_full + 2;    // [2]: epilogue has drained the buffer
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* acc_full = empty + STAGES;   // [NACC]: MMAs of a chunk done
+  uint64_t* acc_empty = acc_full + NACC; // [NACC]: epilogue has drained the buffer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + NACC);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int num_k = (args.K + BK - 1) / BK;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NACC; ++a) {
       mbar_init(&acc_full[a], 1);
       mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
     }
@@ -243,8 +245,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int num_chunks = (ke - kb + CHUNK - 1) / CHUNK;
         int kt = kb;
         for (int ch = 0; ch < num_chunks && ok; ++ch, ++gch) {
-          const int acc = gch & 1;
-          if (gch >= 2 && !mbar_wait(&acc_empty[acc], ((gch >> 1) - 1) & 1)) {
+          const int acc = gch % NACC;
+          if (gch >= NACC && !mbar_wait(&acc_empty[acc], ((gch / NACC) - 1) & 1)) {
             flag(args.status, CHEBFI_ERR_CUDA);
             ok = false;
             break;
@@ -293,8 +295,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int j = 0; j < BN; ++j) racc[j] = 0.f;
       for (int ch = 0; ch < num_chunks; ++ch, ++gch) {
-        const int acc = gch & 1;
-        if (!mbar_wait(&acc_full[acc], (gch >> 1) & 1)) {
+        const int acc = gch % NACC;
+        if (!mbar_wait(&acc_full[acc], (gch / NACC) & 1)) {
           flag(args.status, CHEBFI_ERR_CUDA);
           ok = false;
           break;
