@@ -443,7 +443,7 @@ void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64
   const int64_t tiles = ((N + tc::BN - 1) / tc::BN) * ((M + tc::BM - 1) / tc::BM);
   CHEBFI_REQUIRE(tiles < (1ll << 31), CHEBFI_ERR_ARG, "GEMM too large");
   // K split: when the tiles fill the SMs in a whole number of rounds poorly (e.g. 512 tiles
-  // on 148 SMs: 4 rounds, the last half empty), more and shorter work units balance better;
+  // on 152 SMs: 4 rounds, the last one 1/3 full), more and shorter work units balance better;
   // the split with the fewest rounds x k-tiles per unit wins if it saves at least 5 %, each
   // unit keeping at least one full accumulation chunk, and only for outputs small enough
   // (at most 2^26 elements) that the extra pass over the partial sums costs little
