@@ -446,10 +446,11 @@ void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64
   // on 152 SMs: 4 rounds, the last one 1/3 full), more and shorter work units balance better;
   // the split with the fewest rounds x k-tiles per unit wins if it saves at least 5 %, each
   // unit keeping at least one full accumulation chunk, and only for outputs small enough
-  // (at most 2^26 elements) that the extra pass over the partial sums costs little
+  // (at most 2^26 elements) and contractions long enough (at least 16 chunks) that the
+  // extra pass over the partial sums costs little next to the GEMM
   const int64_t num_k = (K + tc::BK - 1) / tc::BK;
   int splits = 1;
-  if (ws && M * N <= (int64_t(1) << 26)) {
+  if (ws && M * N <= (int64_t(1) << 26) && num_k >= 16 * tc::CHUNK) {
     const int64_t single = ((tiles + sms - 1) / sms) * num_k;
     int64_t best = single;
     for (int sp = 2; sp <= 8; ++sp) {
