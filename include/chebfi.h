@@ -251,6 +251,35 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
  *    on the same device, other host threads) race on it. */
 int chebfi_apply_H_noalloc(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t ld, void* stream);
 
+/* Engines of the FP64 complex GEMMs behind every FP64 step (Rayleigh-Ritz and Cholesky-QR
+ * of Algorithm 2, the FP64 filter's projector products P^H psi and P W of Section 5.1, the
+ * setup products G = P^H P and the Woodbury core).  GB300 issues FP64 FMAs at about 2 per
+ * clock per SM, so large products go to the bf16 tensor cores through an FP64-accurate
+ * modular emulation (the integer-modular "Ozaki scheme II"): every row of op(A) and column of
+ * op(B) is scaled by a power of two to a 2-norm in [2^(E-1), 2^E) and rounded to integers,
+ * one tensor-core GEMM per modulus computes the product of their residues exactly, and the
+ * Chinese remainder theorem recovers the integer product.  The result's error is about
+ * 2^-E ||row of op(A)|| ||column of op(B)|| per entry, E = 53 with the default 14 moduli:
+ * no larger than an FP64 dot product's.  The paper (FP64 BLAS on CPUs) has no counterpart. */
+enum {
+  CHEBFI_GEMM_AUTO = 0,        /* tensor cores when K >= 64 and 8 M N K >= 1e9, else CUDA cores */
+  CHEBFI_GEMM_CUDA_CORES = 1,  /* FP64 FMA on the CUDA cores only */
+  CHEBFI_GEMM_TENSOR = 2       /* the modular emulation for every product */
+};
+/* Select the engine (a CHEBFI_GEMM_* value) and the modulus count of the emulation (8..15;
+ * 0 keeps the current one, initially 14; fewer moduli run faster with a smaller E: 8 -> 30,
+ * 10 -> 38, 12 -> 45, 14 -> 53, 15 -> 57).  *precision_bits (nullable) receives E.  The
+ * emulation keeps residues of P (about 2 x nmod x 4 N_pw N_proj bytes) once used. */
+int chebfi_set_fp64_gemm(chebfi_ctx* ctx, int engine, int nmod, int* precision_bits);
+
+/* Complex FP64 GEMM through the context's engine selection: C = alpha op(A) op(B) + beta C,
+ * C m x n, inner dimension k; op(A) = A (m x k, lda >= m) or A^H (A k x m, lda >= k) when
+ * conjA; op(B) = B (k x n, ldb >= k) or B^H (B n x k, ldb >= n) when conjB.  A, B, C: device,
+ * complex128 column-major; C must not overlap A or B.  Needs no cell or projectors. */
+int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n, int64_t k, double alpha,
+                     const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                     void* stream);
+
 /* Synchronise the context's work and return the first device-detected error, if any. */
 int chebfi_sync_status(chebfi_ctx* ctx);
 

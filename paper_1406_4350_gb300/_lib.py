@@ -17,6 +17,7 @@ P_int = ctypes.POINTER(ctypes.c_int)
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_FILTER_OVERFLOW, ERR_NOMEM = \
     0, -1, -2, -3, -4, -5, -6, -7
 F64, F32, MIXED = 0, 1, 2
+GEMM_AUTO, GEMM_CUDA_CORES, GEMM_TENSOR = 0, 1, 2
 BOUND_PAPER, BOUND_RIGOROUS = 0, 1
 
 
@@ -67,6 +68,9 @@ SIGNATURES = {
     "chebfi_rayleigh_quotients": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64,
                              ctypes.POINTER(Params), c_void_p]),
+    "chebfi_set_fp64_gemm": (c_int, [c_void_p, c_int, c_int, P_int]),
+    "chebfi_gemm_fp64": (c_int, [c_void_p, c_int, c_int, c_int64, c_int64, c_int64, c_double, c_void_p, c_int64,
+                                 c_void_p, c_int64, c_double, c_void_p, c_int64, c_void_p]),
     "chebfi_sync_status": (c_int, [c_void_p]),
     "chebfi_kernel_launches": (c_int64, [c_void_p]),
     "chebfi_profile_enable": (c_int, [c_void_p, c_int]),

@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import F32, F64, BOUND_PAPER, Params
+from ._lib import F32, F64, BOUND_PAPER, GEMM_AUTO, GEMM_CUDA_CORES, GEMM_TENSOR, Params
 
 __all__ = ["ChebFI", "ChebFIBatch", "ChebFIError", "fortran"]
 
@@ -277,6 +277,37 @@ class ChebFI:
         self._check(self.lib.chebfi_solve(self.h, y, ctypes.c_void_p(ev.data_ptr()), ctypes.c_void_p(rs.data_ptr()),
                                           nb, ld, ctypes.byref(p), _stream()))
         return ev, rs
+
+    def set_fp64_gemm(self, engine: int = GEMM_AUTO, nmod: int = 0) -> int:
+        """Engine of the FP64 complex GEMMs (GEMM_AUTO, GEMM_CUDA_CORES, GEMM_TENSOR) and the
+        modulus count of the tensor-core emulation (0 keeps it); returns its precision E."""
+        e = ctypes.c_int(0)
+        self._check(self.lib.chebfi_set_fp64_gemm(self.h, engine, nmod, ctypes.byref(e)))
+        return e.value
+
+    def gemm_fp64(self, A, B, conjA: bool = False, conjB: bool = False, alpha: float = 1.0, beta: float = 0.0,
+                  C=None):
+        """C = alpha op(A) op(B) + beta C for column-major complex128 CUDA matrices."""
+        def mat(X):
+            if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.complex128 and X.dim() == 2):
+                raise TypeError("expected a 2-D complex128 CUDA tensor")
+            if X.shape[0] > 1 and X.shape[1] > 1 and X.stride(0) != 1:
+                raise ValueError("matrices must be column-major (use fortran())")
+            ld = X.stride(1) if X.shape[1] > 1 else X.shape[0]  # a size-1 dimension's stride is free
+            return ctypes.c_void_p(X.data_ptr()), int(max(ld, X.shape[0], 1))
+        m = A.shape[1] if conjA else A.shape[0]
+        k = A.shape[0] if conjA else A.shape[1]
+        n = B.shape[0] if conjB else B.shape[1]
+        if (B.shape[1] if conjB else B.shape[0]) != k:
+            raise ValueError("inner dimensions differ")
+        if C is None:
+            C = torch.zeros((n, m), dtype=torch.complex128, device=A.device).T
+        a, lda = mat(A)
+        b, ldb = mat(B)
+        c, ldc = mat(C)
+        self._check(self.lib.chebfi_gemm_fp64(self.h, int(conjA), int(conjB), m, n, k, alpha, a, lda, b, ldb, beta,
+                                              c, ldc, _stream()))
+        return C
 
     def solve_stats(self):
         """(sweeps performed, band-H-applications of the filters) of the last solve."""

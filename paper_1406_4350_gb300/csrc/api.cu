@@ -12,14 +12,15 @@
 #include <stdexcept>
 #include <vector>
 #include <complex>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "kernels.cuh"
 
 namespace chebfi {
 
-int64_t* g_launch_counter = nullptr;
-Profiler* g_prof = nullptr;
+thread_local int64_t* g_launch_counter = nullptr;
+thread_local Profiler* g_prof = nullptr;
 
 cudaEvent_t Profiler::get() {
   if (pool.empty()) {
@@ -161,6 +162,52 @@ template <> struct Ops<float> {
   static DevBuf<float2>& pb(chebfi_ctx* c) { return c->w.fpw; }
 };
 
+// ------------------------------------------------------------------ FP64 GEMM routing
+// FP64 complex GEMMs large enough to amortise the operand preparation run on the tensor
+// cores through the modular emulation (ozaki.cu), the others on the CUDA cores; the context
+// can force either engine (chebfi_set_fp64_gemm).
+bool use_tensor_fp64(const chebfi_ctx* ctx, int64_t M, int64_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0 || ctx->fp64_gemm == CHEBFI_GEMM_CUDA_CORES) return false;
+  if (ctx->fp64_gemm == CHEBFI_GEMM_TENSOR) return true;
+  return K >= 64 && 8.0 * (double)M * (double)N * (double)K >= 1e9;
+}
+
+// residues of P^H (conj) or P as the A operand, kept while the modulus count is unchanged
+const OzOperand& oz_P(chebfi_ctx* ctx, bool conj, cudaStream_t st) {
+  OzOperand& o = conj ? ctx->ozPh : ctx->ozP;
+  if (o.nmod != ctx->oz_nmod)
+    oz_prepare(ctx->d_P.p, ctx->npw, conj ? ctx->nproj : ctx->npw, conj ? ctx->npw : ctx->nproj, conj, conj, true,
+               ctx->oz_nmod, o, st);
+  return o;
+}
+
+// C = alpha op(A) op(B) + beta C in FP64 (the signature of gemm<double> with the context first)
+void gemm64(chebfi_ctx* ctx, bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const double2* A,
+            int64_t lda, const double2* B, int64_t ldb, double beta, double2* C, int64_t ldc, cudaStream_t st,
+            DevBuf<double2>* ws = nullptr, const char* tag = "k_gemm", bool lower = false) {
+  if (!use_tensor_fp64(ctx, M, N, K)) {
+    gemm<double>(conjA, conjB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag, lower);
+    return;
+  }
+  OzWork& z = ctx->oz;
+  const OzOperand* a = &z.A;
+  const bool is_P = ctx->has_proj && A == ctx->d_P.p && lda == ctx->npw &&
+                    (conjA ? (M == ctx->nproj && K == ctx->npw) : (M == ctx->npw && K == ctx->nproj));
+  if (is_P) a = &oz_P(ctx, conjA, st);
+  else oz_prepare(A, lda, M, K, conjA, conjA, true, ctx->oz_nmod, z.A, st);
+  oz_prepare(B, ldb, N, K, !conjB, conjB, false, ctx->oz_nmod, z.B, st);
+  oz_gemm(*a, z.B, alpha, beta, C, ldc, lower, z.R, ctx->d_status.p, st, tag);
+}
+
+// the GEMM of the form's precision: FP64 through gemm64, FP32 on the CUDA cores
+template <typename R>
+void cgemm(chebfi_ctx* ctx, bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A,
+           int64_t lda, const cplx<R>* B, int64_t ldb, double beta, cplx<R>* C, int64_t ldc, cudaStream_t st,
+           DevBuf<cplx<R>>* ws = nullptr, const char* tag = "k_gemm", bool lower = false) {
+  if constexpr (std::is_same<R, double>::value) gemm64(ctx, conjA, conjB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag, lower);
+  else gemm<R>(conjA, conjB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, ws, tag, lower);
+}
+
 // H Y (FP64 or FP32) with the projections p = P^H Y returned; sorted order, ld = npw.
 template <typename R>
 void apply_H_sorted(chebfi_ctx* ctx, const cplx<R>* Y, cplx<R>* HY, cplx<R>* p, cplx<R>* Dp, cplx<R>* T, int64_t nb,
@@ -173,9 +220,9 @@ void apply_H_sorted(chebfi_ctx* ctx, const cplx<R>* Y, cplx<R>* HY, cplx<R>* p, 
   ep.ldz = npw;
   local_apply<R>(ctx, Y, npw, nb, T, ep, st);
   if (nq > 0) {
-    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, p, nq, st, Ops<R>::ws(ctx), tag);
+    cgemm<R>(ctx, true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, p, nq, st, Ops<R>::ws(ctx), tag);
     blockdiag_apply<R>(ctx, Ops<R>::D(ctx), p, nq, Dp, nq, nb, st);
-    gemm<R>(false, false, npw, nb, nq, 1.0, Ops<R>::P(ctx), npw, Dp, nq, 1.0, HY, npw, st, Ops<R>::ws(ctx), tag);
+    cgemm<R>(ctx, false, false, npw, nb, nq, 1.0, Ops<R>::P(ctx), npw, Dp, nq, 1.0, HY, npw, st, Ops<R>::ws(ctx), tag);
   }
 }
 
@@ -201,7 +248,7 @@ cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb0, int degree
   const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
   cplx<R>*cur = b.Ya, *prev = b.Yb, *pcur = b.pa, *pprev = b.pb;
   if (nq > 0)
-    gemm<R>(true, false, nq, active ? active[0] : nb0, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st,
+    cgemm<R>(ctx, true, false, nq, active ? active[0] : nb0, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st,
             Ops<R>::ws(ctx), "gemm_PhY");
   for (int k = 0; k < degree; ++k) {
     const int64_t nb = active ? active[k] : nb0;  // bands still being filtered (a prefix)
@@ -222,21 +269,21 @@ cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb0, int degree
     local_apply<R>(ctx, cur, npw, nb, b.T, ep, st);
     if (nq > 0) {
       // P^H H Y_k = P^H Z + G D p_k
-      gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, b.Z, npw, 0.0, b.pz, nq, st, Ops<R>::ws(ctx),
+      cgemm<R>(ctx, true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, b.Z, npw, 0.0, b.pz, nq, st, Ops<R>::ws(ctx),
               "gemm_PhY");
       blockdiag_apply<R>(ctx, Ops<R>::D(ctx), pcur, nq, b.pw, nq, nb, st);
-      gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::G(ctx), nq, b.pw, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx),
+      cgemm<R>(ctx, false, false, nq, nb, nq, 1.0, Ops<R>::G(ctx), nq, b.pw, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx),
               "gemm_small");
       if (ctx->paw) {
         // q = M P^H H Y_k;  W = D p_k - q;  P^H S^{-1} H Y_k = P^H H Y_k - G q
-        gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, b.pz, nq, 0.0, b.pq, nq, st, Ops<R>::ws(ctx),
+        cgemm<R>(ctx, false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, b.pz, nq, 0.0, b.pq, nq, st, Ops<R>::ws(ctx),
                 "gemm_small");
         axpby<R>(nq, nb, (R)1, b.pw, nq, (R)-1, b.pq, nq, b.pw, nq, st);
-        gemm<R>(false, false, nq, nb, nq, -1.0, Ops<R>::G(ctx), nq, b.pq, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx),
+        cgemm<R>(ctx, false, false, nq, nb, nq, -1.0, Ops<R>::G(ctx), nq, b.pq, nq, 1.0, b.pz, nq, st, Ops<R>::ws(ctx),
                 "gemm_small");
       }
       // Y_{k+1} = T + a P W
-      gemm<R>(false, false, npw, nb, nq, a, Ops<R>::P(ctx), npw, b.pw, nq, 1.0, prev, npw, st, Ops<R>::ws(ctx),
+      cgemm<R>(ctx, false, false, npw, nb, nq, a, Ops<R>::P(ctx), npw, b.pw, nq, 1.0, prev, npw, st, Ops<R>::ws(ctx),
               "gemm_PW");
       // p_{k+1} = a (P^H S^{-1} H Y_k - c p_k) - bp p_{k-1}
       cheb_combine<R>(nq, nb, (R)a, b.pz, nq, (R)c, pcur, nq, (R)bp, k == 0 ? nullptr : pprev, nq, pprev, nq, st);
@@ -480,11 +527,11 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   apply_H_sorted<double>(ctx, Y, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st, "gemm_rr");
   double2 *Hs = w.small1.p, *Ss = w.small2.p, *Li = w.small3.p, *X = w.small4.p;
   // H_Psi and S_Psi are Hermitian: only their lower triangles are computed, then mirrored
-  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, w.HY.p, npw, 0.0, Hs, nb, st, ws, "gemm_rr", true);
-  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws, "gemm_rr", true);
+  gemm64(ctx, true, false, nb, nb, npw, 1.0, Y, npw, w.HY.p, npw, 0.0, Hs, nb, st, ws, "gemm_rr", true);
+  gemm64(ctx, true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws, "gemm_rr", true);
   if (ctx->paw) {
     blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
-    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws, "gemm_rr", true);
+    gemm64(ctx, true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws, "gemm_rr", true);
   }
   mirror_lower(nb, Hs, nb, st);
   mirror_lower(nb, Ss, nb, st);
@@ -496,27 +543,27 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   cholesky(nb, Ss, nb, ctx->d_status.p, st, ws);
   set_identity(nb, Li, nb, st);
   trsm_lower(nb, nb, Ss, nb, Li, nb, st, ws);
-  gemm<double>(false, false, nb, nb, nb, 1.0, Li, nb, Hs, nb, 0.0, X, nb, st, ws, "gemm_rr");
-  gemm<double>(false, true, nb, nb, nb, 1.0, X, nb, Li, nb, 0.0, Hs, nb, st, ws, "gemm_rr");
+  gemm64(ctx, false, false, nb, nb, nb, 1.0, Li, nb, Hs, nb, 0.0, X, nb, st, ws, "gemm_rr");
+  gemm64(ctx, false, true, nb, nb, nb, 1.0, X, nb, Li, nb, 0.0, Hs, nb, st, ws, "gemm_rr");
   hermitize(nb, Hs, nb, st);
   // C = Z Lambda Z^H
   jacobi_eigh(nb, Hs, nb, evals, X, nb, ctx->d_status.p, st, &w.small5);
   check_status(ctx, st, "rayleigh_ritz");
   // rotation R = s L^{-H} Z; Y <- Y R, HY <- HY R, p <- p R
-  gemm<double>(true, false, nb, nb, nb, 1.0, Li, nb, X, nb, 0.0, Ss, nb, st, ws, "gemm_rr");
+  gemm64(ctx, true, false, nb, nb, nb, 1.0, Li, nb, X, nb, 0.0, Ss, nb, st, ws, "gemm_rr");
   scale_rows(nb, nb, Ss, nb, w.dvec1.p, st);
-  gemm<double>(false, false, npw, nb, nb, 1.0, Y, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws, "gemm_rr");
+  gemm64(ctx, false, false, npw, nb, nb, 1.0, Y, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws, "gemm_rr");
   std::swap(w.Ya.p, w.tmp.p);  // buffers have equal capacity
   std::swap(w.Ya.n, w.tmp.n);
   Y = w.Ya.p;
   if (resid) {
-    gemm<double>(false, false, npw, nb, nb, 1.0, w.HY.p, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws, "gemm_rr");  // H Y_new
+    gemm64(ctx, false, false, npw, nb, nb, 1.0, w.HY.p, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws, "gemm_rr");  // H Y_new
     double2* SY = w.HY.p;  // reuse
     CHEBFI_CUDA(cudaMemcpyAsync(SY, Y, sizeof(double2) * ny, cudaMemcpyDeviceToDevice, st));
     if (ctx->paw) {
-      gemm<double>(false, false, nq, nb, nb, 1.0, w.pa.p, nq, Ss, nb, 0.0, w.pc.p, nq, st, ws, "gemm_rr");  // p_new
+      gemm64(ctx, false, false, nq, nb, nb, 1.0, w.pa.p, nq, Ss, nb, 0.0, w.pc.p, nq, st, ws, "gemm_rr");  // p_new
       blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pc.p, nq, w.pb.p, nq, nb, st);
-      gemm<double>(false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, SY, npw, st, ws, "gemm_rr");
+      gemm64(ctx, false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, SY, npw, st, ws, "gemm_rr");
     }
     residual_norms(npw, nb, w.tmp.p, npw, SY, npw, evals, resid, st);
   }
@@ -534,18 +581,18 @@ void ortho_on_Ya(chebfi_ctx* ctx, int64_t nb, cudaStream_t st) {
   w.small3.alloc(ns);
   DevBuf<double2>* ws = &w.splitk;
   double2 *Ss = w.small2.p, *Li = w.small3.p, *Y = w.Ya.p;
-  gemm<double>(true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws);
+  gemm64(ctx, true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws);
   if (ctx->paw) {
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, Y, npw, 0.0, w.pa.p, nq, st, ws);
+    gemm64(ctx, true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, Y, npw, 0.0, w.pa.p, nq, st, ws);
     blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
-    gemm<double>(true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws);
+    gemm64(ctx, true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws);
   }
   hermitize(nb, Ss, nb, st);
   cholesky(nb, Ss, nb, ctx->d_status.p, st, ws);
   check_status(ctx, st, "orthonormalise");
   set_identity(nb, Li, nb, st);
   trsm_lower(nb, nb, Ss, nb, Li, nb, st, ws);
-  gemm<double>(false, true, npw, nb, nb, 1.0, Y, npw, Li, nb, 0.0, w.tmp.p, npw, st, ws);
+  gemm64(ctx, false, true, npw, nb, nb, 1.0, Y, npw, Li, nb, 0.0, w.tmp.p, npw, st, ws);
   std::swap(w.Ya.p, w.tmp.p);
   std::swap(w.Ya.n, w.tmp.n);
 }
@@ -614,8 +661,8 @@ double rigorous_bound(chebfi_ctx* ctx) {
     for (int which = 0; which < (ctx->paw ? 2 : 1); ++which) {
       CHEBFI_LAUNCH("k_dense_from_blocks", 0, k_dense_from_blocks<<<nblk(nq * nq), 256>>>(nq, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
                                                   which == 0 ? ctx->d_Dblk.p : ctx->d_Qblk.p, Dd.p));
-      gemm<double>(false, false, nq, nq, nq, 1.0, Dd.p, nq, ctx->d_L.p, nq, 0.0, T.p, nq, st, ws);
-      gemm<double>(true, false, nq, nq, nq, 1.0, ctx->d_L.p, nq, T.p, nq, 0.0, A.p, nq, st, ws);
+      gemm64(ctx, false, false, nq, nq, nq, 1.0, Dd.p, nq, ctx->d_L.p, nq, 0.0, T.p, nq, st, ws);
+      gemm64(ctx, true, false, nq, nq, nq, 1.0, ctx->d_L.p, nq, T.p, nq, 0.0, A.p, nq, st, ws);
       hermitize(nq, A.p, nq, st);
       jacobi_eigh(nq, A.p, nq, w.p, V.p, nq, ctx->d_status.p, st, &ctx->w.small5);
       check_status(ctx, st, "upper_bound");
@@ -735,9 +782,9 @@ const cplx<R>* sinv_sorted(chebfi_ctx* ctx, const cplx<R>* X, cplx<R>* out, cplx
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   if (!ctx->paw) return X;
   CHEBFI_CUDA(cudaMemcpyAsync(out, X, sizeof(cplx<R>) * npw * nb, cudaMemcpyDeviceToDevice, st));
-  gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, X, npw, 0.0, pa, nq, st, Ops<R>::ws(ctx), "gemm_grad");
-  gemm<R>(false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, pa, nq, 0.0, pb, nq, st, Ops<R>::ws(ctx), "gemm_grad");
-  gemm<R>(false, false, npw, nb, nq, -1.0, Ops<R>::P(ctx), npw, pb, nq, 1.0, out, npw, st, Ops<R>::ws(ctx),
+  cgemm<R>(ctx, true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, X, npw, 0.0, pa, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+  cgemm<R>(ctx, false, false, nq, nb, nq, 1.0, Ops<R>::M(ctx), nq, pa, nq, 0.0, pb, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+  cgemm<R>(ctx, false, false, npw, nb, nq, -1.0, Ops<R>::P(ctx), npw, pb, nq, 1.0, out, npw, st, Ops<R>::ws(ctx),
           "gemm_grad");
   return out;
 }
@@ -793,8 +840,8 @@ void accumulate_pair(chebfi_ctx* ctx, const cplx<R>* Y, const cplx<R>* G, double
     DevBuf<cplx<R>>& pp = GradBufs<R>::p(ctx);
     q.alloc((size_t)nq * nb);
     pp.alloc((size_t)nq * nb);
-    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, G, npw, 0.0, q.p, nq, st, Ops<R>::ws(ctx), "gemm_grad");
-    gemm<R>(true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, pp.p, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+    cgemm<R>(ctx, true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, G, npw, 0.0, q.p, nq, st, Ops<R>::ws(ctx), "gemm_grad");
+    cgemm<R>(ctx, true, false, nq, nb, npw, 1.0, Ops<R>::P(ctx), npw, Y, npw, 0.0, pp.p, nq, st, Ops<R>::ws(ctx), "gemm_grad");
     block_outer_grad(ctx, q.p, pp.p, nq, nb, gD, st, scale, true);
   }
   if (gV)
@@ -1126,6 +1173,7 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
   ctx->paw = false;
   ctx->bound_rigorous = -1.0;
   ctx->has_proj = false;
+  ctx->ozPh.nmod = ctx->ozP.nmod = 0;  // residues of the previous P are stale
   if (nproj == 0) {
     ctx->has_proj = true;
     return CHEBFI_OK;
@@ -1171,7 +1219,7 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
   DevBuf<double2>* ws = &ctx->w.splitk;
   // G = P^H P (Section 5.1, precomputed once)
   ctx->d_G.alloc((size_t)nproj * nproj);
-  gemm<double>(true, false, nproj, nproj, npw, 1.0, ctx->d_P.p, npw, ctx->d_P.p, npw, 0.0, ctx->d_G.p, nproj, st, ws);
+  gemm64(ctx, true, false, nproj, nproj, npw, 1.0, ctx->d_P.p, npw, ctx->d_P.p, npw, 0.0, ctx->d_G.p, nproj, st, ws);
   hermitize(nproj, ctx->d_G.p, nproj, st);
   // L = chol(G): used by the Woodbury core and the rigorous bound
   ctx->d_L.alloc((size_t)nproj * nproj);
@@ -1190,8 +1238,8 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
     X.alloc(nn);
     CHEBFI_LAUNCH("k_dense_from_blocks", st, k_dense_from_blocks<<<nblk(nproj * nproj), 256, 0, st>>>(nproj, ctx->d_atom_of.p, ctx->d_offs.p, ctx->d_blk_off.p,
                                                              ctx->d_Qblk.p, Qd.p));
-    gemm<double>(false, false, nproj, nproj, nproj, 1.0, Qd.p, nproj, ctx->d_L.p, nproj, 0.0, T.p, nproj, st, ws);
-    gemm<double>(true, false, nproj, nproj, nproj, 1.0, ctx->d_L.p, nproj, T.p, nproj, 0.0, B.p, nproj, st, ws);
+    gemm64(ctx, false, false, nproj, nproj, nproj, 1.0, Qd.p, nproj, ctx->d_L.p, nproj, 0.0, T.p, nproj, st, ws);
+    gemm64(ctx, true, false, nproj, nproj, nproj, 1.0, ctx->d_L.p, nproj, T.p, nproj, 0.0, B.p, nproj, st, ws);
     CHEBFI_LAUNCH("k_add_identity", st, k_add_identity<<<nblk(nproj), 256, 0, st>>>(nproj, B.p, nproj));
     hermitize(nproj, B.p, nproj, st);
     cholesky(nproj, B.p, nproj, ctx->d_status.p, st, ws);
@@ -1201,10 +1249,10 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
     set_identity(nproj, Ri.p, nproj, st);
     trsm_lower(nproj, nproj, B.p, nproj, Ri.p, nproj, st, ws);
     // M = T R^{-H} R^{-1} L^{-1}
-    gemm<double>(false, true, nproj, nproj, nproj, 1.0, T.p, nproj, Ri.p, nproj, 0.0, X.p, nproj, st, ws);
-    gemm<double>(false, false, nproj, nproj, nproj, 1.0, X.p, nproj, Ri.p, nproj, 0.0, B.p, nproj, st, ws);
+    gemm64(ctx, false, true, nproj, nproj, nproj, 1.0, T.p, nproj, Ri.p, nproj, 0.0, X.p, nproj, st, ws);
+    gemm64(ctx, false, false, nproj, nproj, nproj, 1.0, X.p, nproj, Ri.p, nproj, 0.0, B.p, nproj, st, ws);
     ctx->d_M.alloc(nn);
-    gemm<double>(false, false, nproj, nproj, nproj, 1.0, B.p, nproj, Li.p, nproj, 0.0, ctx->d_M.p, nproj, st, ws);
+    gemm64(ctx, false, false, nproj, nproj, nproj, 1.0, B.p, nproj, Li.p, nproj, 0.0, ctx->d_M.p, nproj, st, ws);
     hermitize(nproj, ctx->d_M.p, nproj, st);
     ctx->d_Mf.alloc(nn);
     convert(nproj, nproj, ctx->d_M.p, nproj, ctx->d_Mf.p, nproj, st);
@@ -1295,9 +1343,9 @@ int chebfi_apply_S(chebfi_ctx* ctx, const void* Y, void* SY, int64_t nb, int64_t
     const size_t np = (size_t)nq * nb;
     w.pa.alloc(np);
     w.pb.alloc(np);
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk);
+    gemm64(ctx, true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk);
     blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pa.p, nq, w.pb.p, nq, nb, st);
-    gemm<double>(false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk);
+    gemm64(ctx, false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk);
   }
   scatter_from(ctx, w.Ya.p, SY, nb, ld, st);
   API_END(ctx)
@@ -1318,9 +1366,9 @@ int chebfi_apply_Sinv(chebfi_ctx* ctx, const void* X, void* out, int64_t nb, int
     const size_t np = (size_t)nq * nb;
     w.pa.alloc(np);
     w.pb.alloc(np);
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk);
-    gemm<double>(false, false, nq, nb, nq, 1.0, ctx->d_M.p, nq, w.pa.p, nq, 0.0, w.pb.p, nq, st, &w.splitk);
-    gemm<double>(false, false, npw, nb, nq, -1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk);
+    gemm64(ctx, true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk);
+    gemm64(ctx, false, false, nq, nb, nq, 1.0, ctx->d_M.p, nq, w.pa.p, nq, 0.0, w.pb.p, nq, st, &w.splitk);
+    gemm64(ctx, false, false, npw, nb, nq, -1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk);
   }
   scatter_from(ctx, w.Ya.p, out, nb, ld, st);
   API_END(ctx)
@@ -1640,8 +1688,8 @@ int chebfi_apply_H_backward(chebfi_ctx* ctx, const void* Y, const void* G, void*
   if (gD && nq > 0) {  // gD_ij = sum_n Re(conj((P^H G)_in) (P^H Y)_jn) on the atom blocks
     w.pa.alloc((size_t)nq * nb);
     w.pc.alloc((size_t)nq * nb);
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Yb.p, npw, 0.0, w.pa.p, nq, st, &w.splitk, "gemm_H");
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pc.p, nq, st, &w.splitk, "gemm_H");
+    gemm64(ctx, true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Yb.p, npw, 0.0, w.pa.p, nq, st, &w.splitk, "gemm_H");
+    gemm64(ctx, true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pc.p, nq, st, &w.splitk, "gemm_H");
     block_outer_grad(ctx, w.pa.p, w.pc.p, nq, nb, gD, st);
   }
   if (gV) vloc_gradient<double>(ctx, w.Ya.p, w.Yb.p, nb, gV, st, w.T2, w.tmp, w.tmp2);
@@ -1672,7 +1720,7 @@ int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t
     w.pt.alloc(np);  // B^{-1} r
     w.dvec1.alloc(nb);
     w.dvec2.alloc(nb);
-    gemm<double>(true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk, "gemm_refine");
+    gemm64(ctx, true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, w.Ya.p, npw, 0.0, w.pa.p, nq, st, &w.splitk, "gemm_refine");
     column_dots(nq, nb, w.pa.p, nq, w.pa.p, nq, w.dvec1.p, false, st);
     std::vector<double> bn(nb), rn(nb);
     CHEBFI_CUDA(cudaMemcpyAsync(bn.data(), w.dvec1.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
@@ -1681,7 +1729,7 @@ int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t
       // r = b - A q
       CHEBFI_CUDA(cudaMemcpyAsync(w.pc.p, w.pa.p, sizeof(double2) * np, cudaMemcpyDeviceToDevice, st));
       if (it > 0)
-        gemm<double>(false, false, nq, nb, nq, -1.0, ctx->d_Aref.p, nq, w.pb.p, nq, 1.0, w.pc.p, nq, st, &w.splitk,
+        gemm64(ctx, false, false, nq, nb, nq, -1.0, ctx->d_Aref.p, nq, w.pb.p, nq, 1.0, w.pc.p, nq, st, &w.splitk,
                      "gemm_refine");
       column_dots(nq, nb, w.pc.p, nq, w.pc.p, nq, w.dvec2.p, false, st);
       CHEBFI_CUDA(cudaMemcpyAsync(rn.data(), w.dvec2.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
@@ -1695,7 +1743,7 @@ int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t
       axpby<double>(nq, nb, 1.0, w.pt.p, nq, 1.0, w.pb.p, nq, w.pb.p, nq, st);
     }
     // S^{-1} x = x - P q
-    gemm<double>(false, false, npw, nb, nq, -1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk,
+    gemm64(ctx, false, false, npw, nb, nq, -1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, w.Ya.p, npw, st, &w.splitk,
                  "gemm_refine");
   }
   scatter_from(ctx, w.Ya.p, out, nb, ld, st);
@@ -1744,6 +1792,38 @@ int chebfi_cheb_filter_backward(chebfi_ctx* ctx, const void* Y0, const void* gYn
   if (prec == CHEBFI_F64) filter_backward<double>(ctx, nb, degree, lambda_lo, lambda_hi, s, gV, gD, st);
   else filter_backward<float>(ctx, nb, degree, lambda_lo, lambda_hi, s, gV, gD, st);
   if (gY0) scatter_from(ctx, w.Ya.p, gY0, nb, ld, st);
+  API_END(ctx)
+}
+
+int chebfi_set_fp64_gemm(chebfi_ctx* ctx, int engine, int nmod, int* precision_bits) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(engine >= CHEBFI_GEMM_AUTO && engine <= CHEBFI_GEMM_TENSOR, CHEBFI_ERR_ARG, "unknown GEMM engine");
+  CHEBFI_REQUIRE(nmod == 0 || (nmod >= kOzMinMod && nmod <= kOzMaxMod), CHEBFI_ERR_ARG,
+                 "modulus count must be 0 or 8..15");
+  ctx->fp64_gemm = engine;
+  if (nmod) ctx->oz_nmod = nmod;
+  if (precision_bits) *precision_bits = oz_precision_bits(ctx->oz_nmod);
+  API_END(ctx)
+}
+
+int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n, int64_t k, double alpha,
+                     const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                     void* stream) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(m >= 0 && n >= 0 && k >= 0, CHEBFI_ERR_ARG, "negative size");
+  if (m == 0 || n == 0) return CHEBFI_OK;
+  CHEBFI_REQUIRE(C && ldc >= m, CHEBFI_ERR_ARG, "C must be non-null with ldc >= m");
+  CHEBFI_REQUIRE(k == 0 || (A && B), CHEBFI_ERR_ARG, "null A or B");
+  CHEBFI_REQUIRE(lda >= (conjA ? k : m) && lda >= 1 && ldb >= (conjB ? n : k) && ldb >= 1, CHEBFI_ERR_ARG,
+                 "leading dimension too small");
+  cudaStream_t st = S(stream);
+  if (k == 0) {
+    // C = beta C: an empty product through the CUDA-core path (it applies beta)
+    gemm<double>(false, false, m, n, 0, alpha, nullptr, m, nullptr, 1, beta, (double2*)C, ldc, st);
+    return CHEBFI_OK;
+  }
+  gemm64(ctx, conjA != 0, conjB != 0, m, n, k, alpha, (const double2*)A, lda, (const double2*)B, ldb, beta,
+         (double2*)C, ldc, st, &ctx->w.splitk, "gemm_fp64");
   API_END(ctx)
 }
 

@@ -56,12 +56,13 @@ struct Error {
 
 // Checked kernel launch: counts the launch and turns a launch error into an exception.
 void after_launch(const char* name);
-extern int64_t* g_launch_counter;
+// (per host thread: each thread driving its own context counts into that context)
+extern thread_local int64_t* g_launch_counter;
 
 // Optional per-kernel timing: CUDA events recorded on the launching stream around every
 // launch while a context has profiling switched on (chebfi_profile_enable).
 struct Profiler;
-extern Profiler* g_prof;
+extern thread_local Profiler* g_prof;
 // work: the launch's algorithmic flops (GEMMs) or bytes (FFT passes), summed per name.
 void prof_begin(const char* name, cudaStream_t st, double work = 0.0);
 void prof_end(cudaStream_t st);
@@ -121,6 +122,25 @@ struct SplitBF16Buf {
     lo.alloc(count);
   }
   SplitBF16 view() const { return SplitBF16{hi.p, lo.p, ld}; }
+};
+
+// Residues of a real-embedded complex operand for the modular tensor-core GEMM (ozaki.cu):
+// one K-major bf16 matrix per modulus, res[mod * mstride + row * ld + k], and per complex
+// row the power of two s applied before rounding to integers.
+constexpr int kOzMinMod = 8, kOzMaxMod = 15;
+constexpr int kOzBadShift = -0x40000000;  // shift of a row holding Inf or NaN
+struct OzOperand {
+  DevBuf<__nv_bfloat16> res;
+  DevBuf<int32_t> shift;
+  int64_t crows = 0;   // complex rows
+  int64_t rows = 0;    // real rows (2 crows for the doubled A operand)
+  int64_t kreal = 0;   // reals per row (2 K)
+  int64_t ld = 0, mstride = 0;
+  int nmod = 0;
+};
+struct OzWork {
+  OzOperand A, B;
+  DevBuf<signed char> R;  // residue matrices of the product
 };
 
 // ----------------------------------------------------------------------------- FFT plan
@@ -251,6 +271,12 @@ struct chebfi_ctx {
   bool tc_ready = false;
   chebfi::SplitBF16Buf tcA1, tcA2, tcAG, tcAM;
   chebfi::Work w;
+  // FP64 complex GEMMs: engine choice (chebfi_set_fp64_gemm), modulus count of the
+  // tensor-core emulation, its workspace, and the residues of P^H and P (built on first use)
+  int fp64_gemm = CHEBFI_GEMM_AUTO;
+  int oz_nmod = 14;
+  chebfi::OzWork oz;
+  chebfi::OzOperand ozPh, ozP;
   double bound_rigorous = -1.0;
   // host-block filter: staging buffers, copy streams and their events (created on first use)
   chebfi::DevBuf<double2> stage[2];

@@ -69,6 +69,18 @@ void embed_n(int64_t m, int64_t k, const double2* A, int64_t lda, SplitBF16Buf& 
 // complex FP32 block (m x nb) -> K-major bf16 pair with 2m reals per column
 void split_block(int64_t m, int64_t nb, const float2* x, int64_t ldx, SplitBF16Buf& out, cudaStream_t st);
 
+// ---------------------------------------------------------------- FP64-accurate GEMM on tensor cores (ozaki.cu)
+// Residues of op(X) (nrows x K complex; row r is column r of X when rows_are_columns, else
+// row r of X; conjugated if conj) for the modular GEMM; doubled: the A operand's two real
+// rows per complex row.  The scale makes every row's 2-norm 2^(E-1)..2^E, E = oz_precision_bits.
+void oz_prepare(const double2* X, int64_t ldx, int64_t nrows, int64_t K, bool rows_are_columns, bool conj,
+                bool doubled, int nmod, OzOperand& out, cudaStream_t st);
+// C = alpha op(A) op(B) + beta C (complex, M = A.crows, N = B.crows; lower: only the complex
+// lower triangle of a square C is written) from prepared operands; R: residue workspace.
+void oz_gemm(const OzOperand& A, const OzOperand& B, double alpha, double beta, double2* C, int64_t ldc, bool lower,
+             DevBuf<signed char>& R, int* status, cudaStream_t st, const char* tag);
+int oz_precision_bits(int nmod);
+
 // ---------------------------------------------------------------- small kernels (blas.cu)
 // out = Dbd p: block-diagonal real D (packed row-major per-atom blocks) times complex p.
 template <typename R>
