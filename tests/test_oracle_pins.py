@@ -172,6 +172,56 @@ def _pin_filter_on_eigenvectors():
         assert np.abs(out).max() < 1e-10
 
 
+def _pencil_eigenpairs(cell):
+    """Eigenpairs of the dense pencil (H, S) from LAPACK, S-normalised: x^H S x = 1."""
+    import scipy.linalg
+    op = pw.PWOperator.from_cell(cell)
+    H, S = pw.dense_H(op), pw.dense_S(op)
+    w, X = scipy.linalg.eigh(H, S)
+    return op, H, S, w, X
+
+
+def _pin_rayleigh_quotients():
+    """Rayleigh quotients (Algorithm 2's first step): an exact eigenvector of the pencil gives
+    its eigenvalue whatever its scale; a plane wave e_G with V = V0 and no projectors gives
+    K_G + V0 = 2 pi^2 |m|^2 / L^2 + V0."""
+    cell = _tiny(N=12, natoms=3, nb=6, seed=13)
+    op, H, S, w, X = _pencil_eigenpairs(cell)
+    cols = [0, 1, 5, 17, len(w) - 1]
+    scale = np.array([1.0, -3.0, 0.5j, 2.0 + 1.0j, 1e-3])
+    rq = ch.rayleigh_quotients(op, X[:, cols] * scale[None, :])
+    np.testing.assert_allclose(rq, w[cols], rtol=0, atol=1e-11)
+    L, v0 = 6.0, -0.41
+    free = _free(_tiny(L=L), v0)
+    fop = pw.PWOperator.from_cell(free)
+    m = free.miller.astype(float)
+    pick = [0, 2, 11, 30]
+    E = np.zeros((free.npw, len(pick)), complex)
+    E[pick, range(len(pick))] = 1.0
+    np.testing.assert_allclose(ch.rayleigh_quotients(fop, E),
+                               2 * np.pi ** 2 / L ** 2 * np.sum(m[pick] ** 2, 1) + v0, atol=1e-12)
+
+
+def _pin_residuals():
+    """Residual norms ||H y - w S y||: zero for exact eigenpairs of the pencil; for
+    y = x_i + eps e_G with w = lambda_i, exactly eps ||(H - lambda_i S) e_G||, the norm of
+    column G of the dense H - lambda_i S; and x_i with w = lambda_i + delta gives
+    |delta| ||S x_i||."""
+    cell = _tiny(N=12, natoms=3, nb=6, seed=13)
+    op, H, S, w, X = _pencil_eigenpairs(cell)
+    cols = [0, 3, 8, 21]
+    r = ch.residuals(op, X[:, cols], w[cols])
+    assert np.abs(r).max() <= 1e-10 * max(1.0, np.abs(w).max())
+    eps, g = 1e-3, 7
+    Y = X[:, cols].copy()
+    Y[g, :] += eps
+    expect = eps * np.linalg.norm(H[:, g][:, None] - S[:, g][:, None] * w[cols][None, :], axis=0)
+    np.testing.assert_allclose(ch.residuals(op, Y, w[cols]), expect, rtol=1e-8)
+    delta = 0.125
+    expect2 = delta * np.linalg.norm(S @ X[:, cols], axis=0)
+    np.testing.assert_allclose(ch.residuals(op, X[:, cols], w[cols] + delta), expect2, rtol=1e-8)
+
+
 # ----------------------------------------------------------------------------- tests
 def test_free_electron_shells():
     _pin_free_electron()
@@ -289,6 +339,14 @@ def test_rigorous_upper_bound_is_an_upper_bound():
     assert exact.max() <= ch.upper_bound(op, "rigorous")
 
 
+def test_rayleigh_quotients_of_exact_eigenpairs_and_plane_waves():
+    _pin_rayleigh_quotients()
+
+
+def test_residuals_of_exact_and_perturbed_eigenpairs():
+    _pin_residuals()
+
+
 # --------------------------------------------------------------- planted mistakes
 def _mut_kinetic(monkeypatch):
     orig = pw.kinetic
@@ -320,12 +378,35 @@ def _mut_recurrence(monkeypatch):
     monkeypatch.setattr(ch, "filter_plain", bad)
 
 
+def _mut_rq_without_S(monkeypatch):
+    def bad(op, Y):
+        Y = np.asarray(Y)
+        return (np.einsum("gn,gn->n", Y.conj(), op.apply_H(Y)).real
+                / np.einsum("gn,gn->n", Y.conj(), Y).real)
+    monkeypatch.setattr(ch, "rayleigh_quotients", bad)
+
+
+def _mut_residual_without_S(monkeypatch):
+    monkeypatch.setattr(ch, "residuals",
+                        lambda op, Y, w: np.linalg.norm(op.apply_H(Y) - np.asarray(Y) * np.asarray(w)[None, :],
+                                                        axis=0))
+
+
+def _mut_residual_sign(monkeypatch):
+    monkeypatch.setattr(ch, "residuals",
+                        lambda op, Y, w: np.linalg.norm(op.apply_H(Y) + op.apply_S(Y) * np.asarray(w)[None, :],
+                                                        axis=0))
+
+
 @pytest.mark.parametrize("mutation, pins", [
     (_mut_kinetic, [_pin_free_electron]),
     (_mut_vtilde_conj, [_pin_cosine_potential]),
     (_mut_projection_transpose, [_pin_hermitian]),
     (_mut_woodbury_sign, [_pin_woodbury]),
     (_mut_recurrence, [_pin_filter_on_eigenvectors]),
+    (_mut_rq_without_S, [_pin_rayleigh_quotients]),
+    (_mut_residual_without_S, [_pin_residuals]),
+    (_mut_residual_sign, [_pin_residuals]),
 ])
 def test_pins_catch_planted_mistakes(monkeypatch, mutation, pins):
     mutation(monkeypatch)
