@@ -280,6 +280,20 @@ int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n
                      const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                      void* stream);
 
+/* Dense Hermitian eigensolver of the Rayleigh-Ritz step (Algorithm 2; ELPA in the paper):
+ *  CHEBFI_EIG_JACOBI: FP64 cyclic Jacobi (rounds of n/2 disjoint rotations).
+ *  CHEBFI_EIG_REFINED: FP32 cyclic Jacobi for approximate eigenvectors, then the iterative
+ *    refinement of Ogita & Aishima (2018) in FP64 GEMMs -- from G = X^H X and S = X^H A X,
+ *    lambda_i = S_ii / G_ii, E_ij = (S_ij - lambda_j G_ij) / (lambda_j - lambda_i),
+ *    E_ii = (1 - G_ii) / 2, X <- X (I + E) -- until max |E| <= 1e-10; pairs too close
+ *    for the formula are only orthogonalised and their cluster's block of X^H A X is then
+ *    diagonalised by FP64 Jacobi.  Falls back to CHEBFI_EIG_JACOBI if it does not converge.
+ *  CHEBFI_EIG_AUTO (initial): REFINED from 512 bands up, JACOBI below. */
+enum { CHEBFI_EIG_AUTO = 0, CHEBFI_EIG_JACOBI = 1, CHEBFI_EIG_REFINED = 2 };
+int chebfi_set_eigensolver(chebfi_ctx* ctx, int mode);
+/* Refinement steps taken by the last dense eigensolve on ctx (0: FP64 Jacobi ran). */
+int chebfi_eigensolver_steps(const chebfi_ctx* ctx);
+
 /* Synchronise the context's work and return the first device-detected error, if any. */
 int chebfi_sync_status(chebfi_ctx* ctx);
 

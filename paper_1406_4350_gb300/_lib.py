@@ -18,6 +18,7 @@ OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_FILTER_OV
     0, -1, -2, -3, -4, -5, -6, -7
 F64, F32, MIXED = 0, 1, 2
 GEMM_AUTO, GEMM_CUDA_CORES, GEMM_TENSOR = 0, 1, 2
+EIG_AUTO, EIG_JACOBI, EIG_REFINED = 0, 1, 2
 BOUND_PAPER, BOUND_RIGOROUS = 0, 1
 
 
@@ -71,6 +72,8 @@ SIGNATURES = {
     "chebfi_set_fp64_gemm": (c_int, [c_void_p, c_int, c_int, P_int]),
     "chebfi_gemm_fp64": (c_int, [c_void_p, c_int, c_int, c_int64, c_int64, c_int64, c_double, c_void_p, c_int64,
                                  c_void_p, c_int64, c_double, c_void_p, c_int64, c_void_p]),
+    "chebfi_set_eigensolver": (c_int, [c_void_p, c_int]),
+    "chebfi_eigensolver_steps": (c_int, [c_void_p]),
     "chebfi_sync_status": (c_int, [c_void_p]),
     "chebfi_kernel_launches": (c_int64, [c_void_p]),
     "chebfi_profile_enable": (c_int, [c_void_p, c_int]),

@@ -285,6 +285,16 @@ class ChebFI:
         self._check(self.lib.chebfi_set_fp64_gemm(self.h, engine, nmod, ctypes.byref(e)))
         return e.value
 
+    def set_eigensolver(self, mode: int):
+        """Dense eigensolver of Rayleigh-Ritz: EIG_AUTO, EIG_JACOBI (FP64) or EIG_REFINED (FP32
+        Jacobi + FP64 refinement)."""
+        self._check(self.lib.chebfi_set_eigensolver(self.h, mode))
+
+    @property
+    def eigensolver_steps(self) -> int:
+        """Refinement steps of the last dense eigensolve (0: FP64 Jacobi ran)."""
+        return int(self.lib.chebfi_eigensolver_steps(self.h))
+
     def gemm_fp64(self, A, B, conjA: bool = False, conjB: bool = False, alpha: float = 1.0, beta: float = 0.0,
                   C=None):
         """C = alpha op(A) op(B) + beta C for column-major complex128 CUDA matrices."""

@@ -12,6 +12,7 @@
 #include <stdexcept>
 #include <vector>
 #include <complex>
+#include <functional>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -505,6 +506,114 @@ void rq_sorted(chebfi_ctx* ctx, const double2* Y, int64_t nb, double* rq, cudaSt
   divide(nb, w.dvec1.p, w.dvec2.p, rq, st);
 }
 
+// Dense Hermitian eigenproblem of the Rayleigh-Ritz step (Algorithm 2; the paper calls
+// ELPA): A (n x n, ld n) -> ascending eigenvalues w and orthonormal eigenvectors X (ld n).
+// FP64 cyclic Jacobi for small n; from n = 512 up (or when selected) the FP32 Jacobi gives
+// approximate vectors, which the iterative refinement of Ogita & Aishima (2018) brings to
+// FP64 accuracy with FP64 GEMMs (quadratic convergence, 2-4 steps); pairs too close for its
+// formula end in a dense FP64 Jacobi of their cluster's block.  A is destroyed.
+void eigh_rr(chebfi_ctx* ctx, int64_t n, double2* A, double* w, double2* X, cudaStream_t st) {
+  Work& wk = ctx->w;
+  int* status = ctx->d_status.p;
+  const bool refined = ctx->eig_mode == CHEBFI_EIG_REFINED || (ctx->eig_mode == CHEBFI_EIG_AUTO && n >= 512);
+  ctx->eig_iters = 0;
+  if (!refined || n < 2) {
+    jacobi_eigh(n, A, n, w, X, n, status, st, &wk.small5);
+    return;
+  }
+  const size_t nn = (size_t)n * n;
+  constexpr int kCap = 1 << 16;
+  wk.e32a.alloc(nn);
+  wk.e32b.alloc(nn);
+  wk.e32w.alloc(n);
+  wk.eG.alloc(nn);
+  wk.eS.alloc(nn);
+  wk.eAX.alloc(nn);
+  wk.eM.alloc(nn);
+  wk.eX.alloc(nn);
+  wk.elam.alloc(n);
+  wk.estats.alloc(2);
+  wk.enp.alloc(1);
+  wk.epairs.alloc(kCap);
+  DevBuf<double2>* ws = &wk.splitk;
+  // stage 1: FP32 Jacobi on a copy
+  convert(n, n, A, n, wk.e32a.p, n, st);
+  jacobi_eigh_f32(n, wk.e32a.p, n, wk.e32w.p, wk.e32b.p, n, status, st, &wk.small5);
+  convert(n, n, wk.e32b.p, n, X, n, st);
+  // stage 2: refinement in FP64
+  double2 *Xc = X, *Xn = wk.eX.p;
+  bool conv = false;
+  int npairs = 0;
+  for (int it = 0; it < 8 && !conv; ++it) {
+    gemm64(ctx, true, false, n, n, n, 1.0, Xc, n, Xc, n, 0.0, wk.eG.p, n, st, ws, "gemm_eig", true);
+    mirror_lower(n, wk.eG.p, n, st);
+    gemm64(ctx, false, false, n, n, n, 1.0, A, n, Xc, n, 0.0, wk.eAX.p, n, st, ws, "gemm_eig");
+    gemm64(ctx, true, false, n, n, n, 1.0, Xc, n, wk.eAX.p, n, 0.0, wk.eS.p, n, st, ws, "gemm_eig", true);
+    mirror_lower(n, wk.eS.p, n, st);
+    oa_step(n, wk.eG.p, wk.eS.p, wk.elam.p, wk.eM.p, wk.estats.p, wk.enp.p, wk.epairs.p, kCap, st);
+    unsigned long long hs[2];
+    CHEBFI_CUDA(cudaMemcpyAsync(hs, wk.estats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    CHEBFI_CUDA(cudaMemcpyAsync(&npairs, wk.enp.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    gemm64(ctx, false, false, n, n, n, 1.0, Xc, n, wk.eM.p, n, 0.0, Xn, n, st, ws, "gemm_eig");
+    std::swap(Xc, Xn);
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+    double emax;
+    std::memcpy(&emax, &hs[1], sizeof(double));
+    ctx->eig_iters = it + 1;
+    // after an update of size emax the vectors are accurate to O(emax^2): below rounding
+    conv = std::isfinite(emax) && emax <= 1e-10;
+  }
+  if (!conv || npairs > kCap) {
+    // not converged (or too many near-equal pairs): the FP64 Jacobi of the original matrix
+    // (A is still intact; the refinement only read it)
+    ctx->eig_iters = 0;
+    jacobi_eigh(n, A, n, w, X, n, status, st, &wk.small5);
+    return;
+  }
+  if (npairs > 0) {
+    // clusters: connected components of the listed pairs; each block of X^H A X on a
+    // component is diagonalised by FP64 Jacobi and its columns rotated
+    std::vector<int2> hp(npairs);
+    CHEBFI_CUDA(cudaMemcpyAsync(hp.data(), wk.epairs.p, sizeof(int2) * npairs, cudaMemcpyDeviceToHost, st));
+    gemm64(ctx, false, false, n, n, n, 1.0, A, n, Xc, n, 0.0, wk.eAX.p, n, st, ws, "gemm_eig");
+    gemm64(ctx, true, false, n, n, n, 1.0, Xc, n, wk.eAX.p, n, 0.0, wk.eS.p, n, st, ws, "gemm_eig");
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> parent(n);
+    std::iota(parent.begin(), parent.end(), 0);
+    std::function<int(int)> find = [&](int v) { return parent[v] == v ? v : parent[v] = find(parent[v]); };
+    for (const int2& pr : hp) parent[find(pr.x)] = find(pr.y);
+    std::map<int, std::vector<int>> comp;
+    for (const int2& pr : hp) {
+      comp[find(pr.x)];
+    }
+    for (int v = 0; v < (int)n; ++v)
+      if (comp.count(find(v))) comp[find(v)].push_back(v);
+    for (auto& kv : comp) {
+      const std::vector<int>& idx = kv.second;
+      const int k = (int)idx.size();
+      wk.eidx.upload(idx.data(), k, st);
+      wk.esub.alloc((size_t)k * k);
+      wk.eZ.alloc((size_t)k * k);
+      wk.esw.alloc(k);
+      wk.eC1.alloc((size_t)n * k);
+      wk.eC2.alloc((size_t)n * k);
+      gather_sub(k, wk.eidx.p, wk.eS.p, n, wk.esub.p, st);
+      hermitize(k, wk.esub.p, k, st);
+      jacobi_eigh(k, wk.esub.p, k, wk.esw.p, wk.eZ.p, k, status, st, &wk.small5);
+      gather_cols(n, k, wk.eidx.p, Xc, n, wk.eC1.p, n, st);
+      gemm<double>(false, false, n, k, k, 1.0, wk.eC1.p, n, wk.eZ.p, k, 0.0, wk.eC2.p, n, st, ws, "gemm_eig");
+      scatter_cols(n, k, wk.eidx.p, Xc, n, wk.eC2.p, n, st);
+      scatter_vals(k, wk.eidx.p, wk.esw.p, wk.elam.p, st);
+      CHEBFI_CUDA(cudaStreamSynchronize(st));  // the index list is reused by the next cluster
+    }
+  }
+  if (Xc == X) {
+    CHEBFI_CUDA(cudaMemcpyAsync(wk.eX.p, X, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
+    Xc = wk.eX.p;
+  }
+  sort_eigpairs(n, wk.elam.p, Xc, w, X, st);
+}
+
 // Rayleigh-Ritz (Algorithm 2, last three steps) on the sorted FP64 block w.Ya.
 void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStream_t st) {
   Work& w = ctx->w;
@@ -547,7 +656,7 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   gemm64(ctx, false, true, nb, nb, nb, 1.0, X, nb, Li, nb, 0.0, Hs, nb, st, ws, "gemm_rr");
   hermitize(nb, Hs, nb, st);
   // C = Z Lambda Z^H
-  jacobi_eigh(nb, Hs, nb, evals, X, nb, ctx->d_status.p, st, &w.small5);
+  eigh_rr(ctx, nb, Hs, evals, X, st);
   check_status(ctx, st, "rayleigh_ritz");
   // rotation R = s L^{-H} Z; Y <- Y R, HY <- HY R, p <- p R
   gemm64(ctx, true, false, nb, nb, nb, 1.0, Li, nb, X, nb, 0.0, Ss, nb, st, ws, "gemm_rr");
@@ -664,7 +773,7 @@ double rigorous_bound(chebfi_ctx* ctx) {
       gemm64(ctx, false, false, nq, nq, nq, 1.0, Dd.p, nq, ctx->d_L.p, nq, 0.0, T.p, nq, st, ws);
       gemm64(ctx, true, false, nq, nq, nq, 1.0, ctx->d_L.p, nq, T.p, nq, 0.0, A.p, nq, st, ws);
       hermitize(nq, A.p, nq, st);
-      jacobi_eigh(nq, A.p, nq, w.p, V.p, nq, ctx->d_status.p, st, &ctx->w.small5);
+      eigh_rr(ctx, nq, A.p, w.p, V.p, st);
       check_status(ctx, st, "upper_bound");
       if (which == 0) num += std::max(0.0, host_max(ctx, w.p, nq, st));
       else smin = 1.0 + std::min(0.0, host_max(ctx, w.p, nq, st, true));
@@ -1805,6 +1914,15 @@ int chebfi_set_fp64_gemm(chebfi_ctx* ctx, int engine, int nmod, int* precision_b
   if (precision_bits) *precision_bits = oz_precision_bits(ctx->oz_nmod);
   API_END(ctx)
 }
+
+int chebfi_set_eigensolver(chebfi_ctx* ctx, int mode) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(mode >= CHEBFI_EIG_AUTO && mode <= CHEBFI_EIG_REFINED, CHEBFI_ERR_ARG, "unknown eigensolver");
+  ctx->eig_mode = mode;
+  API_END(ctx)
+}
+
+int chebfi_eigensolver_steps(const chebfi_ctx* ctx) { return ctx ? ctx->eig_iters : CHEBFI_ERR_ARG; }
 
 int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n, int64_t k, double alpha,
                      const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,

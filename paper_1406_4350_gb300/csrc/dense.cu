@@ -149,35 +149,53 @@ __global__ void k_zero_upper(int64_t n, double2* A, int64_t lda) {
 }
 
 // ------------------------------------------------------------------ Jacobi
+// Templated on the real type: FP64 for the eigensolver itself, FP32 for the first stage of
+// the refined eigensolver (whose vectors are then refined to FP64 accuracy).
+template <typename R> struct JacEps;
+template <> struct JacEps<double> {
+  static constexpr double v = 1.1102230246251565e-16, tiny = 1e-300;
+};
+template <> struct JacEps<float> {
+  static constexpr float v = 5.9604645e-8f, tiny = 1e-37f;
+};
+
 __device__ __forceinline__ int64_t rr_player(int64_t pos, int64_t round, int64_t n) {
   return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n - 1);
 }
 
-struct Rot {
-  double c, s;
-  double2 ph;  // e^{i phi}
+template <typename R> struct RotT {
+  R c, s;
+  cplx<R> ph;  // e^{i phi}
 };
 
-__global__ void k_jac_params(int64_t n0, int64_t n, int64_t round, const double2* __restrict__ A, int64_t lda,
-                             Rot* __restrict__ rot, int* __restrict__ pairs) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n / 2) return;
+__device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
+__device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
+
+// rotation parameters of pair t of the given round (p < q; q = -1 for the padding player)
+template <typename R>
+__device__ __forceinline__ void jac_params_item(int64_t t, int64_t n0, int64_t n, int64_t round,
+                                                const cplx<R>* __restrict__ A, int64_t lda, RotT<R>* __restrict__ rot,
+                                                int* __restrict__ pairs) {
   int64_t p = rr_player(t, round, n), q = rr_player(n - 1 - t, round, n);
-  if (p > q) { const int64_t tmp = p; p = q; q = tmp; }
-  Rot r;
-  r.c = 1.0;
-  r.s = 0.0;
-  r.ph = make_double2(1.0, 0.0);
-  if (q < n0) {  // skip pairs with the padding player
-    const double2 h = A[p + q * lda];
-    const double g = hypot(h.x, h.y);
-    const double app = A[p + p * lda].x, aqq = A[q + q * lda].x;
-    if (g > 1e-300 && g > 1.1102230246251565e-16 * sqrt(fabs(app * aqq))) {
-      const double zeta = (aqq - app) / (2.0 * g);
-      const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-      r.c = 1.0 / sqrt(1.0 + t_ * t_);
+  if (p > q) {
+    const int64_t tmp = p;
+    p = q;
+    q = tmp;
+  }
+  RotT<R> r;
+  r.c = (R)1;
+  r.s = (R)0;
+  r.ph = cmake<cplx<R>>(1.0, 0.0);
+  if (q < n0) {
+    const cplx<R> h = A[p + q * lda];
+    const R g = hyp(h.x, h.y);
+    const R app = A[p + p * lda].x, aqq = A[q + q * lda].x;
+    if (g > JacEps<R>::tiny && g > JacEps<R>::v * sqrt(fabs(app * aqq))) {
+      const R zeta = (aqq - app) / ((R)2 * g);
+      const R t_ = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + hyp((R)1, zeta));
+      r.c = (R)1 / sqrt((R)1 + t_ * t_);
       r.s = t_ * r.c;
-      r.ph = make_double2(h.x / g, h.y / g);
+      r.ph = cmake<cplx<R>>(h.x / g, h.y / g);
     }
   } else {
     q = -1;
@@ -187,80 +205,68 @@ __global__ void k_jac_params(int64_t n0, int64_t n, int64_t round, const double2
   pairs[2 * t + 1] = (int)q;
 }
 
-// One round of rotations in one pass: thread (t1, t2) maps the 2 x 2 block of A on rows
+template <typename R>
+__global__ void k_jac_params(int64_t n0, int64_t n, int64_t round, const cplx<R>* __restrict__ A, int64_t lda,
+                             RotT<R>* __restrict__ rot, int* __restrict__ pairs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n / 2) jac_params_item<R>(t, n0, n, round, A, lda, rot, pairs);
+}
+
+// [a, b] <- [c a - s e^{i phi} b, s a + c e^{i phi} b] (rows, U^H from the left) and
+// [a, b] <- [c a - s e^{-i phi} b, s a + c e^{-i phi} b] (columns, U from the right)
+template <typename C, typename R>
+__device__ __forceinline__ void rot2(C& a, C& b, R c, R s, C ph) {
+  C na, nb;
+  na.x = c * a.x - s * (ph.x * b.x - ph.y * b.y);
+  na.y = c * a.y - s * (ph.x * b.y + ph.y * b.x);
+  nb.x = s * a.x + c * (ph.x * b.x - ph.y * b.y);
+  nb.y = s * a.y + c * (ph.x * b.y + ph.y * b.x);
+  a = na;
+  b = nb;
+}
+
+// One round of rotations in one pass: item (t1, t2) maps the 2 x 2 block of A on rows
 // {p1, q1} and columns {p2, q2} to U1^H A U2 (the pairs are disjoint, so every element of A
-// belongs to exactly one block); the remaining threads apply V <- V U2 on columns {p2, q2}.
-__device__ __forceinline__ void jac_apply_item(int64_t idx, int64_t h, int64_t n, double2* A, int64_t lda, double2* V,
-                                               int64_t ldv, const Rot* __restrict__ rot, const int* __restrict__ pairs) {
+// belongs to exactly one block); the remaining items apply V <- V U2 on columns {p2, q2}.
+template <typename R>
+__device__ __forceinline__ void jac_apply_item(int64_t idx, int64_t h, int64_t n, cplx<R>* A, int64_t lda,
+                                               cplx<R>* V, int64_t ldv, const RotT<R>* __restrict__ rot,
+                                               const int* __restrict__ pairs) {
+  using C = cplx<R>;
   const int64_t nblk_a = h * h;
   if (idx < nblk_a) {
     const int64_t t1 = idx % h, t2 = idx / h;
     const int q1 = pairs[2 * t1 + 1], q2 = pairs[2 * t2 + 1];
     const int p1 = pairs[2 * t1], p2 = pairs[2 * t2];
-    const Rot r1 = rot[t1], r2 = rot[t2];
-    const bool act1 = q1 >= 0 && r1.s != 0.0, act2 = q2 >= 0 && r2.s != 0.0;
+    const RotT<R> r1 = rot[t1], r2 = rot[t2];
+    const bool act1 = q1 >= 0 && r1.s != (R)0, act2 = q2 >= 0 && r2.s != (R)0;
     if (!act1 && !act2) return;
-    // the padding player (q < 0) never owns a row or column of A
+    const C cph2 = conjg(r2.ph);
+    // the padding player (q < 0) owns no row or column of A: 1 x 2 or 2 x 1 blocks
     if (q1 < 0 || q2 < 0) {
-      // a real pair against the padding: only the real pair's own rotation applies on its
-      // side of the blocks it shares with other pairs; handled as a 1 x 2 or 2 x 1 block
       if (q1 < 0 && q2 < 0) return;
       if (q1 < 0) {  // row p1 alone, columns {p2, q2} rotate by U2
-        double2 a = A[p1 + (int64_t)p2 * lda], b = A[p1 + (int64_t)q2 * lda];
-        const double2 sc = make_double2(r2.s * r2.ph.x, -r2.s * r2.ph.y), cc = make_double2(r2.c * r2.ph.x, -r2.c * r2.ph.y);
-        double2 na, nb;
-        na.x = r2.c * a.x - (b.x * sc.x - b.y * sc.y);
-        na.y = r2.c * a.y - (b.x * sc.y + b.y * sc.x);
-        nb.x = r2.s * a.x + (b.x * cc.x - b.y * cc.y);
-        nb.y = r2.s * a.y + (b.x * cc.y + b.y * cc.x);
-        A[p1 + (int64_t)p2 * lda] = na;
-        A[p1 + (int64_t)q2 * lda] = nb;
+        C a = A[p1 + (int64_t)p2 * lda], b = A[p1 + (int64_t)q2 * lda];
+        rot2(a, b, r2.c, r2.s, cph2);
+        A[p1 + (int64_t)p2 * lda] = a;
+        A[p1 + (int64_t)q2 * lda] = b;
       } else {  // column p2 alone, rows {p1, q1} rotate by U1^H
-        double2 a = A[p1 + (int64_t)p2 * lda], b = A[q1 + (int64_t)p2 * lda];
-        const double2 sph = make_double2(r1.s * r1.ph.x, r1.s * r1.ph.y), cph = make_double2(r1.c * r1.ph.x, r1.c * r1.ph.y);
-        double2 na, nb;
-        na.x = r1.c * a.x - (sph.x * b.x - sph.y * b.y);
-        na.y = r1.c * a.y - (sph.x * b.y + sph.y * b.x);
-        nb.x = r1.s * a.x + (cph.x * b.x - cph.y * b.y);
-        nb.y = r1.s * a.y + (cph.x * b.y + cph.y * b.x);
-        A[p1 + (int64_t)p2 * lda] = na;
-        A[q1 + (int64_t)p2 * lda] = nb;
+        C a = A[p1 + (int64_t)p2 * lda], b = A[q1 + (int64_t)p2 * lda];
+        rot2(a, b, r1.c, r1.s, r1.ph);
+        A[p1 + (int64_t)p2 * lda] = a;
+        A[q1 + (int64_t)p2 * lda] = b;
       }
       return;
     }
-    double2 m00 = A[p1 + (int64_t)p2 * lda], m10 = A[q1 + (int64_t)p2 * lda];
-    double2 m01 = A[p1 + (int64_t)q2 * lda], m11 = A[q1 + (int64_t)q2 * lda];
+    C m00 = A[p1 + (int64_t)p2 * lda], m10 = A[q1 + (int64_t)p2 * lda];
+    C m01 = A[p1 + (int64_t)q2 * lda], m11 = A[q1 + (int64_t)q2 * lda];
     if (act1) {  // rows: [m0*; m1*] <- U1^H [m0*; m1*]
-      const double2 sph = make_double2(r1.s * r1.ph.x, r1.s * r1.ph.y), cph = make_double2(r1.c * r1.ph.x, r1.c * r1.ph.y);
-      double2 a0, a1;
-      a0.x = r1.c * m00.x - (sph.x * m10.x - sph.y * m10.y);
-      a0.y = r1.c * m00.y - (sph.x * m10.y + sph.y * m10.x);
-      a1.x = r1.s * m00.x + (cph.x * m10.x - cph.y * m10.y);
-      a1.y = r1.s * m00.y + (cph.x * m10.y + cph.y * m10.x);
-      m00 = a0;
-      m10 = a1;
-      a0.x = r1.c * m01.x - (sph.x * m11.x - sph.y * m11.y);
-      a0.y = r1.c * m01.y - (sph.x * m11.y + sph.y * m11.x);
-      a1.x = r1.s * m01.x + (cph.x * m11.x - cph.y * m11.y);
-      a1.y = r1.s * m01.y + (cph.x * m11.y + cph.y * m11.x);
-      m01 = a0;
-      m11 = a1;
+      rot2(m00, m10, r1.c, r1.s, r1.ph);
+      rot2(m01, m11, r1.c, r1.s, r1.ph);
     }
     if (act2) {  // columns: [m*0, m*1] <- [m*0, m*1] U2
-      const double2 sc = make_double2(r2.s * r2.ph.x, -r2.s * r2.ph.y), cc = make_double2(r2.c * r2.ph.x, -r2.c * r2.ph.y);
-      double2 b0, b1;
-      b0.x = r2.c * m00.x - (m01.x * sc.x - m01.y * sc.y);
-      b0.y = r2.c * m00.y - (m01.x * sc.y + m01.y * sc.x);
-      b1.x = r2.s * m00.x + (m01.x * cc.x - m01.y * cc.y);
-      b1.y = r2.s * m00.y + (m01.x * cc.y + m01.y * cc.x);
-      m00 = b0;
-      m01 = b1;
-      b0.x = r2.c * m10.x - (m11.x * sc.x - m11.y * sc.y);
-      b0.y = r2.c * m10.y - (m11.x * sc.y + m11.y * sc.x);
-      b1.x = r2.s * m10.x + (m11.x * cc.x - m11.y * cc.y);
-      b1.y = r2.s * m10.y + (m11.x * cc.y + m11.y * cc.x);
-      m10 = b0;
-      m11 = b1;
+      rot2(m00, m01, r2.c, r2.s, cph2);
+      rot2(m10, m11, r2.c, r2.s, cph2);
     }
     A[p1 + (int64_t)p2 * lda] = m00;
     A[q1 + (int64_t)p2 * lda] = m10;
@@ -273,29 +279,26 @@ __device__ __forceinline__ void jac_apply_item(int64_t idx, int64_t h, int64_t n
   const int64_t i = vidx % n, t = vidx / n;
   const int q = pairs[2 * t + 1];
   if (q < 0) return;
-  const Rot r = rot[t];
-  if (r.s == 0.0) return;
+  const RotT<R> r = rot[t];
+  if (r.s == (R)0) return;
   const int p = pairs[2 * t];
-  const double2 ap = V[i + (int64_t)p * ldv], aq = V[i + (int64_t)q * ldv];
-  const double2 sc = make_double2(r.s * r.ph.x, -r.s * r.ph.y), cc = make_double2(r.c * r.ph.x, -r.c * r.ph.y);
-  double2 np, nq;
-  np.x = r.c * ap.x - (aq.x * sc.x - aq.y * sc.y);
-  np.y = r.c * ap.y - (aq.x * sc.y + aq.y * sc.x);
-  nq.x = r.s * ap.x + (aq.x * cc.x - aq.y * cc.y);
-  nq.y = r.s * ap.y + (aq.x * cc.y + aq.y * cc.x);
-  V[i + (int64_t)p * ldv] = np;
-  V[i + (int64_t)q * ldv] = nq;
+  C ap = V[i + (int64_t)p * ldv], aq = V[i + (int64_t)q * ldv];
+  rot2(ap, aq, r.c, r.s, conjg(r.ph));
+  V[i + (int64_t)p * ldv] = ap;
+  V[i + (int64_t)q * ldv] = aq;
 }
 
-__global__ void k_jac_apply(int64_t h, int64_t n, double2* A, int64_t lda, double2* V, int64_t ldv,
-                            const Rot* __restrict__ rot, const int* __restrict__ pairs) {
+template <typename R>
+__global__ void k_jac_apply(int64_t h, int64_t n, cplx<R>* A, int64_t lda, cplx<R>* V, int64_t ldv,
+                            const RotT<R>* __restrict__ rot, const int* __restrict__ pairs) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  jac_apply_item(idx, h, n, A, lda, V, ldv, rot, pairs);
+  jac_apply_item<R>(idx, h, n, A, lda, V, ldv, rot, pairs);
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks resident).  The wait is bounded:
-// after ~1 s it records CHEBFI_ERR_CUDA and lets the block go on.
-__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* status) {
+// after limit_ns it records CHEBFI_ERR_CUDA and lets the block go on.
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* status,
+                                             unsigned long long limit_ns = 1000000000ull) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned g = atomicAdd(gen, 0u);
@@ -310,7 +313,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, uns
       while (atomicAdd(gen, 0u) == g) {
         __nanosleep(32);
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > 1000000000ull) {
+        if (t - t0 > limit_ns) {
           flag_error(status, CHEBFI_ERR_CUDA);
           break;
         }
@@ -323,86 +326,73 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, uns
 
 // All n-1 rounds of one Jacobi sweep in one cooperative launch: per round, the rotation
 // parameters of the n/2 pairs, a grid barrier, the one-pass update of A and V, a barrier.
-__global__ void k_jac_sweep(int64_t n0, int64_t n, double2* A, int64_t lda, double2* V, int64_t ldv, Rot* rot,
+template <typename R>
+__global__ void k_jac_sweep(int64_t n0, int64_t n, cplx<R>* A, int64_t lda, cplx<R>* V, int64_t ldv, RotT<R>* rot,
                             int* pairs, unsigned* bar, int* status) {
   const int64_t h = n / 2;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t round = 0; round < n - 1; ++round) {
-    // parameters (same arithmetic as k_jac_params)
-    for (int64_t t = tid; t < h; t += nthreads) {
-      int64_t p = rr_player(t, round, n), q = rr_player(n - 1 - t, round, n);
-      if (p > q) {
-        const int64_t tmp = p;
-        p = q;
-        q = tmp;
-      }
-      Rot r;
-      r.c = 1.0;
-      r.s = 0.0;
-      r.ph = make_double2(1.0, 0.0);
-      if (q < n0) {
-        const double2 hh = A[p + q * lda];
-        const double g = hypot(hh.x, hh.y);
-        const double app = A[p + p * lda].x, aqq = A[q + q * lda].x;
-        if (g > 1e-300 && g > 1.1102230246251565e-16 * sqrt(fabs(app * aqq))) {
-          const double zeta = (aqq - app) / (2.0 * g);
-          const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-          r.c = 1.0 / sqrt(1.0 + t_ * t_);
-          r.s = t_ * r.c;
-          r.ph = make_double2(hh.x / g, hh.y / g);
-        }
-      } else {
-        q = -1;
-      }
-      rot[t] = r;
-      pairs[2 * t] = (int)p;
-      pairs[2 * t + 1] = (int)q;
-    }
+    for (int64_t t = tid; t < h; t += nthreads) jac_params_item<R>(t, n0, n, round, A, lda, rot, pairs);
     grid_barrier(bar, bar + 1, gridDim.x, status);
-    for (int64_t i = tid; i < h * h + n0 * h; i += nthreads) jac_apply_item(i, h, n0, A, lda, V, ldv, rot, pairs);
+    for (int64_t i = tid; i < h * h + n0 * h; i += nthreads) jac_apply_item<R>(i, h, n0, A, lda, V, ldv, rot, pairs);
     grid_barrier(bar, bar + 1, gridDim.x, status);
   }
 }
 
-// out[0] = sum of |off-diagonal|^2, out[1] = total |A|^2 (single block, fixed order).
-__global__ void k_offnorm(int64_t n, const double2* A, int64_t lda, double* out) {
+// Per-block partial sums of |off-diagonal|^2 and |A|^2 (FP64), then one block adds the
+// partials in block order: deterministic.
+template <typename R>
+__global__ void k_offnorm_part(int64_t n, const cplx<R>* A, int64_t lda, double* part) {
   __shared__ double r0[256], r1[256];
   double s0 = 0, s1 = 0;
-  for (int64_t e = threadIdx.x; e < n * n; e += blockDim.x) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % n, j = e / n;
-    const double2 a = A[i + j * lda];
-    const double v = a.x * a.x + a.y * a.y;
+    const cplx<R> a = A[i + j * lda];
+    const double v = (double)a.x * a.x + (double)a.y * a.y;
     s1 += v;
     if (i != j) s0 += v;
   }
   r0[threadIdx.x] = s0;
   r1[threadIdx.x] = s1;
   __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) {
-      r0[threadIdx.x] += r0[threadIdx.x + h];
-      r1[threadIdx.x] += r1[threadIdx.x + h];
+  for (int hh = blockDim.x / 2; hh > 0; hh >>= 1) {
+    if ((int)threadIdx.x < hh) {
+      r0[threadIdx.x] += r0[threadIdx.x + hh];
+      r1[threadIdx.x] += r1[threadIdx.x + hh];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = r0[0];
-    out[1] = r1[0];
+    part[2 * blockIdx.x] = r0[0];
+    part[2 * blockIdx.x + 1] = r1[0];
+  }
+}
+
+__global__ void k_offnorm_sum(int nparts, const double* part, double* out) {
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int b = 0; b < nparts; ++b) {
+      s0 += part[2 * b];
+      s1 += part[2 * b + 1];
+    }
+    out[0] = s0;
+    out[1] = s1;
   }
 }
 
 // Sort eigenpairs ascending (stable): rank by counting, then permute w and the columns of V.
-__global__ void k_eig_sort(int64_t n, const double2* __restrict__ A, int64_t lda, const double2* __restrict__ Vin,
-                           int64_t ldvi, double* __restrict__ w, double2* __restrict__ Vout, int64_t ldvo) {
+template <typename R>
+__global__ void k_eig_sort(int64_t n, const cplx<R>* __restrict__ A, int64_t lda, const cplx<R>* __restrict__ Vin,
+                           int64_t ldvi, R* __restrict__ w, cplx<R>* __restrict__ Vout, int64_t ldvo) {
   const int64_t i = blockIdx.x;
   __shared__ int64_t rank;
-  const double wi = A[i + i * lda].x;
+  const R wi = A[i + i * lda].x;
   if (threadIdx.x == 0) rank = 0;
   __syncthreads();
   int64_t cnt = 0;
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-    const double wj = A[j + j * lda].x;
+    const R wj = A[j + j * lda].x;
     if (wj < wi || (wj == wi && j < i)) ++cnt;
   }
   atomicAdd((unsigned long long*)&rank, (unsigned long long)cnt);
@@ -412,7 +402,218 @@ __global__ void k_eig_sort(int64_t n, const double2* __restrict__ A, int64_t lda
   for (int64_t k = threadIdx.x; k < n; k += blockDim.x) Vout[k + r * ldvo] = Vin[k + i * ldvi];
 }
 
+template <typename C> __global__ void k_identity_t(int64_t n, C* A, int64_t lda) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  A[i + j * lda] = cmake<C>(i == j ? 1.0 : 0.0, 0.0);
+}
+template <typename R> void set_identity_t(int64_t n, cplx<R>* A, int64_t lda, cudaStream_t st) {
+  CHEBFI_LAUNCH("k_identity", st, k_identity_t<cplx<R>><<<nblk(n * n), 256, 0, st>>>(n, A, lda));
+}
+
+template <typename R>
+void jacobi_eigh_t(int64_t n0, cplx<R>* A, int64_t lda, R* w, cplx<R>* V, int64_t ldv, int* status, cudaStream_t st,
+                   DevBuf<double2>* ws, double tol_conv, double tol_stall, bool report) {
+  using C = cplx<R>;
+  if (n0 <= 0) return;
+  const int64_t n = n0 + (n0 & 1);  // a padding player never paired for real
+  // workspace (in double2 units): rotations, pair list, norm partials, barrier, a copy of V
+  constexpr int kParts = 256;
+  const size_t rot_c = (size_t)(n / 2) * sizeof(RotT<R>) / sizeof(double2) + 1;
+  const size_t pair_c = (size_t)n * sizeof(int) / sizeof(double2) + 1;
+  const size_t part_c = kParts + 2;
+  const size_t vtmp = ((size_t)n0 * n0 * sizeof(C) + sizeof(double2) - 1) / sizeof(double2);
+  ws->alloc(rot_c + pair_c + part_c + 1 + vtmp);
+  RotT<R>* rot = reinterpret_cast<RotT<R>*>(ws->p);
+  int* pairs = reinterpret_cast<int*>(ws->p + rot_c);
+  double* part = reinterpret_cast<double*>(ws->p + rot_c + pair_c);
+  double* nrm = part + 2 * kParts;
+  unsigned* bar = reinterpret_cast<unsigned*>(ws->p + rot_c + pair_c + part_c);
+  C* Vtmp = reinterpret_cast<C*>(ws->p + rot_c + pair_c + part_c + 1);
+  if (n0 == 1) {
+    set_identity_t<R>(1, Vtmp, 1, st);
+    CHEBFI_LAUNCH("k_eig_sort", st, k_eig_sort<R><<<1, 32, 0, st>>>(1, A, lda, Vtmp, 1, w, V, ldv));
+    return;
+  }
+  CHEBFI_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  // one cooperative launch per sweep when the device allows it (all blocks resident)
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  CHEBFI_CUDA(cudaGetDevice(&dev));
+  CHEBFI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  CHEBFI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CHEBFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_sweep<R>, 256, 0));
+  const int coop_blocks = std::min(sms * std::min(per_sm, 4), 1024);
+  set_identity_t<R>(n0, Vtmp, n0, st);
+  const int max_sweeps = 40;
+  const unsigned parts = (unsigned)std::min<int64_t>(kParts, std::max<int64_t>(1, n0 * n0 / 4096));
+  double prev_off = INFINITY;
+  bool done = false;
+  for (int sweep = 0; sweep <= max_sweeps && !done; ++sweep) {
+    CHEBFI_LAUNCH("k_offnorm", st, k_offnorm_part<R><<<parts, 256, 0, st>>>(n0, A, lda, part));
+    CHEBFI_LAUNCH("k_offnorm", st, k_offnorm_sum<<<1, 32, 0, st>>>((int)parts, part, nrm));
+    double hn[2];
+    CHEBFI_CUDA(cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+    const double off = std::sqrt(hn[0]), tot = std::sqrt(hn[1]);
+    // converged: off-diagonal at the rounding level, or no longer decreasing near it
+    if (off <= tol_conv * tot || off == 0.0 || (sweep > 2 && off > 0.5 * prev_off && off <= tol_stall * tot)) {
+      done = true;
+      break;
+    }
+    if (sweep == max_sweeps) break;
+    prev_off = off;
+    if (coop && coop_blocks > 0) {
+      int64_t n0a = n0, na = n, ldaa = lda, ldva = n0;
+      C* Aa = A;
+      C* Va = Vtmp;
+      void* args[] = {&n0a, &na, &Aa, &ldaa, &Va, &ldva, &rot, &pairs, &bar, &status};
+      CHEBFI_LAUNCH("k_jac_sweep", st,
+                    CHEBFI_CUDA(cudaLaunchCooperativeKernel((const void*)k_jac_sweep<R>, dim3(coop_blocks), dim3(256),
+                                                            args, 0, st)));
+    } else {
+      for (int64_t round = 0; round < n - 1; ++round) {
+        CHEBFI_LAUNCH("k_jac_params", st,
+                      k_jac_params<R><<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs));
+        const int64_t h = n / 2;
+        CHEBFI_LAUNCH("k_jac_apply", st,
+                      k_jac_apply<R><<<nblk(h * h + n0 * h), 256, 0, st>>>(h, n0, A, lda, Vtmp, n0, rot, pairs));
+      }
+    }
+  }
+  if (!done && report) {
+    int code = CHEBFI_ERR_NO_CONVERGENCE;
+    // record on the device flag as well so chebfi_sync_status sees it
+    CHEBFI_CUDA(cudaMemcpyAsync(status, &code, sizeof(int), cudaMemcpyHostToDevice, st));
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+  }
+  CHEBFI_LAUNCH("k_eig_sort", st, k_eig_sort<R><<<(unsigned)n0, 128, 0, st>>>(n0, A, lda, Vtmp, n0, w, V, ldv));
+}
+
+
+// ------------------------------------------------------------------ refinement of eigenvectors
+// One step of the iterative refinement of Ogita & Aishima (2018) for a Hermitian A and
+// approximate eigenvectors X, from G = X^H X (= I - R) and S = X^H A X:
+//   lambda_i = S_ii / G_ii,
+//   E_ij = (S_ij - lambda_j G_ij) / (lambda_j - lambda_i)   (i != j; = (s_ij + lambda_j r_ij)/(...)),
+//   E_ii = (1 - G_ii) / 2,
+// and X <- X (I + E).  A pair whose gap is not large against its numerator (|gap| <=
+// 4 |num|, or below 1e-13 |A|) is treated as a cluster: E_ij = -G_ij / 2 only restores
+// orthogonality, and the pair is listed for a final dense solve of the cluster.
+__global__ void k_oa_lambda(int64_t n, const double2* __restrict__ G, int64_t ldg, const double2* __restrict__ S,
+                            int64_t lds, double* __restrict__ lam, unsigned long long* __restrict__ amax) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l = S[i + i * lds].x / G[i + i * ldg].x;
+  lam[i] = l;
+  atomicMax(amax, (unsigned long long)__double_as_longlong(fabs(l)));
+}
+
+__global__ void k_oa_update(int64_t n, const double2* __restrict__ G, int64_t ldg, const double2* __restrict__ S,
+                            int64_t lds, const double* __restrict__ lam, const unsigned long long* __restrict__ amax,
+                            double2* __restrict__ M, int64_t ldm, unsigned long long* __restrict__ emax,
+                            int* __restrict__ npairs, int2* __restrict__ pairs, int cap) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  const double2 g = G[i + j * ldg];
+  double2 e;
+  double mag;
+  if (i == j) {
+    e = make_double2(0.5 * (1.0 - g.x), 0.0);
+    mag = fabs(e.x);
+  } else {
+    const double2 s = S[i + j * lds];
+    const double lj = lam[j], gap = lj - lam[i];
+    const double2 num = make_double2(s.x - lj * g.x, s.y - lj * g.y);
+    const double anum = hypot(num.x, num.y);
+    const double tiny = 1e-13 * __longlong_as_double((long long)*amax);
+    if (fabs(gap) > 4.0 * anum && fabs(gap) > tiny) {
+      e = make_double2(num.x / gap, num.y / gap);
+    } else {
+      e = make_double2(-0.5 * g.x, -0.5 * g.y);
+      if (i < j) {
+        const int k = atomicAdd(npairs, 1);
+        if (k < cap) pairs[k] = make_int2((int)i, (int)j);
+      }
+    }
+    mag = hypot(e.x, e.y);
+  }
+  atomicMax(emax, (unsigned long long)__double_as_longlong(mag));
+  M[i + j * ldm] = make_double2((i == j ? 1.0 : 0.0) + e.x, e.y);
+}
+
+// ascending order of w (stable), columns of X permuted alike
+__global__ void k_sort_pairs(int64_t n, const double* __restrict__ win, const double2* __restrict__ Xin, int64_t ldi,
+                             double* __restrict__ wout, double2* __restrict__ Xout, int64_t ldo) {
+  const int64_t i = blockIdx.x;
+  __shared__ unsigned long long rank;
+  const double wi = win[i];
+  if (threadIdx.x == 0) rank = 0;
+  __syncthreads();
+  unsigned long long cnt = 0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double wj = win[j];
+    if (wj < wi || (wj == wi && j < i)) ++cnt;
+  }
+  atomicAdd(&rank, cnt);
+  __syncthreads();
+  const int64_t r = (int64_t)rank;
+  if (threadIdx.x == 0) wout[r] = wi;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) Xout[k + r * ldo] = Xin[k + i * ldi];
+}
+
+// sub[a, b] = A[idx[a], idx[b]] (k x k); cols: sub[:, b] = X[:, idx[b]] or the reverse
+__global__ void k_gather_sub(int k, const int* __restrict__ idx, const double2* __restrict__ A, int64_t lda,
+                             double2* __restrict__ sub) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  const int a = e % k, b = e / k;
+  sub[e] = A[idx[a] + (int64_t)idx[b] * lda];
+}
+__global__ void k_cols(int64_t m, int k, const int* __restrict__ idx, double2* X, int64_t ldx, double2* Y,
+                       int64_t ldy, int to_y) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * k) return;
+  const int64_t r = e % m;
+  const int b = (int)(e / m);
+  if (to_y) Y[r + b * ldy] = X[r + idx[b] * ldx];
+  else X[r + idx[b] * ldx] = Y[r + b * ldy];
+}
+__global__ void k_scatter_vals(int k, const int* __restrict__ idx, const double* __restrict__ src, double* dst) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < k) dst[idx[b]] = src[b];
+}
+
 }  // namespace
+
+void oa_step(int64_t n, const double2* G, const double2* S, double* lam, double2* M, unsigned long long* stats,
+             int* npairs, int2* pairs, int cap, cudaStream_t st) {
+  CHEBFI_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), st));
+  CHEBFI_CUDA(cudaMemsetAsync(npairs, 0, sizeof(int), st));
+  CHEBFI_LAUNCH("k_oa_lambda", st, k_oa_lambda<<<nblk(n), 256, 0, st>>>(n, G, n, S, n, lam, stats));
+  CHEBFI_LAUNCH("k_oa_update", st,
+                k_oa_update<<<nblk(n * n), 256, 0, st>>>(n, G, n, S, n, lam, stats, M, n, stats + 1, npairs, pairs, cap));
+}
+
+void sort_eigpairs(int64_t n, const double* win, const double2* Xin, double* wout, double2* Xout, cudaStream_t st) {
+  CHEBFI_LAUNCH("k_sort_pairs", st, k_sort_pairs<<<(unsigned)n, 128, 0, st>>>(n, win, Xin, n, wout, Xout, n));
+}
+
+void gather_sub(int k, const int* idx, const double2* A, int64_t lda, double2* sub, cudaStream_t st) {
+  CHEBFI_LAUNCH("k_gather_sub", st, k_gather_sub<<<nblk((int64_t)k * k), 256, 0, st>>>(k, idx, A, lda, sub));
+}
+void gather_cols(int64_t m, int k, const int* idx, const double2* X, int64_t ldx, double2* Y, int64_t ldy,
+                 cudaStream_t st) {
+  CHEBFI_LAUNCH("k_cols", st, k_cols<<<nblk(m * k), 256, 0, st>>>(m, k, idx, const_cast<double2*>(X), ldx, Y, ldy, 1));
+}
+void scatter_cols(int64_t m, int k, const int* idx, double2* X, int64_t ldx, const double2* Y, int64_t ldy,
+                  cudaStream_t st) {
+  CHEBFI_LAUNCH("k_cols", st, k_cols<<<nblk(m * k), 256, 0, st>>>(m, k, idx, X, ldx, const_cast<double2*>(Y), ldy, 0));
+}
+void scatter_vals(int k, const int* idx, const double* src, double* dst, cudaStream_t st) {
+  CHEBFI_LAUNCH("k_scatter_vals", st, k_scatter_vals<<<nblk(k), 256, 0, st>>>(k, idx, src, dst));
+}
 
 void cholesky(int64_t n, double2* A, int64_t lda, int* status, cudaStream_t st, DevBuf<double2>* ws) {
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
@@ -443,72 +644,13 @@ void trsm_lower(int64_t n, int64_t m, const double2* L, int64_t ldl, double2* B,
 
 void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int64_t ldv, int* status, cudaStream_t st,
                  DevBuf<double2>* ws) {
-  if (n0 <= 0) return;
-  if (n0 == 1) {
-    set_identity(1, V, ldv, st);
-    diag_of(1, A, lda, w, st);
-    return;
-  }
-  const int64_t n = n0 + (n0 & 1);  // a padding player never paired for real
-  // workspace: rotations, pair list, norms, and a copy of V for the final sort
-  const size_t rot_c = (size_t)(n / 2) * sizeof(Rot) / sizeof(double2) + 1;
-  const size_t pair_c = (size_t)n * sizeof(int) / sizeof(double2) + 1;
-  const size_t vtmp = (size_t)n0 * n0;
-  ws->alloc(rot_c + pair_c + 3 + vtmp);
-  Rot* rot = reinterpret_cast<Rot*>(ws->p);
-  int* pairs = reinterpret_cast<int*>(ws->p + rot_c);
-  double* nrm = reinterpret_cast<double*>(ws->p + rot_c + pair_c);
-  unsigned* bar = reinterpret_cast<unsigned*>(ws->p + rot_c + pair_c + 2);
-  double2* Vtmp = ws->p + rot_c + pair_c + 3;
-  CHEBFI_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
-  // one cooperative launch per sweep when the device allows it (all blocks resident)
-  int dev = 0, coop = 0, sms = 0, per_sm = 0;
-  CHEBFI_CUDA(cudaGetDevice(&dev));
-  CHEBFI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  CHEBFI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CHEBFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_sweep, 256, 0));
-  const int coop_blocks = std::min(sms * std::min(per_sm, 4), 1024);
-  set_identity(n0, Vtmp, n0, st);
-  const int max_sweeps = 40;
-  double prev_off = INFINITY;
-  bool done = false;
-  for (int sweep = 0; sweep <= max_sweeps && !done; ++sweep) {
-    CHEBFI_LAUNCH("k_offnorm", st, k_offnorm<<<1, 256, 0, st>>>(n0, A, lda, nrm));
-    double h[2];
-    CHEBFI_CUDA(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st));
-    CHEBFI_CUDA(cudaStreamSynchronize(st));
-    const double off = std::sqrt(h[0]), tot = std::sqrt(h[1]);
-    // converged: off-diagonal at the rounding level, or no longer decreasing
-    if (off <= 1e-15 * tot || off == 0.0 || (sweep > 2 && off > 0.5 * prev_off && off <= 1e-12 * tot)) {
-      done = true;
-      break;
-    }
-    if (sweep == max_sweeps) break;
-    prev_off = off;
-    if (coop && coop_blocks > 0) {
-      int64_t n0a = n0, na = n, ldaa = lda, ldva = n0;
-      double2* Aa = A;
-      double2* Va = Vtmp;
-      void* args[] = {&n0a, &na, &Aa, &ldaa, &Va, &ldva, &rot, &pairs, &bar, &status};
-      CHEBFI_LAUNCH("k_jac_sweep", st,
-                    CHEBFI_CUDA(cudaLaunchCooperativeKernel((const void*)k_jac_sweep, dim3(coop_blocks), dim3(256), args,
-                                                            0, st)));
-    } else {
-      for (int64_t round = 0; round < n - 1; ++round) {
-        CHEBFI_LAUNCH("k_jac_params", st, k_jac_params<<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs));
-        const int64_t h = n / 2;
-        CHEBFI_LAUNCH("k_jac_apply", st,
-                      k_jac_apply<<<nblk(h * h + n0 * h), 256, 0, st>>>(h, n0, A, lda, Vtmp, n0, rot, pairs));
-      }
-    }
-  }
-  if (!done) {
-    int code = CHEBFI_ERR_NO_CONVERGENCE;
-    // record on the device flag as well so chebfi_sync_status sees it
-    CHEBFI_CUDA(cudaMemcpyAsync(status, &code, sizeof(int), cudaMemcpyHostToDevice, st));
-    CHEBFI_CUDA(cudaStreamSynchronize(st));
-  }
-  CHEBFI_LAUNCH("k_eig_sort", st, k_eig_sort<<<(unsigned)n0, 128, 0, st>>>(n0, A, lda, Vtmp, n0, w, V, ldv));
+  jacobi_eigh_t<double>(n0, A, lda, w, V, ldv, status, st, ws, 1e-15, 1e-12, true);
+}
+
+void jacobi_eigh_f32(int64_t n0, float2* A, int64_t lda, float* w, float2* V, int64_t ldv, int* status,
+                     cudaStream_t st, DevBuf<double2>* ws) {
+  // a first stage only: stop at the FP32 rounding level and never report a sweep limit
+  jacobi_eigh_t<float>(n0, A, lda, w, V, ldv, status, st, ws, 4e-7, 1e-5, false);
 }
 
 }  // namespace chebfi

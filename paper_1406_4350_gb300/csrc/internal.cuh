@@ -189,6 +189,14 @@ struct Work {
   DevBuf<double2> pa, pb, pc, pz, pw, pq, pt;             // nproj x nb projections (FP64)
   DevBuf<float2> fpa, fpb, fpz, fpw, fpq, fpt;            // FP32 projections
   DevBuf<double2> small1, small2, small3, small4, small5;  // nb x nb
+  // refined eigensolver: FP32 first stage, FP64 refinement matrices, stats, cluster pairs
+  DevBuf<float2> e32a, e32b;
+  DevBuf<float> e32w;
+  DevBuf<double2> eG, eS, eAX, eM, eX, esub, eZ, eC1, eC2;
+  DevBuf<double> elam, esw;
+  DevBuf<unsigned long long> estats;
+  DevBuf<int> enp, eidx;
+  DevBuf<int2> epairs;
   DevBuf<double> dvec1, dvec2, dvec3;
   DevBuf<double2> splitk;
   DevBuf<float2> fsplitk;
@@ -274,6 +282,8 @@ struct chebfi_ctx {
   // FP64 complex GEMMs: engine choice (chebfi_set_fp64_gemm), modulus count of the
   // tensor-core emulation, its workspace, and the residues of P^H and P (built on first use)
   int fp64_gemm = CHEBFI_GEMM_AUTO;
+  int eig_mode = CHEBFI_EIG_AUTO;  // dense eigensolver of Rayleigh-Ritz (chebfi_set_eigensolver)
+  int eig_iters = 0;               // refinement steps of its last call (0: FP64 Jacobi ran)
   int oz_nmod = 14;
   chebfi::OzWork oz;
   chebfi::OzOperand ozPh, ozP;

@@ -154,5 +154,24 @@ void trsm_lower(int64_t n, int64_t m, const double2* L, int64_t ldl, double2* B,
 // CHEBFI_ERR_NO_CONVERGENCE on the sweep limit.  Synchronises the stream (sweep test).
 void jacobi_eigh(int64_t n, double2* A, int64_t lda, double* w, double2* V, int64_t ldv, int* status,
                  cudaStream_t st, DevBuf<double2>* ws);
+// The same in FP32, stopping at the FP32 rounding level (first stage of the refined solver;
+// never reports a sweep limit).  ws holds its rotations, pair list and a copy of V.
+void jacobi_eigh_f32(int64_t n, float2* A, int64_t lda, float* w, float2* V, int64_t ldv, int* status,
+                     cudaStream_t st, DevBuf<double2>* ws);
+// One Ogita-Aishima refinement step (n x n, lda = n): from G = X^H X and S = X^H A X, the
+// approximate eigenvalues lam and M = I + E with X (I + E) the refined vectors; stats[0] =
+// max |lam| bits, stats[1] = max |E| bits (doubles as ordered integers); pairs whose gap is
+// too small for the formula are listed (i < j, at most cap) and only orthogonalised.
+void oa_step(int64_t n, const double2* G, const double2* S, double* lam, double2* M, unsigned long long* stats,
+             int* npairs, int2* pairs, int cap, cudaStream_t st);
+// (w, X) sorted ascending in w (stable): wout, Xout (n x n, ld n)
+void sort_eigpairs(int64_t n, const double* win, const double2* Xin, double* wout, double2* Xout, cudaStream_t st);
+// index-list gathers: sub = A[idx, idx] (k x k); Y = X[:, idx]; X[:, idx] = Y; dst[idx] = src
+void gather_sub(int k, const int* idx, const double2* A, int64_t lda, double2* sub, cudaStream_t st);
+void gather_cols(int64_t m, int k, const int* idx, const double2* X, int64_t ldx, double2* Y, int64_t ldy,
+                 cudaStream_t st);
+void scatter_cols(int64_t m, int k, const int* idx, double2* X, int64_t ldx, const double2* Y, int64_t ldy,
+                  cudaStream_t st);
+void scatter_vals(int k, const int* idx, const double* src, double* dst, cudaStream_t st);
 
 }  // namespace chebfi
