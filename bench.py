@@ -298,6 +298,57 @@ def run_extra(args):
                 "gpu_launches_per_call": launches, "autotuned_shapes": shapes, "split_k_PhY": split,
                 "autotune_ms": tune.round(4).tolist(), "split_ms": split_ms.round(4).tolist(),
                 "clocks": clk.summary()}
+    elif args.task == "gate":
+        # Accuracy gate at the benchmark workload: Algorithm 2 from the same start in the
+        # FP64 form until the residual certificate holds for the lowest 75 % of the bands,
+        # then the mixed form for the same sweeps; their Ritz values are compared.
+        from paper_1406_4350_gb300 import MIXED
+        cell = config_cell(WORKLOAD)
+        nb = cell.nbands
+        k75 = (3 * nb) // 4
+        g = ChebFI.from_cell(cell)
+        hi = g.upper_bound(BOUND_RIGOROUS)
+        smin = g.overlap_lower_bound()
+
+        def run(prec, sweeps_max, certify):
+            Y = fortran(cell.Y0)
+            lo = float(g.rayleigh_quotients(Y).max().item())
+            hist = []
+            ev = rs = None
+            t0 = time.perf_counter()
+            for s_ in range(sweeps_max):
+                g.cheb_filter(Y, DEGREE, lo, hi, prec=prec)
+                ev, rs = g.rayleigh_ritz(Y)
+                lo = float(ev.max().item())
+                cert = float(rs[:k75].max().item()) / np.sqrt(smin)
+                hist.append(cert)
+                if certify and cert <= 1e-8:
+                    break
+            torch.cuda.synchronize()
+            return ev.cpu().numpy(), rs.cpu().numpy(), len(hist), hist, time.perf_counter() - t0
+
+        ev64, rs64, n64, h64, t64 = run(F64, args.gate_sweeps, True)
+        certified = h64[-1] <= 1e-8
+        evmx, rsmx, nmx, hmx, tmx = run(MIXED, n64, False)
+        diff = np.abs(evmx[:k75] - ev64[:k75])
+        line = {"metric": "config-3 accuracy gate: max |lambda_mixed - lambda_FP64| over the lowest 75% of bands",
+                "unit": "Ha", "value": float(diff.max()), "dtype": "f64 / bf16x3+f32",
+                "config": {"workload": "paw96: 96^3 grid, %d plane waves, %d bands, %d projectors, PAW, degree %d, "
+                                       "Algorithm 2 from the seeded start, lambda_+ rigorous %.4f Ha"
+                                       % (cell.npw, nb, cell.nproj, DEGREE, hi)},
+                "fp64": {"sweeps": n64, "certified": bool(certified),
+                         "certificate_Ha": h64[-1],
+                         "certificate": "max over the lowest %d bands of ||H y - theta S y||_2 / sqrt(smin), "
+                                        "smin = %.6f a proven lower bound of lambda_min(S): every such Ritz value "
+                                        "is within it of an eigenvalue of the pencil" % (k75, smin),
+                         "max_residual_lowest_75pct": float(rs64[:k75].max()),
+                         "max_residual_all": float(rs64.max()), "lambda_min": float(ev64[0]),
+                         "lambda_k75": float(ev64[k75 - 1]), "s": t64, "history": h64},
+                "mixed": {"sweeps": nmx, "max_residual_lowest_75pct": float(rsmx[:k75].max()),
+                          "max_abs_diff_lowest_75pct_Ha": float(diff.max()),
+                          "mean_abs_diff_lowest_75pct_Ha": float(diff.mean()),
+                          "max_abs_diff_all_Ha": float(np.abs(evmx - ev64).max()), "s": tmx, "history": hmx},
+                "passed": bool(certified and diff.max() <= 1e-8)}
     else:
         cell = config_cell(WORKLOAD, nbands=256)
         g = ChebFI.from_cell(cell)
@@ -331,7 +382,8 @@ def main():
     ap.add_argument("--ref-bands", type=int, default=4)
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
-    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking"],
+    ap.add_argument("--gate-sweeps", type=int, default=120, help="gate: most FP64 sweeps before giving up")
+    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking", "gate"],
                     help="filter: the benchmark; backward / refine: the differentiation and the "
                          "refinement-Woodbury measurements (their own JSON line)")
     args = ap.parse_args()

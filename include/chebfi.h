@@ -62,7 +62,8 @@ enum {
   CHEBFI_ERR_NOT_SPD = -4,        /* Cholesky met a non-positive pivot (Gram or S) */
   CHEBFI_ERR_NO_CONVERGENCE = -5, /* the Jacobi eigensolver hit its sweep limit */
   CHEBFI_ERR_FILTER_OVERFLOW = -6,/* T_degree((lambda_1-c)/r) too large for the precision */
-  CHEBFI_ERR_NOMEM = -7           /* device allocation failed */
+  CHEBFI_ERR_NOMEM = -7,          /* device allocation failed */
+  CHEBFI_ERR_NONFINITE = -8       /* Inf or NaN in an input or in a block entering Rayleigh-Ritz */
 };
 
 typedef struct {
@@ -112,6 +113,11 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
 
 /* Section 5.3: lambda_+ for the filter.  Synchronises. */
 int chebfi_upper_bound(chebfi_ctx* ctx, int mode, double* lambda_hi);
+/* A proven lower bound of the smallest eigenvalue of S: 1 + min(0, l_min(L^H Q L)) with
+ * P^H P = L L^H (1 for S = I).  With it a Ritz pair (theta, y), y S-normalised, certifies
+ * an eigenvalue of the pencil within ||H y - theta S y||_2 / sqrt(smin) of theta (the
+ * residual in the S^{-1} norm bounds the distance).  Synchronises. */
+int chebfi_overlap_lower_bound(chebfi_ctx* ctx, double* smin);
 
 /* Algorithm 1: HY = H Y for nb bands.  prec selects FP64 or FP32 arithmetic (MIXED acts
  * as F32 here).  Y and HY must not overlap. */
@@ -212,7 +218,7 @@ int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void
 /* Algorithm 2's last three steps (FP64): columns scaled to unit S-norm, H_Psi = Y^H H Y,
  * S_Psi = Y^H S Y, H_Psi X = S_Psi X Lambda (Cholesky reduction + Jacobi), Y <- Y X.
  * evals: device, nb doubles, ascending.  resid: device, nb doubles ||H y - lambda S y||_2,
- * or NULL.  Synchronises. */
+ * or NULL.  Synchronises.  A block holding Inf or NaN is reported as CHEBFI_ERR_NONFINITE. */
 int chebfi_rayleigh_ritz(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb,
                          int64_t ld, void* stream);
 
@@ -227,7 +233,8 @@ int chebfi_rayleigh_quotients(chebfi_ctx* ctx, const void* Y, double* rq, int64_
  * params->degree for every band and each later sweep gives band i the degree
  * chebfi_adaptive_degrees predicts for params->tol from its Ritz value and residual (at
  * most params->degree; 0 = locked, not filtered, still in the Rayleigh-Ritz space); the
- * solve stops early when every band is locked.  Synchronises. */
+ * solve stops early when every band is locked.  Synchronises.  Every sweep checks the block
+ * entering Rayleigh-Ritz and the Ritz values for Inf / NaN (CHEBFI_ERR_NONFINITE). */
 int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb, int64_t ld,
                  const chebfi_params* params, void* stream);
 
@@ -293,6 +300,17 @@ enum { CHEBFI_EIG_AUTO = 0, CHEBFI_EIG_JACOBI = 1, CHEBFI_EIG_REFINED = 2 };
 int chebfi_set_eigensolver(chebfi_ctx* ctx, int mode);
 /* Refinement steps taken by the last dense eigensolve on ctx (0: FP64 Jacobi ran). */
 int chebfi_eigensolver_steps(const chebfi_ctx* ctx);
+
+/* Self-test of the bounded device waits (a library diagnostic; the paper has no counterpart).
+ * Every spin of the library's kernels -- the grid barrier of the cooperative Jacobi sweep,
+ * the mbarrier waits of the tensor-core pipelines -- gives up after a time limit, records
+ * CHEBFI_ERR_CUDA on the device and lets the kernel end.  which = 0 runs the grid barrier
+ * with one block that never arrives, which = 1 an mbarrier wait for an arrival nobody makes,
+ * each with a limit of limit_ms (0 < limit_ms <= 2000).  *recorded (nullable) receives the
+ * code the waiting threads recorded (CHEBFI_ERR_CUDA when the wait ran out), *elapsed_ms
+ * (nullable) the kernel's duration.  Uses its own status word, not the context's.
+ * Synchronises. */
+int chebfi_selftest_bounded_wait(chebfi_ctx* ctx, int which, double limit_ms, int* recorded, double* elapsed_ms);
 
 /* Synchronise the context's work and return the first device-detected error, if any. */
 int chebfi_sync_status(chebfi_ctx* ctx);

@@ -14,8 +14,8 @@ P_double = ctypes.POINTER(ctypes.c_double)
 P_int = ctypes.POINTER(ctypes.c_int)
 
 # error codes (chebfi.h)
-OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_FILTER_OVERFLOW, ERR_NOMEM = \
-    0, -1, -2, -3, -4, -5, -6, -7
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_FILTER_OVERFLOW, ERR_NOMEM, ERR_NONFINITE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
 F64, F32, MIXED = 0, 1, 2
 GEMM_AUTO, GEMM_CUDA_CORES, GEMM_TENSOR = 0, 1, 2
 EIG_AUTO, EIG_JACOBI, EIG_REFINED = 0, 1, 2
@@ -37,6 +37,7 @@ SIGNATURES = {
     "chebfi_set_projectors": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int, c_int, P_int32,
                                       P_double, P_double]),
     "chebfi_upper_bound": (c_int, [c_void_p, c_int, P_double]),
+    "chebfi_overlap_lower_bound": (c_int, [c_void_p, P_double]),
     "chebfi_apply_H": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p]),
     "chebfi_apply_H_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_set_D": (c_int, [c_void_p, c_void_p, c_int]),
@@ -74,6 +75,7 @@ SIGNATURES = {
                                  c_void_p, c_int64, c_double, c_void_p, c_int64, c_void_p]),
     "chebfi_set_eigensolver": (c_int, [c_void_p, c_int]),
     "chebfi_eigensolver_steps": (c_int, [c_void_p]),
+    "chebfi_selftest_bounded_wait": (c_int, [c_void_p, c_int, c_double, P_int, P_double]),
     "chebfi_sync_status": (c_int, [c_void_p]),
     "chebfi_kernel_launches": (c_int64, [c_void_p]),
     "chebfi_profile_enable": (c_int, [c_void_p, c_int]),

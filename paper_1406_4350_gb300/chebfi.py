@@ -145,6 +145,12 @@ class ChebFI:
         self._check(self.lib.chebfi_upper_bound(self.h, mode, ctypes.byref(out)))
         return out.value
 
+    def overlap_lower_bound(self) -> float:
+        """Proven lower bound of the smallest eigenvalue of S (1 for S = I)."""
+        out = ctypes.c_double()
+        self._check(self.lib.chebfi_overlap_lower_bound(self.h, ctypes.byref(out)))
+        return out.value
+
     # -- operators -------------------------------------------------------------------
     def _out_like(self, Y):
         return torch.empty((Y.shape[1], Y.shape[0]), dtype=torch.complex128, device=Y.device).T
@@ -284,6 +290,15 @@ class ChebFI:
         e = ctypes.c_int(0)
         self._check(self.lib.chebfi_set_fp64_gemm(self.h, engine, nmod, ctypes.byref(e)))
         return e.value
+
+    def selftest_bounded_wait(self, which: int, limit_ms: float):
+        """Run a wait that nothing satisfies (0: grid barrier, 1: mbarrier); returns (code the
+        kernel recorded, elapsed ms)."""
+        code = ctypes.c_int(0)
+        ms = ctypes.c_double(0.0)
+        self._check(self.lib.chebfi_selftest_bounded_wait(self.h, which, limit_ms, ctypes.byref(code),
+                                                          ctypes.byref(ms)))
+        return code.value, ms.value
 
     def set_eigensolver(self, mode: int):
         """Dense eigensolver of Rayleigh-Ritz: EIG_AUTO, EIG_JACOBI (FP64) or EIG_REFINED (FP32

@@ -121,6 +121,7 @@ void check_status(chebfi_ctx* ctx, cudaStream_t st, const char* where) {
     int zero = 0;
     CHEBFI_CUDA(cudaMemcpy(ctx->d_status.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
     const char* what = h == CHEBFI_ERR_NOT_SPD ? "matrix not positive definite"
+                       : h == CHEBFI_ERR_NONFINITE ? "Inf or NaN in the block or matrix"
                        : h == CHEBFI_ERR_NO_CONVERGENCE ? "Jacobi eigensolver did not converge"
                                                          : "device error";
     throw Error{h, std::string(where) + ": " + what};
@@ -521,6 +522,7 @@ void eigh_rr(chebfi_ctx* ctx, int64_t n, double2* A, double* w, double2* X, cuda
     jacobi_eigh(n, A, n, w, X, n, status, st, &wk.small5);
     return;
   }
+  check_status(ctx, st, "rayleigh_ritz");  // a non-finite block was flagged before the Gram matrices
   const size_t nn = (size_t)n * n;
   constexpr int kCap = 1 << 16;
   wk.e32a.alloc(nn);
@@ -632,6 +634,7 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   w.dvec1.alloc(nb);
   double2* Y = w.Ya.p;
   DevBuf<double2>* ws = &w.splitk;
+  scan_nonfinite(npw, nb, Y, npw, ctx->d_status.p, st);  // first flag wins: reported before any NOT_SPD
   // H Y and p = P^H Y
   apply_H_sorted<double>(ctx, Y, w.HY.p, w.pa.p, w.pb.p, w.T1.p, nb, st, "gemm_rr");
   double2 *Hs = w.small1.p, *Ss = w.small2.p, *Li = w.small3.p, *X = w.small4.p;
@@ -690,6 +693,7 @@ void ortho_on_Ya(chebfi_ctx* ctx, int64_t nb, cudaStream_t st) {
   w.small3.alloc(ns);
   DevBuf<double2>* ws = &w.splitk;
   double2 *Ss = w.small2.p, *Li = w.small3.p, *Y = w.Ya.p;
+  scan_nonfinite(npw, nb, Y, npw, ctx->d_status.p, st);
   gemm64(ctx, true, false, nb, nb, npw, 1.0, Y, npw, Y, npw, 0.0, Ss, nb, st, ws);
   if (ctx->paw) {
     gemm64(ctx, true, false, nq, nb, npw, 1.0, ctx->d_P.p, npw, Y, npw, 0.0, w.pa.p, nq, st, ws);
@@ -747,7 +751,10 @@ double host_max(chebfi_ctx* ctx, const double* d, int64_t n, cudaStream_t st, bo
   CHEBFI_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   CHEBFI_CUDA(cudaStreamSynchronize(st));
   double m = minimum ? INFINITY : -INFINITY;
-  for (double v : h) m = minimum ? std::min(m, v) : std::max(m, v);
+  for (double v : h) {
+    if (std::isnan(v)) return v;  // a NaN must not hide behind the comparisons
+    m = minimum ? std::min(m, v) : std::max(m, v);
+  }
   return m;
 }
 
@@ -780,6 +787,7 @@ double rigorous_bound(chebfi_ctx* ctx) {
     }
   }
   ctx->bound_rigorous = std::max(0.0, num) / smin;
+  ctx->smin = smin;
   return ctx->bound_rigorous;
 }
 
@@ -1239,7 +1247,7 @@ int chebfi_set_vloc(chebfi_ctx* ctx, const double* vloc, int on_device) {
     for (int y = 0; y < n2; ++y)
       for (int z = 0; z < n3; ++z) {
         const double v = h[((size_t)x * n2 + y) * n3 + z];
-        CHEBFI_REQUIRE(std::isfinite(v), CHEBFI_ERR_ARG, "V_loc is not finite");
+        CHEBFI_REQUIRE(std::isfinite(v), CHEBFI_ERR_NONFINITE, "V_loc is not finite");
         t[((size_t)z * n1 + x) * n2 + y] = v;
         tf[((size_t)z * n1 + x) * n2 + y] = (float)v;
         vmax = std::max(vmax, v);
@@ -1300,6 +1308,10 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
     nblkv += (int64_t)na * na;
     for (int i = offs[a]; i < offs[a + 1]; ++i) atom_of[i] = a;
   }
+  for (int64_t i = 0; i < nblkv; ++i) {
+    CHEBFI_REQUIRE(std::isfinite(D[i]), CHEBFI_ERR_NONFINITE, "D is not finite");
+    CHEBFI_REQUIRE(!Q || std::isfinite(Q[i]), CHEBFI_ERR_NONFINITE, "Q is not finite");
+  }
   ctx->offs = offs;
   ctx->d_offs.upload(offs.data(), offs.size());
   ctx->d_atom_of.upload(atom_of.data(), nproj);
@@ -1325,6 +1337,8 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
       for (int64_t j = 0; j < npw; ++j) h[i * npw + j] = src[i * ldP + ctx->sorted_to_user[j]];
     CHEBFI_CUDA(cudaMemcpy(ctx->d_P.p, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
   }
+  scan_nonfinite(npw, nproj, ctx->d_P.p, npw, ctx->d_status.p, st);
+  check_status(ctx, st, "set_projectors (P)");
   DevBuf<double2>* ws = &ctx->w.splitk;
   // G = P^H P (Section 5.1, precomputed once)
   ctx->d_G.alloc((size_t)nproj * nproj);
@@ -1382,6 +1396,15 @@ int chebfi_upper_bound(chebfi_ctx* ctx, int mode, double* lambda_hi) {
   if (mode == CHEBFI_BOUND_PAPER) *lambda_hi = ctx->kmax;
   else if (mode == CHEBFI_BOUND_RIGOROUS) *lambda_hi = rigorous_bound(ctx);
   else throw Error{CHEBFI_ERR_ARG, "unknown bound mode"};
+  API_END(ctx)
+}
+
+int chebfi_overlap_lower_bound(chebfi_ctx* ctx, double* smin) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  CHEBFI_REQUIRE(smin, CHEBFI_ERR_ARG, "null output");
+  rigorous_bound(ctx);
+  *smin = ctx->smin;
   API_END(ctx)
 }
 
@@ -1664,6 +1687,8 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
   rq_sorted(ctx, ctx->w.Ya.p, nb, ctx->w.dvec3.p, st);
   double lo = host_max(ctx, ctx->w.dvec3.p, nb, st);
   double l1 = host_max(ctx, ctx->w.dvec3.p, nb, st, true);
+  CHEBFI_REQUIRE(std::isfinite(lo) && std::isfinite(l1), CHEBFI_ERR_NONFINITE,
+                 "solve: Inf or NaN in the Rayleigh quotients of the starting block");
   // locking (Section 5.4): after a full-degree sweep, each band gets the degree its residual
   // estimate needs for params->tol; converged bands are not filtered
   const bool lock = params->lock != 0;
@@ -1690,6 +1715,8 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
     rr_on_Ya(ctx, nb, evals, res, st);
     lo = host_max(ctx, evals, nb, st);
     l1 = host_max(ctx, evals, nb, st, true);
+    CHEBFI_REQUIRE(std::isfinite(lo) && std::isfinite(l1), CHEBFI_ERR_NONFINITE,
+                   "solve: Inf or NaN in the Ritz values of sweep " + std::to_string(s + 1));
     if (lock) {
       std::vector<double> he(nb), hr(nb);
       CHEBFI_CUDA(cudaMemcpyAsync(he.data(), evals, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
@@ -1758,7 +1785,7 @@ int chebfi_set_D(chebfi_ctx* ctx, const double* D, int on_device) {
   std::vector<double> h(nblkv);
   if (on_device) CHEBFI_CUDA(cudaMemcpy(h.data(), D, sizeof(double) * nblkv, cudaMemcpyDeviceToHost));
   else std::memcpy(h.data(), D, sizeof(double) * nblkv);
-  for (double v : h) CHEBFI_REQUIRE(std::isfinite(v), CHEBFI_ERR_ARG, "D is not finite");
+  for (double v : h) CHEBFI_REQUIRE(std::isfinite(v), CHEBFI_ERR_NONFINITE, "D is not finite");
   ctx->d_Dblk.upload(h.data(), nblkv);
   std::vector<float> hf(h.begin(), h.end());
   ctx->d_Dblkf.upload(hf.data(), nblkv);

@@ -411,4 +411,21 @@ void reduce_max(int64_t n, const double* x, double* out, cudaStream_t st) {
   CHEBFI_LAUNCH("k_reduce_max", st, k_reduce_max<<<1, 256, 0, st>>>(n, x, out));
 }
 
+namespace {
+__global__ void k_scan_nonfinite(int64_t m, int64_t nb, const double2* __restrict__ x, int64_t ldx, int* status) {
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * nb; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[e % m + (e / m) * ldx];
+    bad |= !(isfinite(v.x) && isfinite(v.y));
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(status, 0, CHEBFI_ERR_NONFINITE);
+}
+}  // namespace
+
+void scan_nonfinite(int64_t m, int64_t nb, const double2* x, int64_t ldx, int* status, cudaStream_t st) {
+  if (m <= 0 || nb <= 0) return;
+  const int64_t blocks = std::min<int64_t>((m * nb + 255) / 256, 152 * 8);
+  CHEBFI_LAUNCH("k_scan_nonfinite", st, k_scan_nonfinite<<<(unsigned)blocks, 256, 0, st>>>(m, nb, x, ldx, status));
+}
+
 }  // namespace chebfi

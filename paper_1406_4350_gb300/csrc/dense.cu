@@ -14,6 +14,7 @@
 
 #include "internal.cuh"
 #include "kernels.cuh"
+#include "grid_barrier.cuh"
 
 namespace chebfi {
 namespace {
@@ -295,35 +296,6 @@ __global__ void k_jac_apply(int64_t h, int64_t n, cplx<R>* A, int64_t lda, cplx<
   jac_apply_item<R>(idx, h, n, A, lda, V, ldv, rot, pairs);
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks resident).  The wait is bounded:
-// after limit_ns it records CHEBFI_ERR_CUDA and lets the block go on.
-__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* status,
-                                             unsigned long long limit_ns = 1000000000ull) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned g = atomicAdd(gen, 0u);
-    __threadfence();
-    if (atomicAdd(count, 1u) == nblocks - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      unsigned long long t0, t;
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-      while (atomicAdd(gen, 0u) == g) {
-        __nanosleep(32);
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > limit_ns) {
-          flag_error(status, CHEBFI_ERR_CUDA);
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
-
 // All n-1 rounds of one Jacobi sweep in one cooperative launch: per round, the rotation
 // parameters of the n/2 pairs, a grid barrier, the one-pass update of A and V, a barrier.
 template <typename R>
@@ -456,6 +428,13 @@ void jacobi_eigh_t(int64_t n0, cplx<R>* A, int64_t lda, R* w, cplx<R>* V, int64_
     CHEBFI_CUDA(cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
     CHEBFI_CUDA(cudaStreamSynchronize(st));
     const double off = std::sqrt(hn[0]), tot = std::sqrt(hn[1]);
+    if (!std::isfinite(tot)) {  // Inf or NaN in the matrix: no sweep can help
+      int code = CHEBFI_ERR_NONFINITE;
+      CHEBFI_CUDA(cudaMemcpyAsync(status, &code, sizeof(int), cudaMemcpyHostToDevice, st));
+      CHEBFI_CUDA(cudaStreamSynchronize(st));
+      report = false;
+      break;
+    }
     // converged: off-diagonal at the rounding level, or no longer decreasing near it
     if (off <= tol_conv * tot || off == 0.0 || (sweep > 2 && off > 0.5 * prev_off && off <= tol_stall * tot)) {
       done = true;

@@ -288,6 +288,7 @@ struct chebfi_ctx {
   chebfi::OzWork oz;
   chebfi::OzOperand ozPh, ozP;
   double bound_rigorous = -1.0;
+  double smin = 1.0;  // lower bound of lambda_min(S), set with bound_rigorous
   // host-block filter: staging buffers, copy streams and their events (created on first use)
   chebfi::DevBuf<double2> stage[2];
   cudaStream_t copy_in = nullptr, copy_out = nullptr;

@@ -119,6 +119,8 @@ void column_dots(int64_t m, int64_t nb, const double2* x, int64_t ldx, const dou
 // out[b] = || h_b - w_b s_b ||_2
 void residual_norms(int64_t m, int64_t nb, const double2* h, int64_t ldh, const double2* s, int64_t lds,
                     const double* w, double* out, cudaStream_t st);
+// *status = CHEBFI_ERR_NONFINITE (unless already set) if the m x nb block holds Inf or NaN
+void scan_nonfinite(int64_t m, int64_t nb, const double2* x, int64_t ldx, int* status, cudaStream_t st);
 // out[b] = num[b] / den[b]
 void divide(int64_t n, const double* num, const double* den, double* out, cudaStream_t st);
 // identity matrix n x n
