@@ -32,7 +32,7 @@ import scipy.linalg
 from .planewave import PWOperator
 
 __all__ = [
-    "cheb_T", "filter_plain", "filter_reuse", "rayleigh_quotients", "upper_bound", "bounds",
+    "cheb_T", "filter_plain", "filter_setup", "filter_reuse", "rayleigh_quotients", "upper_bound", "bounds",
     "rayleigh_ritz", "residuals", "residual_bound", "solve", "adaptive_degrees", "filter_adaptive",
     "solve_locked",
 ]
@@ -77,8 +77,16 @@ def _woodbury_reduced(op: PWOperator):
     return Dinv + op.P.conj().T @ op.P
 
 
+def filter_setup(op: PWOperator):
+    """The quantities of Section 5.1 that depend only on P and D_S, formed once:
+    G = P^H P and the LU factors of the reduced matrix D_S^{-1} + P^H P (None for S = I)."""
+    G = op.P.conj().T @ op.P
+    lu = None if op.Ds is None else scipy.linalg.lu_factor(_woodbury_reduced(op))
+    return {"G": G, "lu": lu}
+
+
 def filter_reuse(op: PWOperator, Y, degree: int, lam_lo: float, lam_hi: float,
-                 return_proj: bool = False):
+                 return_proj: bool = False, setup=None):
     """Algorithm 2's inner loop with the projection-reuse identity of Section 5.1.
 
     For one step with current iterate psi and its carried projections p = P^H psi:
@@ -87,7 +95,8 @@ def filter_reuse(op: PWOperator, Y, degree: int, lam_lo: float, lam_hi: float,
       q      = (D_S^{-1} + G)^{-1} P^H H psi          (Woodbury reduced solve)
       S^{-1} H psi = Z + P D_V p - P q
       P^H S^{-1} H psi = P^H H psi - G q              (the identity of Section 5.1)
-    and both psi and p follow the Chebyshev recurrence.
+    and both psi and p follow the Chebyshev recurrence.  ``setup`` (from filter_setup) holds
+    G and the reduced matrix's LU factors when they are formed once for many calls.
     """
     c = 0.5 * (lam_hi + lam_lo)
     r = 0.5 * (lam_hi - lam_lo)
@@ -95,17 +104,18 @@ def filter_reuse(op: PWOperator, Y, degree: int, lam_lo: float, lam_hi: float,
     p_prev = op.projections(psi_prev)
     if degree == 0:
         return (psi_prev, p_prev) if return_proj else psi_prev
-    G = op.P.conj().T @ op.P
-    reduced = None if op.Ds is None else _woodbury_reduced(op)
+    if setup is None:
+        setup = filter_setup(op)
+    G, lu = setup["G"], setup["lu"]
 
     def sinv_h(psi, p):
         Z = op.K[:, None] * psi + op.apply_local(psi)
         Dp = op.Dv @ p
         pHpsi = op.P.conj().T @ Z + G @ Dp
-        if reduced is None:
+        if lu is None:
             q = np.zeros_like(pHpsi)
         else:
-            q = np.linalg.solve(reduced, pHpsi)
+            q = scipy.linalg.lu_solve(lu, pHpsi)
         u = Z + op.P @ (Dp - q)
         pu = pHpsi - G @ q
         return u, pu

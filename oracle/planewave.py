@@ -74,6 +74,9 @@ class PWOperator:
         self.Ds = None if Q is None else blockdiag(np.asarray(Q, dtype=np.float64), proj_offsets)
         self.offsets = np.asarray(proj_offsets)
         self._idx = tuple((self.miller[:, i] % self.grid[i]) for i in range(3))
+        # threads for the 3-D FFTs (None: numpy's single-threaded FFT; an int: scipy.fft with
+        # that many workers -- the same transform definition, only the speed differs)
+        self.fft_workers = None
 
     @classmethod
     def from_cell(cls, cell):
@@ -92,9 +95,15 @@ class PWOperator:
         n3 = self.vloc.size
         grid = np.zeros((nb,) + self.grid, dtype=np.complex128)
         grid[(slice(None),) + self._idx] = Y.T
-        psi_r = np.fft.ifftn(grid, axes=(1, 2, 3)) * n3
-        psi_r *= self.vloc[None]
-        out = np.fft.fftn(psi_r, axes=(1, 2, 3)) / n3
+        if self.fft_workers is None:
+            psi_r = np.fft.ifftn(grid, axes=(1, 2, 3)) * n3
+            psi_r *= self.vloc[None]
+            out = np.fft.fftn(psi_r, axes=(1, 2, 3)) / n3
+        else:
+            import scipy.fft
+            psi_r = scipy.fft.ifftn(grid, axes=(1, 2, 3), workers=self.fft_workers) * n3
+            psi_r *= self.vloc[None]
+            out = scipy.fft.fftn(psi_r, axes=(1, 2, 3), workers=self.fft_workers) / n3
         return out[(slice(None),) + self._idx].T
 
     def projections(self, Y):

@@ -435,3 +435,16 @@ def test_woodbury_iterative_refinement_reaches_the_direct_solve():
     assert op.apply_Sinv_refined(x, tol=1.0)[1] == 0
     y0, its0 = op.apply_Sinv_refined(x, tol=1e-14, maxit=0)
     assert its0 == 0 and np.allclose(y0, x)
+
+
+def test_filter_setup_and_threaded_ffts_do_not_change_the_filter():
+    """The CPU baseline forms Section 5.1's G = P^H P and the reduced matrix's factors once and
+    runs the FFTs on several threads: the filter's result is the same to rounding."""
+    cell = _tiny(N=12, natoms=3, nb=5, seed=17)
+    op = pw.PWOperator.from_cell(cell)
+    lo, hi = 0.4, ch.upper_bound(op, "rigorous")
+    ref = ch.filter_reuse(op, cell.Y0, 6, lo, hi)
+    setup = ch.filter_setup(op)
+    op.fft_workers = 4
+    got = ch.filter_reuse(op, cell.Y0, 6, lo, hi, setup=setup)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
