@@ -129,16 +129,25 @@ def aggregate(filter_s: float, step_s: float, units_per_rank: float, world: int)
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
-def oracle_rate(cell, nbands_sample: int, degree: int):
-    """The FP64 oracle's Algorithm-2 filter on a sample of bands: band-applies/s, seconds."""
-    import numpy as np
+def oracle_setup(cell):
+    """The oracle's operator and its one-time filter setup (Section 5.1's G = P^H P and the
+    reduced matrix's LU factors), FFTs on every host core; not part of any timing."""
     from oracle import chebyshev as ch
     from oracle.planewave import PWOperator
     op = PWOperator.from_cell(cell)
+    op.fft_workers = os.cpu_count()
+    return op, ch.filter_setup(op)
+
+
+def oracle_rate(cell, nbands_sample: int, degree: int, prepared=None):
+    """The FP64 oracle's Algorithm-2 filter on a sample of bands: band-applies/s, seconds."""
+    import numpy as np
+    from oracle import chebyshev as ch
+    op, setup = prepared if prepared is not None else oracle_setup(cell)
     Y = np.asfortranarray(cell.Y0[:, :nbands_sample])
     lo, hi = 1.0, float(op.K.max()) + 10.0
     t0 = time.perf_counter()
-    ch.filter_reuse(op, Y, degree, lo, hi)
+    ch.filter_reuse(op, Y, degree, lo, hi, setup=setup)
     dt = time.perf_counter() - t0
     return nbands_sample * degree / dt, dt
 
@@ -151,11 +160,12 @@ def run_reference(args):
     from synth import config_cell
     cell = config_cell(WORKLOAD)
     sample = args.ref_bands
+    prepared = oracle_setup(cell)
     for _ in range(args.warmup):
-        oracle_rate(cell, sample, DEGREE)
+        oracle_rate(cell, sample, DEGREE, prepared)
     rates, secs = [], []
     for _ in range(args.steps):
-        r, dt = oracle_rate(cell, sample, DEGREE)
+        r, dt = oracle_rate(cell, sample, DEGREE, prepared)
         rates.append(r)
         secs.append(dt)
     value = sample * DEGREE * args.steps / sum(secs)
@@ -168,9 +178,9 @@ def run_reference(args):
         "config": {"workload": WORKLOAD + " (96^3 grid, 60005 plane waves, 2048 projectors, PAW, degree 4)",
                    "sample": "%d of 2048 bands per step" % sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d bands x degree %d per step; includes the oracle's own P^H P and "
-                                   "reduced-matrix setup each call; numpy FFTs single-threaded, BLAS on all "
-                                   "cores" % (sample, DEGREE)},
+                         "sample": "%d bands x degree %d per step; the oracle's P^H P and reduced-matrix LU "
+                                   "formed once before timing; FFTs (scipy) and BLAS on all %d cores"
+                                   % (sample, DEGREE, cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -378,8 +388,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "f32", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64-form filter calls (0: skip)")
-    ap.add_argument("--cpu-bands", type=int, default=16, help="bands in the oracle's timed CPU sample")
-    ap.add_argument("--ref-bands", type=int, default=4)
+    ap.add_argument("--cpu-bands", type=int, default=64, help="bands in the oracle's timed CPU sample")
+    ap.add_argument("--ref-bands", type=int, default=64)
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
     ap.add_argument("--gate-sweeps", type=int, default=120, help="gate: most FP64 sweeps before giving up")
@@ -406,16 +416,27 @@ def main():
     from paper_1406_4350_gb300 import build as b
     from paper_1406_4350_gb300 import F32, F64, MIXED, BOUND_RIGOROUS
     from paper_1406_4350_gb300.chebfi import ChebFI, fortran
+    from paper_1406_4350_gb300.parallel import band_range, gather_bands
     from synth import config_cell
     b.build()
     prec = {"mixed": MIXED, "f32": F32, "f64": F64}[args.prec]
 
     cell = config_cell(args.workload, nbands=args.nbands)
     nb, npw, nq = cell.nbands, cell.npw, cell.nproj
+    # one problem split over the ranks by bands (the filter treats bands independently):
+    # rank r filters bands [b0, b1); Rayleigh-Ritz gathers the block (the method's exchange
+    # step) and every rank keeps its own bands of the rotated block
+    b0, b1 = band_range(nb, world, rank)
     g = ChebFI.from_cell(cell, device=local)
     hi = g.upper_bound(BOUND_RIGOROUS)
     Y = fortran(cell.Y0, device="cuda:%d" % local)
     lo = float(g.rayleigh_quotients(Y).max().item())
+    if world > 1:
+        Y = Y[:, b0:b1].T.contiguous().T
+
+    # measured CUDA-core peaks of this device (the roofline denominators of the SIMT kernels)
+    fp64_peak, _ = g.probe_fma_rate(F64)
+    fp32_peak, _ = g.probe_fma_rate(F32)
 
     def barrier():
         if world > 1:
@@ -432,7 +453,7 @@ def main():
             a[2] += wk
 
     def step(p, timed=None):
-        nonlocal lo
+        nonlocal lo, Y
         st = torch.cuda.current_stream()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         if timed is not None:
@@ -446,7 +467,10 @@ def main():
             _acc("filter")
             g.profile(True)
         torch.cuda.nvtx.range_push("rr")
-        ev, rs = g.rayleigh_ritz(Y)
+        full = gather_bands(Y, nb, world) if world > 1 else Y
+        ev, rs = g.rayleigh_ritz(full)
+        if world > 1:
+            Y = full[:, b0:b1].clone().T.contiguous().T
         torch.cuda.nvtx.range_pop()
         e2.record(st)
         if timed is not None:
@@ -476,9 +500,12 @@ def main():
     step_ms = [a.elapsed_time(c) for a, b_, c, _, _ in timed]
     ev_last = timed[-1][3].cpu().numpy()
     rs_last = timed[-1][4].cpu().numpy()
-    value, filt_s, step_total = aggregate(sum(filt_ms) / 1e3, sum(step_ms) / 1e3, nb * DEGREE * args.steps, world)
+    # the job's units: every band of the one problem, degree applications per step
+    value, filt_s, step_total = aggregate(sum(filt_ms) / 1e3, sum(step_ms) / 1e3, (b1 - b0) * DEGREE * args.steps,
+                                          world)
+    value = nb * DEGREE * args.steps / filt_s
 
-    # FP64 form of the same filter, same workload
+    # FP64 form of the same filter, same bands
     fp64 = None
     if args.fp64_steps > 0 and prec != F64:
         Yc = Y.clone()
@@ -486,6 +513,7 @@ def main():
         g.cheb_filter(Yc, DEGREE, lo, hi, prec=F64)
         Yc.copy_(Y)
         barrier()
+        g.profile(True)
         a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
         for _ in range(args.fp64_steps):
@@ -493,16 +521,20 @@ def main():
         c.record(st)
         barrier()
         ms = a.elapsed_time(c)
-        fp64 = {"value": nb * DEGREE * args.fp64_steps / (ms / 1e3), "unit": UNIT,
-                "ms_per_filter": ms / args.fp64_steps, "dtype": "f64"}
+        tot = g.profile_totals()
+        g.profile(False)
+        fp_s = aggregate(ms / 1e3, 0.0, 0.0, world)[1]  # slowest rank
+        fp64 = {"value": nb * DEGREE * args.fp64_steps / fp_s, "unit": UNIT, "ms_per_filter": ms / args.fp64_steps, "dtype": "f64",
+                "kernels_ms": {k: round(v[0] / args.fp64_steps, 3) for k, v in
+                               sorted(tot.items(), key=lambda kv: -kv[1][0])[:8]}}
         del Yc
 
     # end to end through the public API with host buffers: chebfi_cheb_filter_host takes the
     # pinned host block, copies it in, filters it and copies it back every step (band chunks
     # whose copies overlap the neighbouring chunks' filters)
-    host = torch.empty((nb, npw), dtype=torch.complex128, pin_memory=True).T
+    host = torch.empty((Y.shape[1], npw), dtype=torch.complex128, pin_memory=True).T
     host.copy_(Y)
-    torch.cuda.synchronize()
+    barrier()
     st = torch.cuda.current_stream()
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ea.record(st)
@@ -511,39 +543,67 @@ def main():
     eb.record(st)
     torch.cuda.synchronize()
     e2e_s = ea.elapsed_time(eb) / 1e3
-    nbytes = npw * nb * 16
+    _, e2e_s, _ = aggregate(e2e_s, 0.0, 0.0, world)
+    nbytes = npw * (b1 - b0) * 16
 
-    # roofline of the dominant kernel over the timed region, from the library's per-launch
-    # CUDA events and each launch's algorithmic work (flops for GEMMs, bytes for the FFT passes)
+    # rooflines from the library's per-launch CUDA events and each launch's algorithmic work
+    # (flops for GEMMs and the Jacobi sweeps, bytes for the FFT passes)
     peaks = _peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", 1713.1)
+    hbm = peaks.get("hbm_gbs", 6762.3)
+    nmod = 14
 
     def roofline(phase, name):
         ms_tot, cnt, work = prof_acc[phase][name]
         avg_s = ms_tot / cnt / 1e3
+        out = {"kernel": name, "phase": phase}
         if name.startswith("tc_"):
-            peak, bound, unit, src = peaks.get("bf16_tflops_sustained", 1713.1), "tensor", "TFLOP/s", \
-                "bf16_tflops_sustained (measured); bf16x3 executes 3x the algorithmic flops"
+            # bf16x3: the pipe executes 3 MMAs per algorithmic product
+            ach = work / cnt / avg_s / 1e12
+            out.update(bound="tensor", unit="TFLOP/s", achieved=ach, peak=bf16, frac=ach / bf16,
+                       frac_executed=3 * ach / bf16,
+                       peak_source="bf16_tflops_sustained (measured); algorithmic flops, the pipe executes 3x")
+        elif name == "k_oz_gemm":
+            # FP64 products on the tensor cores: one bf16 GEMM per modulus
+            ach = work / cnt / avg_s / 1e12
+            out.update(bound="tensor", unit="TFLOP/s", achieved=ach * nmod, peak=bf16, frac=ach * nmod / bf16,
+                       fp64_equivalent_tflops=ach, fp64_equivalent_over_fp64_peak=ach / fp64_peak,
+                       peak_source="bf16_tflops_sustained (measured); executed = %d moduli x the FP64 flops" % nmod)
+        elif name == "k_jac_sweep":
+            ach = work / cnt / avg_s / 1e12
+            out.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp32_peak, frac=ach / fp32_peak,
+                       peak_source="FP32 FMA rate measured in this run (chebfi_probe_fma_rate)")
         elif "gemm" in name:
-            fp64 = phase == "rr" or prec == F64
-            if fp64:
-                peak, bound, unit, src = 1.25, "alu", "TFLOP/s", "FP64 nominal 1.25 TFLOP/s (recipe)"
-            else:
-                peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-                bound, unit, src = "alu", "TFLOP/s", "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max clock"
+            ach = work / cnt / avg_s / 1e12
+            pk = fp64_peak if prec == F64 else fp32_peak
+            out.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=pk, frac=ach / pk,
+                       peak_source="FMA rate measured in this run (chebfi_probe_fma_rate)")
         else:
-            peak, bound, unit, src = peaks.get("hbm_gbs", 6762.3), "hbm", "GB/s", "hbm_gbs (measured)"
-        scale = 1e12 if unit == "TFLOP/s" else 1e9
-        achieved = work / cnt / avg_s / scale
-        traffic = _traffic(name) if (args.workload == WORKLOAD and args.nbands is None) else None
-        return {"bound": bound, "kernel": name, "phase": phase, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
-                "launches_per_step": cnt / args.steps, "work_per_launch": work / cnt}
+            ach = work / cnt / avg_s / 1e9
+            out.update(bound="hbm", unit="GB/s", achieved=ach, peak=hbm, frac=ach / hbm,
+                       peak_source="hbm_gbs (measured)")
+        out["traffic"] = _traffic(name) if (args.workload == WORKLOAD and args.nbands is None and world == 1) else None
+        out.update(avg_launch_ms=avg_s * 1e3, launches_per_step=cnt / args.steps, work_per_launch=work / cnt)
+        return out
 
-    allk = [(v[0], ph, k) for ph in prof_acc for k, v in prof_acc[ph].items()]
-    _, ph_dom, k_dom = max(allk)
-    roof = roofline(ph_dom, k_dom)
-    _, k_fdom = max((v[0], k) for k, v in prof_acc["filter"].items())
-    roof_filter = roofline("filter", k_fdom)
+    def dominant(phase):
+        return max((v[0], k) for k, v in prof_acc[phase].items() if v[2] > 0)[1]
+
+    roof = roofline("filter", dominant("filter"))
+    # the whole filter against its roofline: sum over its kernels of work / peak, over the time
+    ideal = 0.0
+    for k, (ms_tot, cnt, work) in prof_acc["filter"].items():
+        if work <= 0:
+            continue
+        r_ = roofline("filter", k)
+        scale = 1e12 if r_["unit"] == "TFLOP/s" else 1e9
+        ideal += work / (r_["peak"] * scale)
+    filt_mean_s = statistics.mean(filt_ms) / 1e3
+    roof["combined"] = {"frac": ideal / args.steps / filt_mean_s, "ideal_ms": 1e3 * ideal / args.steps,
+                        "measured_ms": 1e3 * filt_mean_s,
+                        "what": "sum over the filter's kernels of algorithmic work / that kernel's peak, "
+                                "over the filter's measured time"}
+    roof_rr = roofline("rr", dominant("rr"))
 
     # eigenvalue state after the timed steps (residual norms in FP64)
     k75 = (3 * nb) // 4
@@ -551,33 +611,37 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
         "dtype": {"mixed": "bf16x3+f32", "f32": "f32", "f64": "f64"}[args.prec], "data": "synthetic",
         "config": {"workload": "%s: %d^3 grid, %d plane waves, %d bands, %d projectors, PAW=%s, degree 4, one "
                                "filter + FP64 Rayleigh-Ritz per step" % (args.workload, cell.grid[0], npw, nb, nq,
                                                                          cell.Q is not None),
                    "filter_form": args.prec, "l2": "inputs (2 GB per block) larger than L2; no flush",
-                   "lambda_hi": "rigorous bound %.4f Ha" % hi},
+                   "lambda_hi": "rigorous bound %.4f Ha" % hi,
+                   "parallelism": "bands split over %d rank(s), block gathered for Rayleigh-Ritz" % world},
         "phases_ms": {"filter": statistics.mean(filt_ms), "rayleigh_ritz": statistics.mean(rr_ms)},
         "fp64_form": fp64,
-        "e2e": {"value": world * nb * DEGREE * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        "e2e": {"value": nb * DEGREE * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "roofline": roof,
-        "filter_roofline": roof_filter,
+        "rr_roofline": roof_rr,
+        "measured_peaks": {"fp64_fma_tflops": fp64_peak, "fp32_fma_tflops": fp32_peak, "hbm_gbs": hbm,
+                           "bf16_tflops_sustained": bf16},
         "kernels_ms": {ph: {k: round(v[0] / args.steps, 3) for k, v in sorted(prof_acc[ph].items(),
-                                                                              key=lambda kv: -kv[1][0])[:10]}
+                                                                              key=lambda kv: -kv[1][0])[:12]}
                        for ph in prof_acc},
         "ritz": {"max_residual_lowest_75pct": float(rs_last[:k75].max()), "lambda_min": float(ev_last[0])},
         "clocks": clocks,
         "wall_s_timed": wall,
     }
     if rank == 0 and world == 1 and args.cpu_bands > 0:
-        r, dt = oracle_rate(cell, args.cpu_bands, DEGREE)
+        prepared = oracle_setup(cell)
+        r, dt = oracle_rate(cell, args.cpu_bands, DEGREE, prepared)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": "%d of %d bands, degree %d, one filter call (%.1f s incl. the "
-                                          "oracle's P^H P setup); numpy FFTs single-threaded, BLAS on all cores"
-                                          % (args.cpu_bands, nb, DEGREE, dt)}
+                                "sample": "%d of %d bands, degree %d, one filter call (%.1f s); the oracle's "
+                                          "P^H P and reduced-matrix LU formed once before timing; FFTs (scipy) "
+                                          "and BLAS on all cores" % (args.cpu_bands, nb, DEGREE, dt)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -312,6 +312,12 @@ int chebfi_eigensolver_steps(const chebfi_ctx* ctx);
  * Synchronises. */
 int chebfi_selftest_bounded_wait(chebfi_ctx* ctx, int which, double limit_ms, int* recorded, double* elapsed_ms);
 
+/* FMA rate of the device's CUDA cores (a library diagnostic): eight independent FMA chains
+ * per thread on every SM, timed with CUDA events after one warm-up run.  prec: CHEBFI_F64 or
+ * CHEBFI_F32.  *tflops receives 2 x FMAs / time in TFLOP/s, *ms the timed run.  About 0.2 s
+ * of device time.  Synchronises. */
+int chebfi_probe_fma_rate(chebfi_ctx* ctx, int prec, double* tflops, double* ms);
+
 /* Synchronise the context's work and return the first device-detected error, if any. */
 int chebfi_sync_status(chebfi_ctx* ctx);
 

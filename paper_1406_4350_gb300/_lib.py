@@ -76,6 +76,7 @@ SIGNATURES = {
     "chebfi_set_eigensolver": (c_int, [c_void_p, c_int]),
     "chebfi_eigensolver_steps": (c_int, [c_void_p]),
     "chebfi_selftest_bounded_wait": (c_int, [c_void_p, c_int, c_double, P_int, P_double]),
+    "chebfi_probe_fma_rate": (c_int, [c_void_p, c_int, P_double, P_double]),
     "chebfi_sync_status": (c_int, [c_void_p]),
     "chebfi_kernel_launches": (c_int64, [c_void_p]),
     "chebfi_profile_enable": (c_int, [c_void_p, c_int]),

@@ -300,6 +300,13 @@ class ChebFI:
                                                           ctypes.byref(ms)))
         return code.value, ms.value
 
+    def probe_fma_rate(self, prec: int = F64):
+        """Measured FMA throughput of the CUDA cores: (TFLOP/s, ms of the timed run)."""
+        tf = ctypes.c_double(0.0)
+        ms = ctypes.c_double(0.0)
+        self._check(self.lib.chebfi_probe_fma_rate(self.h, prec, ctypes.byref(tf), ctypes.byref(ms)))
+        return tf.value, ms.value
+
     def set_eigensolver(self, mode: int):
         """Dense eigensolver of Rayleigh-Ritz: EIG_AUTO, EIG_JACOBI (FP64) or EIG_REFINED (FP32
         Jacobi + FP64 refinement)."""

@@ -447,9 +447,11 @@ void jacobi_eigh_t(int64_t n0, cplx<R>* A, int64_t lda, R* w, cplx<R>* V, int64_
       C* Aa = A;
       C* Va = Vtmp;
       void* args[] = {&n0a, &na, &Aa, &ldaa, &Va, &ldva, &rot, &pairs, &bar, &status};
-      CHEBFI_LAUNCH("k_jac_sweep", st,
-                    CHEBFI_CUDA(cudaLaunchCooperativeKernel((const void*)k_jac_sweep<R>, dim3(coop_blocks), dim3(256),
-                                                            args, 0, st)));
+      // work: per round every entry of A gets two rotations and every entry of V one, about
+      // 11 real flops per complex entry per rotation: 33 n^3 per sweep
+      CHEBFI_LAUNCH_W("k_jac_sweep", st, 33.0 * (double)n0 * (double)n0 * (double)n0,
+                      CHEBFI_CUDA(cudaLaunchCooperativeKernel((const void*)k_jac_sweep<R>, dim3(coop_blocks),
+                                                              dim3(256), args, 0, st)));
     } else {
       for (int64_t round = 0; round < n - 1; ++round) {
         CHEBFI_LAUNCH("k_jac_params", st,
