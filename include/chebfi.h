@@ -251,8 +251,10 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
  *  - Bands are processed in chunks that fit the array.  A problem whose single band needs
  *    more than 32 MiB of scratch (FFT column buffer N3 x columns, plus 2 npw + 2 nproj, in
  *    complex doubles) is rejected with CHEBFI_ERR_ARG and a message naming the sizes.
- *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - The first call on each device does one-time set-up with that device current: it looks
+ *    up the array's device address (cudaGetSymbolAddress) and uploads the FFT twiddle tables
+ *    to constant memory (a synchronous copy).  Make that first call before any stream
+ *    capture.
  *  - All calls share the one array, which keeps the previous call's contents (nothing in it
  *    needs to start at zero); calls that overlap on the GPU (other streams, other contexts
  *    on the same device, other host threads) race on it. */

@@ -1,8 +1,8 @@
 // Allocation-free application of H, for callers that cannot allocate device memory at
-// the point of use: code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a stream operation and breaks the capture), code inside a host
-// callback or a real-time section that must not take the allocator's locks, and hosts
-// whose memory is handed out by a framework that forbids outside allocations.
+// the point of use: code inside a host callback or a latency-critical section that must
+// not take the CUDA allocator's lock, frameworks that hand out every byte of device memory
+// through their own pool and forbid outside allocations, and processes that have already
+// reserved all of it.
 //
 // Everything this entry point needs beyond its inputs and outputs lives in one
 // file-scope __device__ array of fixed size.  The context must have been set up before
