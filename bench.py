@@ -308,6 +308,22 @@ def run_extra(args):
                 "gpu_launches_per_call": launches, "autotuned_shapes": shapes, "split_k_PhY": split,
                 "autotune_ms": tune.round(4).tolist(), "split_ms": split_ms.round(4).tolist(),
                 "clocks": clk.summary()}
+    elif args.task == "filter_only":
+        # the filter alone (no Rayleigh-Ritz) on a named cell: the command behind the
+        # per-kernel counter captures of small cases
+        from paper_1406_4350_gb300 import MIXED
+        prec = {"mixed": MIXED, "f32": F32, "f64": F64}[args.prec]
+        cell = config_cell(args.workload, nbands=args.nbands)
+        g = ChebFI.from_cell(cell)
+        hi = g.upper_bound(BOUND_RIGOROUS)
+        Y = fortran(cell.Y0)
+        lo = float(g.rayleigh_quotients(Y).max().item())
+        ms = _timed(lambda: g.cheb_filter(Y, DEGREE, lo, hi, prec=prec), args.steps, args.warmup)
+        line = {"metric": "filter band-H-applies/s (filter only)", "unit": UNIT,
+                "value": Y.shape[1] * DEGREE / (ms / 1e3), "dtype": args.prec, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_filter": ms,
+                "config": {"workload": "%s: %d^3 grid, %d plane waves, %d bands, %d projectors, degree %d"
+                                       % (args.workload, cell.grid[0], cell.npw, Y.shape[1], cell.nproj, DEGREE)}}
     elif args.task == "gate":
         # Accuracy gate at the benchmark workload: Algorithm 2 from the same start in the
         # FP64 form until the residual certificate holds for the lowest 75 % of the bands,
@@ -393,7 +409,7 @@ def main():
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
     ap.add_argument("--gate-sweeps", type=int, default=120, help="gate: most FP64 sweeps before giving up")
-    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking", "gate"],
+    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking", "gate", "filter_only"],
                     help="filter: the benchmark; backward / refine: the differentiation and the "
                          "refinement-Woodbury measurements (their own JSON line)")
     args = ap.parse_args()

@@ -250,7 +250,8 @@ template <typename R, int N>
 __global__ void __launch_bounds__(kThreads) k_plane_f(cplx<R>* __restrict__ T, const R* __restrict__ Vs, FastArgs fa,
                                                       const cplx<R>* __restrict__ twxy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fk::plane_body<R, N>(T, Vs, fa, twxy, blockIdx.x, blockIdx.y, smem_raw);
+  (void)twxy;
+  fk::plane_body_pruned<R, N>(T, Vs, fa, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 template <typename R, int N3>
@@ -288,6 +289,11 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   fa.pw_z = s.pw_z.p;
   fa.col_off = s.col_off_nat.p;
   fa.row_off = s.rows_nat.p;
+  fa.row_col = s.row_col.p;
+  for (int w = 0; w < 4; ++w) fa.act[w] = s.act_mask[w];
+  // ceil(2^32 / nxa): exact quotients t / nxa for t < 2^32 / nxa (the row passes use t < 2^12)
+  fa.nl_magic = s.nxa > 1 ? (unsigned)(((1ull << 32) + s.nxa - 1) / (unsigned long long)s.nxa) : 0u;
+  CHEBFI_REQUIRE(s.nxa >= 1, CHEBFI_ERR_STATE, "sphere without columns");
   const cplx<R>* tw = sizeof(R) == 8 ? (const cplx<R>*)ctx->ax[0].tw64.p : (const cplx<R>*)ctx->ax[0].tw32.p;
   const R* Vs = sizeof(R) == 8 ? (const R*)ctx->d_vs.p : (const R*)ctx->d_vsf.p;
   const size_t zbytes = (size_t)(N + kCBF * s.zpitch) * sizeof(cplx<R>);

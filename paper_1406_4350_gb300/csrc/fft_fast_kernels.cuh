@@ -32,6 +32,9 @@ struct FastArgs {
   const int32_t* pw_z;      // natural z of each sorted sphere point
   const int32_t* col_off;   // slot(x) * pitch + y of each column (plane rows cyclically shifted)
   const int32_t* row_off;   // slot(x) * pitch of each active x
+  const int32_t* row_col = nullptr;            // (active row, natural y) -> column, or -1
+  unsigned long long act[4] = {0, 0, 0, 0};    // active slots (pruned plane pass)
+  unsigned nl_magic = 0;                       // t / nxa == umulhi(t, nl_magic) for t < 2^16
 };
 
 template <typename R, int N>
@@ -161,6 +164,144 @@ __device__ __forceinline__ void plane_body(cplx<R>* __restrict__ T, const R* __r
   __syncthreads();
   fast::lines_G<N, -1>(plane, fa.nxa, rows, 1, tw);       // along y on the needed rows
   for (int c = threadIdx.x; c < fa.ncol; c += blockDim.x) t[c] = plane[fa.col_off[c]];
+}
+
+// The plane pass of plane_body with its zero rows pruned and its scatter / gather fused:
+// the first y pass reads the sphere columns straight from the column buffer (no zeroed
+// plane, no scatter), the x passes skip the loads of rows that hold no column (they are
+// zero) and the stores of rows no later pass reads, and the last y pass stores the columns
+// straight to the column buffer (no gather).  Same arithmetic, in the same order.
+template <typename R, int N>
+__device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const R* __restrict__ Vs,
+                                                  const FastArgs& fa, int z, int64_t b, unsigned char* smem_raw) {
+  using C = cplx<R>;
+  constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB;
+  const ConstTw<R, N> tw;
+  C* plane = reinterpret_cast<C*>(smem_raw) + N;
+  const C zero = cmake<C>(0.0, 0.0);
+  C* t = T + b * fa.ldt + (int64_t)z * fa.ncolp;
+  const int nl = fa.nxa;
+  const unsigned long long m0 = fa.act[0], m1 = fa.act[1], m2 = fa.act[2], m3 = fa.act[3];
+  auto active = [=](int slot) {
+    const unsigned long long w = slot < 64 ? m0 : slot < 128 ? m1 : slot < 192 ? m2 : m3;
+    return ((w >> (slot & 63)) & 1ull) != 0;
+  };
+  LineMap rows;
+  rows.off = fa.row_off;
+  // y, inverse: F's pass A on the active rows, its inputs read from the column buffer;
+  // consecutive threads take consecutive y of one row, so they read consecutive columns
+  {
+    // blockDim.x is a multiple of NB, so every item of this thread has the same nb: its
+    // twiddles are read once (a warp's threads hold NB different nb)
+    const int nb = threadIdx.x % NB;
+    C w[NA];
+#pragma unroll
+    for (int ka = 1; ka < NA; ++ka) w[ka] = fast::twN<+1>(tw, nb * ka);
+    for (int it = threadIdx.x; it < nl * NB; it += blockDim.x) {
+      const int a = it / NB;
+      C* row = plane + fa.row_off[a] + nb;
+      const int32_t* rc = fa.row_col + a * N + nb;
+      C v[NA];
+#pragma unroll
+      for (int na = 0; na < NA; ++na) {
+        const int c = __ldg(rc + NB * na);
+        v[na] = c >= 0 ? t[c] : zero;
+      }
+      fast::dft<NA, +1>(v);
+      row[0] = v[0];
+#pragma unroll
+      for (int ka = 1; ka < NA; ++ka) row[NB * ka] = v[ka] * w[ka];
+    }
+  }
+  __syncthreads();
+  // F's pass B on the active rows: item t = (ka, row) with the row fastest (rows are an odd
+  // pitch apart: no bank conflicts); ka = t / nl by the multiplier of fa.nl_magic
+  for (int it = threadIdx.x; it < nl * NA; it += blockDim.x) {
+    const int ka = nl == 1 ? it : (int)__umulhi((unsigned)it, fa.nl_magic), a = it - ka * nl;
+    C* g = plane + fa.row_off[a] + NB * ka;
+    C u[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) u[q] = g[q];
+    fast::dft<NB, +1>(u);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) g[q] = u[q];
+  }
+  __syncthreads();
+  // x, inverse: F's pass A on every y line, rows without columns are zero
+  for (int it = threadIdx.x; it < N * NB; it += blockDim.x) {
+    const int nb = it / N, yy = it - nb * N;
+    C* a = plane + yy + nb * fa.pitch;
+    C v[NA];
+#pragma unroll
+    for (int na = 0; na < NA; ++na) v[na] = active(NB * na + nb) ? a[NB * na * fa.pitch] : zero;
+    fast::dft<NA, +1>(v);
+#pragma unroll
+    for (int ka = 0; ka < NA; ++ka) a[NB * ka * fa.pitch] = ka == 0 ? v[0] : v[ka] * fast::twN<+1>(tw, nb * ka);
+  }
+  __syncthreads();
+  {
+    // F's pass B, the multiply by V_loc and G's pass B, in registers per contiguous group
+    const R* v = Vs + (int64_t)z * N * N;
+    for (int it = threadIdx.x; it < N * NA; it += blockDim.x) {
+      const int ka = it / N, yy = it - ka * N;
+      C* a = plane + yy + NB * ka * fa.pitch;
+      const R* vv = v + (NB * ka) * N + yy;
+      C u[NB];
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb) u[nb] = a[nb * fa.pitch];
+      fast::dft<NB, +1>(u);
+#pragma unroll
+      for (int kb = 0; kb < NB; ++kb) {
+        const R s = vv[kb * N];
+        u[kb].x *= s;
+        u[kb].y *= s;
+      }
+      fast::dft<NB, -1>(u);
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb)
+        a[nb * fa.pitch] = (ka == 0 || nb == 0) ? u[nb] : u[nb] * fast::twN<-1>(tw, nb * ka);
+    }
+  }
+  __syncthreads();
+  // x, forward: G's pass A, storing only the rows the y pass reads
+  for (int it = threadIdx.x; it < N * NB; it += blockDim.x) {
+    const int nb = it / N, yy = it - nb * N;
+    C* a = plane + yy + nb * fa.pitch;
+    C v[NA];
+#pragma unroll
+    for (int ka = 0; ka < NA; ++ka) v[ka] = a[NB * ka * fa.pitch];
+    fast::dft<NA, -1>(v);
+#pragma unroll
+    for (int na = 0; na < NA; ++na)
+      if (active(NB * na + nb)) a[NB * na * fa.pitch] = v[na];
+  }
+  __syncthreads();
+  // y, forward: G's pass B, then G's pass A storing the columns to the column buffer
+  for (int it = threadIdx.x; it < nl * NA; it += blockDim.x) {
+    const int ka = nl == 1 ? it : (int)__umulhi((unsigned)it, fa.nl_magic), a = it - ka * nl;
+    C* g = plane + fa.row_off[a] + NB * ka;
+    C u[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) u[q] = g[q];
+    fast::dft<NB, -1>(u);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) g[q] = (ka == 0 || q == 0) ? u[q] : u[q] * fast::twN<-1>(tw, q * ka);
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nl * NB; it += blockDim.x) {
+    const int a = it / NB, nb = it - a * NB;  // consecutive columns per warp, as above
+    const C* row = plane + fa.row_off[a] + nb;
+    const int32_t* rc = fa.row_col + a * N + nb;
+    C v[NA];
+#pragma unroll
+    for (int ka = 0; ka < NA; ++ka) v[ka] = row[NB * ka];
+    fast::dft<NA, -1>(v);
+#pragma unroll
+    for (int na = 0; na < NA; ++na) {
+      const int c = __ldg(rc + NB * na);
+      if (c >= 0) t[c] = v[na];
+    }
+  }
 }
 
 // columns [c0, c0 + kCBF) of block b: forward z transform, back to the sphere, + K psi and

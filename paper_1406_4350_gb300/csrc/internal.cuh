@@ -180,6 +180,8 @@ struct SphereFFT {
   DevBuf<int32_t> pw_z;        // sorted sphere point -> z
   DevBuf<int32_t> col_off_nat; // column -> slot(x) * pitch + y, slot(x) = (x + n1/2) mod n1
   DevBuf<int32_t> rows_nat;    // slot(x) * pitch of the active rows, consecutive slots
+  DevBuf<int32_t> row_col;     // active row a, natural y -> column index, or -1 (nxa x n2)
+  unsigned long long act_mask[4] = {0, 0, 0, 0};  // bit slot(x) set for the active rows
 };
 
 // Workspace grown on demand (never shrinks while the context lives).

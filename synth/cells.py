@@ -218,6 +218,11 @@ CONFIGS = {
     # wavefunction block (512 bands) still exceeds the L2 cache
     "paw72": dict(L=30.0, grid=72, ecut=7.275, natoms=108, nlmn=8, nbands=512, paw=True,
                   degree=4, sweeps=4, seed=1006),
+    # paw96's FFT geometry (same cell, grid and E_cut: the same 60005-point sphere and 1861
+    # columns) with 4 atoms: a small device footprint for counter captures of the FFT passes,
+    # its column buffer (128 bands, 183 MB) still larger than the L2 cache
+    "prof96": dict(L=40.0, grid=96, ecut=7.275, natoms=4, nlmn=8, nbands=128, paw=True,
+                   degree=4, sweeps=4, seed=1007),
 }
 
 
