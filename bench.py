@@ -212,14 +212,15 @@ def run_extra(args):
     refine: S^{-1} by Section 5.1's iterative refinement against the direct Woodbury form on
     the benchmark workload's first 256 bands.
     kpoints: the batched k-point filter (64 k-points of a 48^3 PAW cell, spheres of 3000 to
-    12000 plane waves, 128 bands each, FP32, degree 8) against one filter call per k-point.
+    12000 plane waves, 128 bands each, FP32, degree 8) against one filter call per k-point,
+    and the same batch in the mixed form (projector products on the tensor cores).
     locking: the 48^3 PAW cell (8025 plane waves, 256 bands), 20 sweeps with and without
     locking: FP64 form at degree 10 and residual 1e-9, mixed form at degree 8 (degree 10 trips
     its overflow guard there) and residual 3e-5, above its floor; time, band-applies."""
     import numpy as np
     import torch
     from paper_1406_4350_gb300 import build as b
-    from paper_1406_4350_gb300 import F32, F64, BOUND_RIGOROUS
+    from paper_1406_4350_gb300 import F32, F64, MIXED, BOUND_RIGOROUS
     from paper_1406_4350_gb300.chebfi import ChebFI, fortran
     from synth import config_cell
     b.build()
@@ -298,6 +299,12 @@ def run_extra(args):
                 g_.cheb_filter(Y, deg, l, h, prec=F32)
         ms_l = _timed(loop, args.steps, args.warmup)
         units = sum(c.nbands for c in cells) * deg
+        # mixed form: the same batch with the projector products as grouped tensor-core GEMMs
+        mixed = [Y.clone() for Y in Ys]
+        l0 = bt.kernel_launches
+        bt.cheb_filter(mixed, deg, los, his, prec=MIXED)
+        ms_m = _timed(lambda: bt.cheb_filter(mixed, deg, los, his, prec=MIXED), args.steps, args.warmup)
+        launches_m = (bt.kernel_launches - l0) // (args.steps + args.warmup + 1)
         line = {"metric": "batched k-point filter band-H-applies/s", "unit": "band-H-applies/s",
                 "value": units / (ms_b / 1e3), "dtype": "f32", "steps": args.steps, "warmup": args.warmup,
                 "config": {"workload": "64 k-points of a 48^3 PAW cell (L = 20 bohr, 32 atoms x 8 projectors), "
@@ -305,9 +312,34 @@ def run_extra(args):
                                        "per step" % (min(c.npw for c in cells), max(c.npw for c in cells),
                                                      cells[0].nbands, deg)},
                 "ms_batched": ms_b, "ms_per_kpoint_loop": ms_l, "speedup_over_loop": ms_l / ms_b,
-                "gpu_launches_per_call": launches, "autotuned_shapes": shapes, "split_k_PhY": split,
+                "gpu_launches_per_call": launches,
+                "mixed": {"ms_batched": ms_m, "band_H_applies_per_s": units / (ms_m / 1e3),
+                          "gpu_launches_per_call": launches_m}, "autotuned_shapes": shapes, "split_k_PhY": split,
                 "autotune_ms": tune.round(4).tolist(), "split_ms": split_ms.round(4).tolist(),
                 "clocks": clk.summary()}
+    elif args.task == "gemm64":
+        # the FP64 complex GEMM engines on one product C = A^H B (m x n, inner k): the modular
+        # tensor-core emulation against FP64 FMA on the CUDA cores
+        from paper_1406_4350_gb300._lib import GEMM_CUDA_CORES, GEMM_TENSOR
+        m, n, k = args.gemm_mnk
+        g = ChebFI(0)
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        A = torch.randn((m, k), dtype=torch.complex128, device="cuda", generator=gen).T
+        B = torch.randn((n, k), dtype=torch.complex128, device="cuda", generator=gen).T
+        out = {}
+        for name, eng in (("tensor", GEMM_TENSOR), ("cuda_cores", GEMM_CUDA_CORES)):
+            g.set_fp64_gemm(eng, 14)
+            C = torch.zeros((n, m), dtype=torch.complex128, device="cuda").T
+            reps = args.steps if eng == GEMM_TENSOR else 1
+            ms = _timed(lambda: g.gemm_fp64(A, B, conjA=True, C=C), reps, 1 if eng == GEMM_TENSOR else 0)
+            out[name] = {"ms": ms, "tflops_fp64_equivalent": 8.0 * m * n * k / (ms / 1e3) / 1e12, "C": C}
+        diff = float((out["tensor"]["C"] - out["cuda_cores"]["C"]).abs().max() / out["cuda_cores"]["C"].abs().max())
+        for v in out.values():
+            v.pop("C")
+        line = {"metric": "FP64 complex GEMM, FP64-equivalent TFLOP/s (modular tensor-core emulation)",
+                "unit": "TFLOP/s", "value": out["tensor"]["tflops_fp64_equivalent"], "dtype": "f64",
+                "steps": args.steps, "config": {"workload": "C = A^H B, m = %d, n = %d, k = %d, 14 moduli" % (m, n, k)},
+                "engines": out, "max_rel_diff": diff}
     elif args.task == "filter_only":
         # the filter alone (no Rayleigh-Ritz) on a named cell: the command behind the
         # per-kernel counter captures of small cases
@@ -408,8 +440,10 @@ def main():
     ap.add_argument("--ref-bands", type=int, default=64)
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
+    ap.add_argument("--gemm-mnk", type=int, nargs=3, default=[2048, 2048, 8192], help="gemm64: m n k")
     ap.add_argument("--gate-sweeps", type=int, default=120, help="gate: most FP64 sweeps before giving up")
-    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking", "gate", "filter_only"],
+    ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking", "gate", "filter_only",
+                             "gemm64"],
                     help="filter: the benchmark; backward / refine: the differentiation and the "
                          "refinement-Woodbury measurements (their own JSON line)")
     args = ap.parse_args()

@@ -376,8 +376,11 @@ int chebfi_batch_set_tiles(chebfi_batch* batch, int prec, const int* shapes, int
 /* In place on Y[k] (device, complex128, npw_k x nb column-major, leading dimension ld[k],
  * caller's plane-wave order) for k = 0..nk-1: Algorithm 2's filter of the given degree on
  * [lambda_lo[k], lambda_hi[k]] (host arrays of nk doubles), exactly as chebfi_cheb_filter
- * computes it per k-point, in the FP64 or FP32 form.  Stream-ordered on `stream`; the first
- * call of a (form, degree) pair tunes and captures, later calls replay the graph.  The
+ * computes it per k-point, in the FP64, FP32 or mixed form (CHEBFI_MIXED: FP32 iterates and
+ * FFT, the projector products as grouped tcgen05 GEMMs over all k-points on bf16 (hi, lo)
+ * pairs; needs projectors).  Stream-ordered on `stream`; the first call of a (form, degree)
+ * pair tunes (FP64/FP32) or builds the tensor-core operands (mixed) and captures, later calls
+ * replay the graph.  The
  * batch's workspaces and per-call descriptor table are shared by its calls: calls on one
  * batch must be ordered (one stream, or synchronised between streams). */
 int chebfi_batch_cheb_filter(chebfi_batch* batch, void* const* Y, const int64_t* ld, int degree,

@@ -245,13 +245,20 @@ template <typename R> struct FilterBufs {
 // Y (sorted, ld = npw, its buffer is bufs.Ya on entry).  Returns the buffer holding Y_n.
 template <typename R>
 cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb0, int degree, double lo, double hi,
-                       cudaStream_t st, const int64_t* active = nullptr) {
+                       cudaStream_t st, const int64_t* active = nullptr, const double2* p0 = nullptr) {
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
   cplx<R>*cur = b.Ya, *prev = b.Yb, *pcur = b.pa, *pprev = b.pb;
-  if (nq > 0)
+  if (nq > 0 && p0) {
+    // p_0 = P^H Y_0 handed over by the Rayleigh-Ritz step that produced Y_0
+    if constexpr (std::is_same<R, double>::value)
+      CHEBFI_CUDA(cudaMemcpyAsync(pcur, p0, sizeof(double2) * nq * nb0, cudaMemcpyDeviceToDevice, st));
+    else
+      convert(nq, nb0, p0, nq, pcur, nq, st);
+  } else if (nq > 0) {
     cgemm<R>(ctx, true, false, nq, active ? active[0] : nb0, npw, 1.0, Ops<R>::P(ctx), npw, cur, npw, 0.0, pcur, nq, st,
             Ops<R>::ws(ctx), "gemm_PhY");
+  }
   for (int k = 0; k < degree; ++k) {
     const int64_t nb = active ? active[k] : nb0;  // bands still being filtered (a prefix)
     const double a = (k == 0 ? 1.0 : 2.0) / r;
@@ -312,7 +319,7 @@ void ensure_tc(chebfi_ctx* ctx, cudaStream_t st) {
 // with split bf16 operands.  Same steps as filter_sorted; Y_0 and the result are the FP32
 // buffers b.Ya / returned pointer.
 float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb0, int degree, double lo, double hi,
-                     cudaStream_t st, const int64_t* active = nullptr) {
+                     cudaStream_t st, const int64_t* active = nullptr, const double2* p0 = nullptr) {
   const int64_t nb = active ? active[0] : nb0;
   const int64_t npw = ctx->npw, nq = ctx->nproj;
   const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
@@ -324,9 +331,13 @@ float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb0, int degr
     ensure_tc(ctx, st);
     w.Zb.ld = ldzb;
     w.Zb.alloc((size_t)ldzb * nb);
-    split_block(npw, nb, cur, npw, w.Zb, st);
-    tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)pcur, 2 * nq, status, st,
-            "tc_gemm_PhY", &ctx->w.tcws);
+    if (p0) {
+      convert(nq, nb, p0, nq, pcur, nq, st);  // FP64 projections from the Rayleigh-Ritz step
+    } else {
+      split_block(npw, nb, cur, npw, w.Zb, st);
+      tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)pcur, 2 * nq, status,
+              st, "tc_gemm_PhY", &ctx->w.tcws);
+    }
   }
   for (int k = 0; k < degree; ++k) {
     const int64_t nb = active ? active[k] : nb0;  // bands still being filtered (a prefix)
@@ -405,20 +416,23 @@ void ensure_filter_ws(chebfi_ctx* ctx, int64_t nb, int prec) {
   }
 }
 
-// Filter on the sorted FP64 block ctx->w.Ya (in place).
-void filter_on_Ya(chebfi_ctx* ctx, int64_t nb, int degree, double lo, double hi, int prec, cudaStream_t st) {
+// Filter on the sorted FP64 block ctx->w.Ya (in place).  p0: P^H Y_0 when already known
+// (the rotated projections of the Rayleigh-Ritz step that produced Y_0), else null.
+void filter_on_Ya(chebfi_ctx* ctx, int64_t nb, int degree, double lo, double hi, int prec, cudaStream_t st,
+                  const double2* p0 = nullptr) {
   ensure_filter_ws(ctx, nb, prec);
   Work& w = ctx->w;
   const int64_t npw = ctx->npw;
+  w.pc_of = nullptr;  // the filter replaces the block
   if (prec == CHEBFI_F64) {
     FilterBufs<double> b{w.Ya.p, w.Yb.p, w.Z.p, w.T1.p, w.pa.p, w.pb.p, w.pz.p, w.pw.p, w.pq.p};
-    double2* out = filter_sorted<double>(ctx, b, nb, degree, lo, hi, st);
+    double2* out = filter_sorted<double>(ctx, b, nb, degree, lo, hi, st, nullptr, p0);
     if (out != w.Ya.p) CHEBFI_CUDA(cudaMemcpyAsync(w.Ya.p, out, sizeof(double2) * npw * nb, cudaMemcpyDeviceToDevice, st));
   } else {
     convert(npw, nb, w.Ya.p, npw, w.fYa.p, npw, st);
     FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
-    float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lo, hi, st)
-                                       : filter_sorted<float>(ctx, b, nb, degree, lo, hi, st);
+    float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lo, hi, st, nullptr, p0)
+                                       : filter_sorted<float>(ctx, b, nb, degree, lo, hi, st, nullptr, p0);
     convert(npw, nb, out, npw, w.Ya.p, npw, st);
   }
 }
@@ -668,12 +682,14 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   std::swap(w.Ya.p, w.tmp.p);  // buffers have equal capacity
   std::swap(w.Ya.n, w.tmp.n);
   Y = w.Ya.p;
+  // p_new = P^H Y_new = p R: the residuals' S Y_new, and p_0 of the next filter in a solve
+  if (nq > 0) gemm64(ctx, false, false, nq, nb, nb, 1.0, w.pa.p, nq, Ss, nb, 0.0, w.pc.p, nq, st, ws, "gemm_rr");
+  w.pc_of = nq > 0 ? Y : nullptr;
   if (resid) {
     gemm64(ctx, false, false, npw, nb, nb, 1.0, w.HY.p, npw, Ss, nb, 0.0, w.tmp.p, npw, st, ws, "gemm_rr");  // H Y_new
     double2* SY = w.HY.p;  // reuse
     CHEBFI_CUDA(cudaMemcpyAsync(SY, Y, sizeof(double2) * ny, cudaMemcpyDeviceToDevice, st));
     if (ctx->paw) {
-      gemm64(ctx, false, false, nq, nb, nb, 1.0, w.pa.p, nq, Ss, nb, 0.0, w.pc.p, nq, st, ws, "gemm_rr");  // p_new
       blockdiag_apply<double>(ctx, ctx->d_Qblk.p, w.pc.p, nq, w.pb.p, nq, nb, st);
       gemm64(ctx, false, false, npw, nb, nq, 1.0, ctx->d_P.p, npw, w.pb.p, nq, 1.0, SY, npw, st, ws, "gemm_rr");
     }
@@ -711,6 +727,7 @@ void ortho_on_Ya(chebfi_ctx* ctx, int64_t nb, cudaStream_t st) {
 }
 
 void gather_to_Ya(chebfi_ctx* ctx, const void* Y, int64_t nb, int64_t ld, cudaStream_t st) {
+  ctx->w.pc_of = nullptr;  // new contents: no projections known for them
   ctx->w.Ya.alloc((size_t)ctx->npw * nb);
   gather_rows(ctx->npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y, ld, ctx->w.Ya.p, ctx->npw, st);
 }
@@ -1050,6 +1067,9 @@ void filter_backward(chebfi_ctx* ctx, int64_t nb, int n, double lo, double hi, i
 }
 
 }  // namespace
+
+void ensure_tc_operands(chebfi_ctx* ctx, cudaStream_t st) { ensure_tc(ctx, st); }
+
 }  // namespace chebfi
 
 using namespace chebfi;
@@ -1723,8 +1743,14 @@ int chebfi_solve(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t
     const double c = 0.5 * (hi + lo), r = 0.5 * (hi - lo);
     if (cheb_T_abs(dmax, (l1 - c) / r) >= 1.0 / (100.0 * eps))
       throw Error{CHEBFI_ERR_FILTER_OVERFLOW, "T_n((lambda_1 - c)/r) exceeds 1/(100 eps) of the filter precision"};
-    if (lock && s > 0) filter_on_Ya_adaptive(ctx, nb, deg, lo, hi, params->prec, st);
-    else filter_on_Ya(ctx, nb, params->degree, lo, hi, params->prec, st);
+    if (lock && s > 0) {
+      filter_on_Ya_adaptive(ctx, nb, deg, lo, hi, params->prec, st);
+    } else {
+      // after the first sweep the previous Rayleigh-Ritz step holds P^H Y (FP64): the
+      // filter starts from it instead of forming it again
+      const double2* p0 = (s > 0 && ctx->w.pc_of == ctx->w.Ya.p) ? ctx->w.pc.p : nullptr;
+      filter_on_Ya(ctx, nb, params->degree, lo, hi, params->prec, st, p0);
+    }
     for (int64_t j = 0; j < nb; ++j) applies += (lock && s > 0) ? deg[j] : params->degree;
     sweeps_done = s + 1;
     ctx->w.tmp.alloc(ctx->w.Ya.n);

@@ -123,6 +123,24 @@ __global__ void __launch_bounds__(kT) k_bzfwd(const KDesc<R>* __restrict__ ks, c
 
 // ---------------------------------------------------------------- projection-space combination
 // p_next = a_k (pz - c_k pcur) - b pprev, written over pprev (flat over nk x nq x nb)
+// bf16 (hi, lo) pair of every k-point's Z block: row b of k-point k holds its 2 npw_k reals
+template <typename R>
+__global__ void k_bsplit_z(const KDesc<R>* __restrict__ ks, int64_t nb, const cplx<R>* __restrict__ Z,
+                           const int64_t* __restrict__ zb_off, const int64_t* __restrict__ zb_ld,
+                           __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t kb = blockIdx.y, k = kb / nb, b = kb - k * nb;
+  const KDesc<R>& d = ks[k];
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.npw) return;
+  const float2 v = Z[d.y_off + b * d.npw + j];
+  const int64_t o = zb_off[k] + b * zb_ld[k] + 2 * j;
+  const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi_ = __float2bfloat16_rn(v.y);
+  hi[o] = hr;
+  hi[o + 1] = hi_;
+  lo[o] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
+  lo[o + 1] = __float2bfloat16_rn(v.y - __bfloat162float(hi_));
+}
+
 template <typename R>
 __global__ void k_bcombine(const KDesc<R>* __restrict__ ks, int64_t per_k, int64_t n, const cplx<R>* __restrict__ pz,
                            const cplx<R>* __restrict__ pcur, cplx<R>* pprev, int first) {
@@ -403,6 +421,18 @@ struct chebfi_batch {
   std::map<std::pair<int, int>, int> nitems;
   int grid_per_sm[2][kNumShapes] = {};
   int nsm = 0;
+  // mixed form (form 2): FP32 iterates and FFT, projector products as grouped tensor-core
+  // GEMMs with bf16 (hi, lo) operands; problem tables built on first use
+  bool tc_built = false;
+  SplitBF16Buf zb, sb;                   // bf16 pairs of Z (per k: nb rows of 2 npw_k reals) and of the projection blocks
+  std::vector<int64_t> zb_off, zb_ld;    // per k: first element and row stride of its Z pair
+  DevBuf<int64_t> d_zb_off, d_zb_ld;
+  DevBuf<CUtensorMap> tcmaps;            // [kind][k][A hi, A lo, B hi, B lo]
+  std::vector<TcGroupProb> h_tcprobs;    // [variant][k]
+  DevBuf<TcGroupProb> tcprobs;
+  DevBuf<int2> tcitems[7];
+  int ntcitems[7] = {0, 0, 0, 0, 0, 0, 0};
+  double tcwork[7] = {0, 0, 0, 0, 0, 0, 0};
   // captured filters: (form, degree) -> graph
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   std::map<std::pair<int, int>, int64_t> graph_launches;
@@ -625,6 +655,179 @@ void batch_filter_body(chebfi_batch* bt, int degree, cudaStream_t st) {
   (void)slot;
 }
 
+// ---------------------------------------------------------------- mixed form
+// problem variants of the mixed step, each one problem per k-point
+enum TcVariant : int { TV_PHY0 = 0, TV_PHY = 1, TV_G = 2, TV_M = 3, TV_GNEG = 4, TV_PW0 = 5, TV_PW1 = 6 };
+// tensor-map kinds: (A operand, B operand) of the GEMM class
+enum TcKind : int { TK_PHY = 0, TK_G = 1, TK_M = 2, TK_PW = 3 };
+
+// Operands, tensor maps, problem tables and work items of the mixed form (first use).
+void ensure_tc_batch(chebfi_batch* bt, cudaStream_t st) {
+  if (bt->tc_built) return;
+  const int nk = bt->nk;
+  const int64_t nq = bt->nq, nb = bt->nb;
+  CHEBFI_REQUIRE(nq > 0, CHEBFI_ERR_ARG, "the mixed batch needs projectors");
+  ensure_ws<float>(bt);
+  for (chebfi_ctx* c : bt->ks) ensure_tc_operands(c, st);
+  // Z pairs: per k nb rows of 2 npw_k reals, rows 8-element aligned (TMA's 16-byte rule)
+  bt->zb_off.resize(nk);
+  bt->zb_ld.resize(nk);
+  int64_t tot = 0;
+  for (int k = 0; k < nk; ++k) {
+    bt->zb_ld[k] = (2 * bt->npw[k] + 7) / 8 * 8;
+    bt->zb_off[k] = tot;
+    tot += bt->zb_ld[k] * nb;
+  }
+  bt->zb.alloc((size_t)tot);
+  bt->zb.ld = 0;
+  bt->d_zb_off.upload(bt->zb_off.data(), nk, st);
+  bt->d_zb_ld.upload(bt->zb_ld.data(), nk, st);
+  bt->sb.ld = (2 * nq + 7) / 8 * 8;
+  bt->sb.alloc((size_t)bt->sb.ld * nb * nk);
+  // tensor maps [kind][k][4]
+  std::vector<CUtensorMap> maps((size_t)4 * nk * 4);
+  for (int k = 0; k < nk; ++k) {
+    chebfi_ctx* c = bt->ks[k];
+    const int64_t np2 = 2 * bt->npw[k];
+    const __nv_bfloat16* sbh = bt->sb.hi.p + (int64_t)k * nb * bt->sb.ld;
+    const __nv_bfloat16* sbl = bt->sb.lo.p + (int64_t)k * nb * bt->sb.ld;
+    CUtensorMap* m = maps.data() + ((size_t)TK_PHY * nk + k) * 4;
+    m[0] = tc_map(c->tcA1.hi.p, np2, 2 * nq, c->tcA1.ld);
+    m[1] = tc_map(c->tcA1.lo.p, np2, 2 * nq, c->tcA1.ld);
+    m[2] = tc_map(bt->zb.hi.p + bt->zb_off[k], np2, nb, bt->zb_ld[k]);
+    m[3] = tc_map(bt->zb.lo.p + bt->zb_off[k], np2, nb, bt->zb_ld[k]);
+    m = maps.data() + ((size_t)TK_G * nk + k) * 4;
+    m[0] = tc_map(c->tcAG.hi.p, 2 * nq, 2 * nq, c->tcAG.ld);
+    m[1] = tc_map(c->tcAG.lo.p, 2 * nq, 2 * nq, c->tcAG.ld);
+    m[2] = tc_map(sbh, 2 * nq, nb, bt->sb.ld);
+    m[3] = tc_map(sbl, 2 * nq, nb, bt->sb.ld);
+    m = maps.data() + ((size_t)TK_M * nk + k) * 4;
+    if (bt->paw) {
+      m[0] = tc_map(c->tcAM.hi.p, 2 * nq, 2 * nq, c->tcAM.ld);
+      m[1] = tc_map(c->tcAM.lo.p, 2 * nq, 2 * nq, c->tcAM.ld);
+    } else {
+      m[0] = m[1] = maps[((size_t)TK_G * nk + k) * 4];
+    }
+    m[2] = tc_map(sbh, 2 * nq, nb, bt->sb.ld);
+    m[3] = tc_map(sbl, 2 * nq, nb, bt->sb.ld);
+    m = maps.data() + ((size_t)TK_PW * nk + k) * 4;
+    m[0] = tc_map(c->tcA2.hi.p, 2 * nq, np2, c->tcA2.ld);
+    m[1] = tc_map(c->tcA2.lo.p, 2 * nq, np2, c->tcA2.ld);
+    m[2] = tc_map(sbh, 2 * nq, nb, bt->sb.ld);
+    m[3] = tc_map(sbl, 2 * nq, nb, bt->sb.ld);
+  }
+  bt->tcmaps.upload(maps.data(), maps.size(), st);
+  // problems [variant][k]; the PW alphas (1/r_k) are refreshed every call
+  float2* pa = bt->p32[0].p;
+  float2* pz = bt->p32[2].p;
+  float2* pq = bt->p32[4].p;
+  bt->h_tcprobs.assign((size_t)7 * nk, TcGroupProb{});
+  for (int v = 0; v < 7; ++v) {
+    std::vector<std::pair<int64_t, int>> order;  // (work of one tile, k): longest first
+    for (int k = 0; k < nk; ++k) {
+      TcGroupProb& p = bt->h_tcprobs[(size_t)v * nk + k];
+      const int64_t np2 = 2 * bt->npw[k];
+      float* pzk = (float*)(pz + (int64_t)k * nq * nb);
+      p.N = (int)nb;
+      p.alpha = 1.f;
+      p.beta = 0.f;
+      p.scale_alpha = 0;
+      p.C = nullptr;
+      p.ldc = 2 * nq;
+      p.ldd = 2 * nq;
+      if (v == TV_PHY0 || v == TV_PHY) {
+        p.M = (int)(2 * nq);
+        p.K = (int)np2;
+        p.map = TK_PHY * nk + k;
+        p.D = (float*)((v == TV_PHY0 ? pa : pz) + (int64_t)k * nq * nb);
+      } else if (v == TV_G || v == TV_GNEG || v == TV_M) {
+        p.M = (int)(2 * nq);
+        p.K = (int)(2 * nq);
+        p.map = (v == TV_M ? TK_M : TK_G) * nk + k;
+        if (v == TV_M) {
+          p.D = (float*)(pq + (int64_t)k * nq * nb);
+        } else {
+          p.D = pzk;
+          p.C = pzk;
+          p.beta = 1.f;
+          p.alpha = v == TV_GNEG ? -1.f : 1.f;
+        }
+      } else {
+        float2* Yv = bt->Y32[v == TV_PW0 ? 0 : 1].p + bt->y_off[k];
+        p.M = (int)np2;
+        p.K = (int)(2 * nq);
+        p.map = TK_PW * nk + k;
+        p.D = (float*)Yv;
+        p.C = (const float*)Yv;
+        p.ldd = p.ldc = np2;
+        p.beta = 1.f;
+        p.scale_alpha = 1;
+      }
+      order.emplace_back((int64_t)p.K, k);
+    }
+    std::stable_sort(order.begin(), order.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<int2> items;
+    double work = 0.0;
+    for (const auto& o : order) {
+      const TcGroupProb& p = bt->h_tcprobs[(size_t)v * nk + o.second];
+      const int tiles = ((p.M + 127) / 128) * ((p.N + 127) / 128);
+      for (int t = 0; t < tiles; ++t) items.push_back(make_int2(v * nk + o.second, t));
+      work += 2.0 * p.M * p.N * p.K;
+    }
+    bt->tcitems[v].upload(items.data(), items.size(), st);
+    bt->ntcitems[v] = (int)items.size();
+    bt->tcwork[v] = work;
+  }
+  bt->tcprobs.upload(bt->h_tcprobs.data(), bt->h_tcprobs.size(), st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  bt->tc_built = true;
+}
+
+void tc_group(chebfi_batch* bt, int v, float alpha_mul, cudaStream_t st) {
+  static const char* tags[7] = {"tcb_gemm_PhY", "tcb_gemm_PhY", "tcb_gemm_small", "tcb_gemm_small",
+                                "tcb_gemm_small", "tcb_gemm_PW", "tcb_gemm_PW"};
+  tc_gemm_grouped(bt->tcmaps.p, bt->tcprobs.p, bt->tcitems[v].p, bt->ntcitems[v], alpha_mul, bt->ks[0]->d_status.p, st,
+                  tags[v], bt->tcwork[v]);
+}
+
+// The mixed form of batch_filter_body: the same steps with the projector products as grouped
+// tensor-core GEMMs on bf16 (hi, lo) pairs of the FP32 operands.
+void batch_filter_body_mixed(chebfi_batch* bt, int degree, cudaStream_t st) {
+  using C = float2;
+  const KDesc<float>* d = bt->d32.p;
+  C* Yb[2] = {bt->Y32[0].p, bt->Y32[1].p};
+  C* Z = bt->Z32.p;
+  C *pa = bt->p32[0].p, *pb = bt->p32[1].p, *pz = bt->p32[2].p, *pw = bt->p32[3].p, *pq = bt->p32[4].p;
+  const int64_t nq = bt->nq, nb = bt->nb, nk = bt->nk;
+  const dim3 gg(nblk(*std::max_element(bt->npw.begin(), bt->npw.end())), (unsigned)(nk * nb));
+  CHEBFI_LAUNCH("k_bgather", st, (k_bgather<float><<<gg, 256, 0, st>>>(d, nb, Yb[0])));
+  C *cur = Yb[0], *prev = Yb[1], *pcur = pa, *pprev = pb;
+  CHEBFI_LAUNCH("k_bsplit_z", st, (k_bsplit_z<float><<<gg, 256, 0, st>>>(d, nb, cur, bt->d_zb_off.p, bt->d_zb_ld.p, bt->zb.hi.p, bt->zb.lo.p)));
+  tc_group(bt, TV_PHY0, 1.f, st);  // p_0 = P^H Y_0, into pa
+  for (int k = 0; k < degree; ++k) {
+    const int first = k == 0 ? 1 : 0;
+    blocal_n<float>(bt, cur, Z, prev, first, st);
+    CHEBFI_LAUNCH("k_bsplit_z", st, (k_bsplit_z<float><<<gg, 256, 0, st>>>(d, nb, Z, bt->d_zb_off.p, bt->d_zb_ld.p, bt->zb.hi.p, bt->zb.lo.p)));
+    tc_group(bt, TV_PHY, 1.f, st);                                                                    // P^H Z
+    blockdiag_apply<float>(bt->ks[0], BatchOps<float>::D(bt->ks[0]), pcur, nq, pw, nq, nk * nb, st);  // D p
+    split_block(nq, nk * nb, pw, nq, bt->sb, st);
+    tc_group(bt, TV_G, 1.f, st);                                                                      // + G D p
+    if (bt->paw) {
+      split_block(nq, nk * nb, pz, nq, bt->sb, st);
+      tc_group(bt, TV_M, 1.f, st);                                                // q = M P^H H Y
+      axpby<float>(nq, nk * nb, 1.f, pw, nq, -1.f, pq, nq, pw, nq, st);           // W = D p - q
+      split_block(nq, nk * nb, pq, nq, bt->sb, st);
+      tc_group(bt, TV_GNEG, 1.f, st);                                             // P^H S^{-1} H Y
+    }
+    split_block(nq, nk * nb, pw, nq, bt->sb, st);
+    tc_group(bt, prev == Yb[0] ? TV_PW0 : TV_PW1, first ? 1.f : 2.f, st);       // Y_{k+1} = T + a P W
+    CHEBFI_LAUNCH("k_bcombine", st, (k_bcombine<float><<<nblk(nk * nq * nb), 256, 0, st>>>(d, nq * nb, nk * nq * nb, pz, pcur, pprev, first)));
+    std::swap(cur, prev);
+    std::swap(pcur, pprev);
+  }
+  CHEBFI_LAUNCH("k_bscatter", st, (k_bscatter<float><<<gg, 256, 0, st>>>(d, nb, cur)));
+}
+
 // Time every tile shape of every GEMM class on the batch's own problems; keep the fastest.
 template <typename R>
 void autotune(chebfi_batch* bt, cudaStream_t st) {
@@ -713,11 +916,13 @@ void autotune(chebfi_batch* bt, cudaStream_t st) {
   cudaEventDestroy(b);
 }
 
+// mixed: the FP32 form with the projector products on the tensor cores (R = float only)
 template <typename R>
 void batch_filter(chebfi_batch* bt, void* const* Y, const int64_t* ld, int degree, const double* lo, const double* hi,
-                  cudaStream_t st) {
-  const int f = BatchOps<R>::form;
-  autotune<R>(bt, st);
+                  cudaStream_t st, bool mixed = false) {
+  const int f = mixed ? 2 : BatchOps<R>::form;
+  if (mixed) ensure_tc_batch(bt, st);
+  else autotune<R>(bt, st);
   ensure_ws<R>(bt);
   set_fft_smem_n<R>(bt);
   fk::init_twiddles();
@@ -731,6 +936,13 @@ void batch_filter(chebfi_batch* bt, void* const* Y, const int64_t* ld, int degre
   }
   // pageable source: the copy is staged before cudaMemcpyAsync returns
   CHEBFI_CUDA(cudaMemcpyAsync(BatchOps<R>::desc(bt).p, h.data(), sizeof(KDesc<R>) * h.size(), cudaMemcpyHostToDevice, st));
+  if (mixed) {  // alpha of Y_{k+1} = T + alpha P W is 1/r_k (times 2 after the first step)
+    const int nk = bt->nk;
+    for (int v = TV_PW0; v <= TV_PW1; ++v)
+      for (int k = 0; k < nk; ++k) bt->h_tcprobs[(size_t)v * nk + k].alpha = (float)(1.0 / (double)h[k].r);
+    CHEBFI_CUDA(cudaMemcpyAsync(bt->tcprobs.p + (size_t)TV_PW0 * nk, bt->h_tcprobs.data() + (size_t)TV_PW0 * nk,
+                                sizeof(TcGroupProb) * 2 * nk, cudaMemcpyHostToDevice, st));
+  }
   const auto key = std::make_pair(f, degree);
   auto itg = bt->graphs.find(key);
   if (itg == bt->graphs.end()) {
@@ -743,7 +955,8 @@ void batch_filter(chebfi_batch* bt, void* const* Y, const int64_t* ld, int degre
     cudaGraph_t graph = nullptr;
     CHEBFI_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
     try {
-      batch_filter_body<R>(bt, degree, bt->cap);
+      if (mixed) batch_filter_body_mixed(bt, degree, bt->cap);
+      else batch_filter_body<R>(bt, degree, bt->cap);
     } catch (...) {
       cudaStreamEndCapture(bt->cap, &graph);
       if (graph) cudaGraphDestroy(graph);
@@ -911,7 +1124,9 @@ int64_t chebfi_batch_kernel_launches(const chebfi_batch* bt) { return bt ? bt->l
 
 int chebfi_batch_autotune(chebfi_batch* bt, int prec, int* shapes, double* ms) {
   BAPI_BEGIN(bt)
-  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32, CHEBFI_ERR_ARG, "the batch runs the FP64 or FP32 form");
+  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32 || prec == CHEBFI_MIXED, CHEBFI_ERR_ARG,
+                 "the batch runs the FP64, FP32 or mixed form");
+  CHEBFI_REQUIRE(prec != CHEBFI_MIXED || bt->nq > 0, CHEBFI_ERR_ARG, "the mixed batch needs projectors");
   const int f = prec == CHEBFI_F64 ? 0 : 1;
   if (prec == CHEBFI_F64) autotune<double>(bt, 0);
   else autotune<float>(bt, 0);
@@ -929,7 +1144,9 @@ int chebfi_batch_autotune(chebfi_batch* bt, int prec, int* shapes, double* ms) {
 
 int chebfi_batch_set_tiles(chebfi_batch* bt, int prec, const int* shapes, int split) {
   BAPI_BEGIN(bt)
-  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32, CHEBFI_ERR_ARG, "the batch runs the FP64 or FP32 form");
+  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32 || prec == CHEBFI_MIXED, CHEBFI_ERR_ARG,
+                 "the batch runs the FP64, FP32 or mixed form");
+  CHEBFI_REQUIRE(prec != CHEBFI_MIXED || bt->nq > 0, CHEBFI_ERR_ARG, "the mixed batch needs projectors");
   CHEBFI_REQUIRE(shapes, CHEBFI_ERR_ARG, "null shapes");
   for (int gc = 0; gc < GC_N; ++gc)
     CHEBFI_REQUIRE(shapes[gc] >= 0 && shapes[gc] < kNumShapes, CHEBFI_ERR_ARG, "tile shape index out of range");
@@ -958,7 +1175,9 @@ int chebfi_batch_cheb_filter(chebfi_batch* bt, void* const* Y, const int64_t* ld
   BAPI_BEGIN(bt)
   CHEBFI_REQUIRE(Y && ld && lambda_lo && lambda_hi, CHEBFI_ERR_ARG, "null argument");
   CHEBFI_REQUIRE(degree >= 0 && degree <= 1000, CHEBFI_ERR_ARG, "degree out of range");
-  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32, CHEBFI_ERR_ARG, "the batch runs the FP64 or FP32 form");
+  CHEBFI_REQUIRE(prec == CHEBFI_F64 || prec == CHEBFI_F32 || prec == CHEBFI_MIXED, CHEBFI_ERR_ARG,
+                 "the batch runs the FP64, FP32 or mixed form");
+  CHEBFI_REQUIRE(prec != CHEBFI_MIXED || bt->nq > 0, CHEBFI_ERR_ARG, "the mixed batch needs projectors");
   for (int k = 0; k < bt->nk; ++k) {
     CHEBFI_REQUIRE(Y[k] && ld[k] >= bt->npw[k], CHEBFI_ERR_ARG, "bad block of k-point " + std::to_string(k));
     CHEBFI_REQUIRE(std::isfinite(lambda_lo[k]) && std::isfinite(lambda_hi[k]) && lambda_hi[k] > lambda_lo[k],
@@ -967,7 +1186,7 @@ int chebfi_batch_cheb_filter(chebfi_batch* bt, void* const* Y, const int64_t* ld
   if (degree == 0) return CHEBFI_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (prec == CHEBFI_F64) batch_filter<double>(bt, Y, ld, degree, lambda_lo, lambda_hi, st);
-  else batch_filter<float>(bt, Y, ld, degree, lambda_lo, lambda_hi, st);
+  else batch_filter<float>(bt, Y, ld, degree, lambda_lo, lambda_hi, st, prec == CHEBFI_MIXED);
   BAPI_END(bt)
 }
 

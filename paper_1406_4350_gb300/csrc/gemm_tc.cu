@@ -240,6 +240,176 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// Grouped form for many independent problems of different sizes (the batched k-points):
+// work item i = (problem, output tile), CTA b taking items b, b + gridDim.x, ... (ordered by
+// the caller, longest contraction first).  The four bf16 tensor maps of each problem (A hi,
+// A lo, B hi, B lo) live in a device table, written before the launch; the pipeline is
+// k_tc_gemm's (TMA warp, MMA warp, four epilogue warps, chunked TMEM accumulation).
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gemm_grouped(const CUtensorMap* __restrict__ maps, const TcGroupProb* __restrict__ probs,
+                      const int2* __restrict__ items, int nitems, float alpha_mul, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + NACC;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + NACC);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < NACC; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nitems && ok; u += gridDim.x) {
+        const int2 it = items[u];
+        const TcGroupProb& p = probs[it.x];
+        const CUtensorMap* mp = maps + 4 * p.map;
+        const int tiles_n = (p.N + BN - 1) / BN;
+        const int n0 = (it.y % tiles_n) * BN, m0 = (it.y / tiles_n) * BM;
+        const int num_k = (p.K + BK - 1) / BK;
+        for (int kt = 0; kt < num_k; ++kt, ++g) {
+          const int s = g % STAGES;
+          const uint32_t par = (g / STAGES) & 1;
+          if (g >= STAGES && !mbar_wait(&empty[s], par ^ 1)) {
+            flag(status, CHEBFI_ERR_CUDA);
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          const int x = kt * BK;
+          tma_load_2d(st, mp + 0, x, m0, &full[s]);
+          tma_load_2d(st + A_BYTES, mp + 1, x, m0, &full[s]);
+          tma_load_2d(st + 2 * A_BYTES, mp + 2, x, n0, &full[s]);
+          tma_load_2d(st + 2 * A_BYTES + B_BYTES, mp + 3, x, n0, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+      bool ok = true;
+      int g = 0, gch = 0;
+      for (int u = blockIdx.x; u < nitems && ok; u += gridDim.x) {
+        const TcGroupProb& p = probs[items[u].x];
+        const int num_k = (p.K + BK - 1) / BK;
+        const int num_chunks = (num_k + CHUNK - 1) / CHUNK;
+        int kt = 0;
+        for (int ch = 0; ch < num_chunks && ok; ++ch, ++gch) {
+          const int acc = gch % NACC;
+          if (gch >= NACC && !mbar_wait(&acc_empty[acc], ((gch / NACC) - 1) & 1)) {
+            flag(status, CHEBFI_ERR_CUDA);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(acc * BN);
+          const int kend = min(num_k, (ch + 1) * CHUNK);
+          for (; kt < kend; ++kt, ++g) {
+            const int s = g % STAGES;
+            const uint32_t par = (g / STAGES) & 1;
+            if (!mbar_wait(&full[s], par)) {
+              flag(status, CHEBFI_ERR_CUDA);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+            const bool first = kt == ch * CHUNK;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t off = kk * 32;
+              const uint64_t ah = sw128_desc(base + off), al = sw128_desc(base + A_BYTES + off);
+              const uint64_t bh = sw128_desc(base + 2 * A_BYTES + off),
+                             bl = sw128_desc(base + 2 * A_BYTES + B_BYTES + off);
+              mma_bf16(d, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
+              mma_bf16(d, ah, bl, idesc, 1);
+              mma_bf16(d, al, bh, idesc, 1);
+            }
+            mma_commit(&empty[s]);
+          }
+          mma_commit(&acc_full[acc]);
+        }
+      }
+    }
+  } else {
+    const int lane_base = 32 * (warp % 4);
+    bool ok = true;
+    int gch = 0;
+    for (int u = blockIdx.x; u < nitems && ok; u += gridDim.x) {
+      const int2 it = items[u];
+      const TcGroupProb& p = probs[it.x];
+      const int tiles_n = (p.N + BN - 1) / BN;
+      const int n0 = (it.y % tiles_n) * BN, m0 = (it.y / tiles_n) * BM;
+      const int num_chunks = ((p.K + BK - 1) / BK + CHUNK - 1) / CHUNK;
+      const int m = m0 + lane_base + lane;
+      float racc[BN];
+#pragma unroll
+      for (int j = 0; j < BN; ++j) racc[j] = 0.f;
+      for (int ch = 0; ch < num_chunks; ++ch, ++gch) {
+        const int acc = gch % NACC;
+        if (!mbar_wait(&acc_full[acc], (gch / NACC) & 1)) {
+          flag(status, CHEBFI_ERR_CUDA);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < BN; c += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(acc * BN + c), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) racc[c + j] += v[j];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      }
+      if (ok && m < p.M) {
+        const int nvalid = min(BN, p.N - n0);
+        const float alpha = p.alpha * (p.scale_alpha ? alpha_mul : 1.f);
+        if (p.beta != 0.f) {
+          const float* c = p.C + (int64_t)m + (int64_t)n0 * p.ldc;
+#pragma unroll
+          for (int j = 0; j < BN; ++j)
+            if (j < nvalid) racc[j] = fmaf(p.beta, c[(int64_t)j * p.ldc], alpha * racc[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < BN; ++j) racc[j] *= alpha;
+        }
+        float* dd = p.D + (int64_t)m + (int64_t)n0 * p.ldd;
+#pragma unroll
+        for (int j = 0; j < BN; ++j)
+          if (j < nvalid) dd[(int64_t)j * p.ldd] = racc[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
 // D = alpha * (sum of the K-split partial sums, in split order) + beta * C; C may be D
 // (M x N <= 2^26 in split mode, so 32-bit indices; one thread per 4 consecutive rows)
 __global__ void k_tc_reduce(int M, int N, int splits, const float* __restrict__ ws, float alpha, float beta,
@@ -364,6 +534,23 @@ void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64
     const int64_t n4 = (M * N + 3) / 4;
     CHEBFI_LAUNCH("k_tc_reduce", st, tc::k_tc_reduce<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>((int)M, (int)N, splits, a.ws, alpha, beta, C, ldc, D, ldd));
   }
+}
+
+CUtensorMap tc_map(const __nv_bfloat16* base, int64_t k, int64_t rows, int64_t ld) {
+  return tc::make_map(base, k, rows, ld, tc::BM);
+}
+
+void tc_gemm_grouped(const CUtensorMap* maps, const TcGroupProb* probs, const int2* items, int nitems, float alpha_mul,
+                     int* status, cudaStream_t st, const char* tag, double work) {
+  if (nitems <= 0) return;
+  CHEBFI_CUDA(cudaFuncSetAttribute(tc::k_tc_gemm_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  int dev = 0, sms = 0;
+  CHEBFI_CUDA(cudaGetDevice(&dev));
+  CHEBFI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)std::min(nitems, sms);
+  CHEBFI_LAUNCH_W(tag, st, work,
+                  tc::k_tc_gemm_grouped<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(maps, probs, items, nitems, alpha_mul,
+                                                                                 status));
 }
 
 }  // namespace chebfi

@@ -124,6 +124,20 @@ struct SplitBF16Buf {
   SplitBF16 view() const { return SplitBF16{hi.p, lo.p, ld}; }
 };
 
+// One problem of a grouped tensor-core GEMM (gemm_tc.cu): D = alpha' A B + beta C with FP32
+// column-major C / D, A and B given by the four bf16 tensor maps maps[4 map .. 4 map + 3]
+// (A hi, A lo, B hi, B lo; boxes of 128 rows); alpha' = alpha, times the launch's alpha_mul
+// when scale_alpha is set.
+struct TcGroupProb {
+  int M, N, K, map;
+  float alpha, beta;
+  int scale_alpha, pad;
+  float* D;
+  int64_t ldd;
+  const float* C;
+  int64_t ldc;
+};
+
 // Residues of a real-embedded complex operand for the modular tensor-core GEMM (ozaki.cu):
 // one K-major bf16 matrix per modulus, res[mod * mstride + row * ld + k], and per complex
 // row the power of two s applied before rounding to integers.
@@ -189,6 +203,7 @@ struct Work {
   DevBuf<double2> Ya, Yb, Yc, Z, HY, T1, T2, tmp, tmp2;   // FP64 (npw x nb or grid)
   DevBuf<float2> fYa, fYb, fZ, fT1, fT2, ftmp;            // FP32 filter iterates
   DevBuf<double2> pa, pb, pc, pz, pw, pq, pt;             // nproj x nb projections (FP64)
+  const double2* pc_of = nullptr;  // the block whose P^H Y is held in pc (set by Rayleigh-Ritz)
   DevBuf<float2> fpa, fpb, fpz, fpw, fpq, fpt;            // FP32 projections
   DevBuf<double2> small1, small2, small3, small4, small5;  // nb x nb
   // refined eigensolver: FP32 first stage, FP64 refinement matrices, stats, cluster pairs

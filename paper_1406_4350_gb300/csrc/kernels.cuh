@@ -2,6 +2,7 @@
 // blas.cu, dense.cu).  All matrices are column-major; complex values interleaved.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -62,6 +63,16 @@ void gemm(bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha,
 void tc_gemm(const SplitBF16& A, const SplitBF16& B, int64_t M, int64_t N, int64_t K, float alpha, float beta,
              const float* C, int64_t ldc, float* D, int64_t ldd, int* status, cudaStream_t st, const char* tag,
              DevBuf<float>* ws = nullptr);
+// Grouped form: items (problem, output tile of 128 x 128) over problems whose tensor maps
+// and sizes sit in device tables; CTA b takes items b, b + grid, ...  work: the algorithmic
+// flops of all items, for the profiler.
+void tc_gemm_grouped(const CUtensorMap* maps, const TcGroupProb* probs, const int2* items, int nitems, float alpha_mul,
+                     int* status, cudaStream_t st, const char* tag, double work);
+// the bf16 (hi, lo) real embeddings of P^H, P, G and M of a context, built on first use
+void ensure_tc_operands(chebfi_ctx* ctx, cudaStream_t st);
+// bf16 tensor map of a K-major operand (k reals per row, `rows` rows, row stride ld) with the
+// boxes of the tensor-core GEMMs
+CUtensorMap tc_map(const __nv_bfloat16* base, int64_t k, int64_t rows, int64_t ld);
 // Real embeddings (bf16 pairs) of complex operators applied to interleaved complex data:
 // embed_ph: the (2 nq) x (2 npw) matrix of x -> P^H x;  embed_n: the (2m) x (2k) matrix of x -> A x.
 void embed_ph(int64_t npw, int64_t nq, const double2* P, int64_t ldp, SplitBF16Buf& out, cudaStream_t st);

@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-11  # the FP64 parity tolerance of the single-problem tests
 TOL32 = 2e-5   # the FP32 one
+TOLMIX = 1e-4  # the mixed one, per filter step
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -46,7 +47,7 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("prec, tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("prec, tol", [(0, TOL64), (1, TOL32), (2, TOLMIX * 6)])
 def test_batch_filter_matches_oracle_per_kpoint(prec, tol):
     from paper_1406_4350_gb300.chebfi import fortran
     cells = _small()
@@ -145,7 +146,7 @@ def test_batch_rejects_incompatible_contexts():
     with pytest.raises(ChebFIError):
         bt.cheb_filter(Ys, 2, [1.0, 1.0], [0.0, 2.0], prec=1)  # lambda_hi <= lambda_lo at k = 0
     with pytest.raises(ChebFIError):
-        bt.cheb_filter(Ys, 2, [0.0, 0.0], [1.0, 1.0], prec=2)  # no mixed form in the batch
+        bt.cheb_filter(Ys, 2, [0.0, 0.0], [1.0, 1.0], prec=3)  # no such form
 
 
 def test_batch_kpoint_workload_sampled():
@@ -163,8 +164,43 @@ def test_batch_kpoint_workload_sampled():
     hi = [40.0] * len(cells)
     Ys = [fortran(c.Y0) for c in cells]
     bt.cheb_filter(Ys, 8, lo, hi, prec=1)
+    Ym = [fortran(cells[i].Y0) if i in picks else Y.clone() for i, Y in enumerate(Ys)]
+    bt.cheb_filter(Ym, 8, lo, hi, prec=2)
     torch.cuda.synchronize()
     for i in picks:
         c = cells[i]
         ref = ch.filter_reuse(PWOperator.from_cell(c), c.Y0, 8, lo[i], hi[i])
         assert _rel(Ys[i].cpu().numpy(), ref) <= 1e-4
+        assert _rel(Ym[i].cpu().numpy(), ref) <= TOLMIX * 8
+
+
+@pytest.mark.parametrize("paw", [True, False])
+def test_batch_mixed_replay_ragged_band_tiles(paw):
+    """Mixed form: 136 bands (a full and a ragged 128-band tile of the grouped tensor-core
+    GEMMs), spheres of several 512-real chunks, PAW and norm-conserving; the second call
+    replays the graph with new blocks and intervals (the 1/r_k of P W is refreshed)."""
+    from paper_1406_4350_gb300.chebfi import fortran
+    cells = kpoint_cells(nk=3, nbands=136, seed=1210, npw_range=(400, 1100), L=8.0, grid=24, natoms=3)
+    if not paw:
+        cells = [dataclasses.replace(c, Q=None) for c in cells]
+    lo, hi = _intervals(cells)
+    bt = _batch(cells)
+    deg = 5
+    Ys = [fortran(c.Y0) for c in cells]
+    bt.cheb_filter(Ys, deg, lo, hi, prec=2)
+    torch.cuda.synchronize()
+    n1 = bt.kernel_launches
+    for c, Y, l, h in zip(cells, Ys, lo, hi):
+        ref = ch.filter_plain(PWOperator.from_cell(c), c.Y0, deg, l, h)
+        assert _rel(Y.cpu().numpy(), ref) <= TOLMIX * deg
+    rng = np.random.default_rng(5)
+    Y2 = [np.asfortranarray(rng.normal(size=c.Y0.shape) + 1j * rng.normal(size=c.Y0.shape)) for c in cells]
+    lo2 = [l - 0.2 for l in lo]
+    hi2 = [h + 2.0 for h in hi]
+    second = [fortran(y) for y in Y2]
+    bt.cheb_filter(second, deg, lo2, hi2, prec=2)
+    torch.cuda.synchronize()
+    assert bt.kernel_launches == 2 * n1 > 0
+    for c, Y, y0, l, h in zip(cells, second, Y2, lo2, hi2):
+        ref = ch.filter_plain(PWOperator.from_cell(c), y0, deg, l, h)
+        assert _rel(Y.cpu().numpy(), ref) <= TOLMIX * deg
