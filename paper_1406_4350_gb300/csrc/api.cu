@@ -1218,21 +1218,17 @@ int chebfi_set_sphere(chebfi_ctx* ctx, int64_t npw, const int32_t* miller) {
     if (xact[x]) rows_nat.push_back(r * s.pitch);
   }
   s.nxa = (int)rows.size();
-  // for the pruned plane pass: which column sits at (active row a, natural y), and which
-  // slots are active
+  // for the pruned plane pass: the slot range [act_lo, act_lo + nact) covering the active
+  // rows, and which column sits at (row act_lo + a, natural y)
   {
-    std::vector<int32_t> slot_to_a(n1, -1), row_col((size_t)s.nxa * n2, -1);
-    for (int a = 0; a < s.nxa; ++a) slot_to_a[rows_nat[a] / s.pitch] = a;
+    s.act_lo = rows_nat.front() / s.pitch;
+    s.nact = rows_nat.back() / s.pitch - s.act_lo + 1;
+    std::vector<int32_t> row_col((size_t)s.nact * n2, -1);
     for (int c = 0; c < s.ncol; ++c) {
       const int slot = col_nat[c] / s.pitch, y = col_nat[c] % s.pitch;
-      row_col[(size_t)slot_to_a[slot] * n2 + y] = c;
+      row_col[(size_t)(slot - s.act_lo) * n2 + y] = c;
     }
     s.row_col.upload(row_col.data(), row_col.size());
-    for (int w = 0; w < 4; ++w) s.act_mask[w] = 0;
-    for (int a = 0; a < s.nxa; ++a) {
-      const int slot = rows_nat[a] / s.pitch;
-      if (slot < 256) s.act_mask[slot >> 6] |= 1ull << (slot & 63);
-    }
   }
   s.col_start.upload(col_start.data(), col_start.size());
   s.pw_line.upload(pw_line.data(), npw);

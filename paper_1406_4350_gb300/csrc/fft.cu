@@ -290,10 +290,12 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   fa.col_off = s.col_off_nat.p;
   fa.row_off = s.rows_nat.p;
   fa.row_col = s.row_col.p;
-  for (int w = 0; w < 4; ++w) fa.act[w] = s.act_mask[w];
-  // ceil(2^32 / nxa): exact quotients t / nxa for t < 2^32 / nxa (the row passes use t < 2^12)
-  fa.nl_magic = s.nxa > 1 ? (unsigned)(((1ull << 32) + s.nxa - 1) / (unsigned long long)s.nxa) : 0u;
-  CHEBFI_REQUIRE(s.nxa >= 1, CHEBFI_ERR_STATE, "sphere without columns");
+  fa.act_lo = s.act_lo;
+  fa.nact = s.nact;
+  // ceil(2^32 / nact): exact quotients t / nact for t < 2^32 / nact (the row passes use t < 2^12)
+  fa.nl_magic = s.nact > 1 ? (unsigned)(((1ull << 32) + s.nact - 1) / (unsigned long long)s.nact) : 0u;
+  CHEBFI_REQUIRE(s.nxa >= 1 && s.nact >= 1, CHEBFI_ERR_STATE, "sphere without columns");
+  CHEBFI_REQUIRE(s.pitch == N + 1, CHEBFI_ERR_STATE, "plane pitch of the compile-time path");
   const cplx<R>* tw = sizeof(R) == 8 ? (const cplx<R>*)ctx->ax[0].tw64.p : (const cplx<R>*)ctx->ax[0].tw32.p;
   const R* Vs = sizeof(R) == 8 ? (const R*)ctx->d_vs.p : (const R*)ctx->d_vsf.p;
   const size_t zbytes = (size_t)(N + kCBF * s.zpitch) * sizeof(cplx<R>);

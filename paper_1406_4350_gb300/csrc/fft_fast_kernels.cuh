@@ -32,9 +32,9 @@ struct FastArgs {
   const int32_t* pw_z;      // natural z of each sorted sphere point
   const int32_t* col_off;   // slot(x) * pitch + y of each column (plane rows cyclically shifted)
   const int32_t* row_off;   // slot(x) * pitch of each active x
-  const int32_t* row_col = nullptr;            // (active row, natural y) -> column, or -1
-  unsigned long long act[4] = {0, 0, 0, 0};    // active slots (pruned plane pass)
-  unsigned nl_magic = 0;                       // t / nxa == umulhi(t, nl_magic) for t < 2^16
+  const int32_t* row_col = nullptr;            // (row act_lo + a, natural y) -> column, or -1
+  int act_lo = 0, nact = 0;                    // slot range of the pruned plane pass
+  unsigned nl_magic = 0;                       // t / nact == umulhi(t, nl_magic) for t < 2^16
 };
 
 template <typename R, int N>
@@ -168,26 +168,25 @@ __device__ __forceinline__ void plane_body(cplx<R>* __restrict__ T, const R* __r
 
 // The plane pass of plane_body with its zero rows pruned and its scatter / gather fused:
 // the first y pass reads the sphere columns straight from the column buffer (no zeroed
-// plane, no scatter), the x passes skip the loads of rows that hold no column (they are
-// zero) and the stores of rows no later pass reads, and the last y pass stores the columns
-// straight to the column buffer (no gather).  Same arithmetic, in the same order.
+// plane, no scatter), the x passes skip the loads of rows outside the active slot range
+// [act_lo, act_lo + nact) (they are zero) and the stores of rows no later pass reads, and
+// the last y pass stores the columns straight to the column buffer (no gather).  Same
+// arithmetic, in the same order.  The row pitch is the compile-time N + 1 (odd: the
+// row-wise passes meet no bank conflicts), so every shared-memory offset of a pass is an
+// immediate; where NB warps tile the block (N = 64, 96) each warp of an x pass keeps one nb
+// and its twiddles in registers.
 template <typename R, int N>
 __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const R* __restrict__ Vs,
                                                   const FastArgs& fa, int z, int64_t b, unsigned char* smem_raw) {
   using C = cplx<R>;
-  constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB;
+  constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB, P = N + 1;
+  constexpr bool kWarpNb = N % 32 == 0 && NB * 32 == kThreadsF;
   const ConstTw<R, N> tw;
   C* plane = reinterpret_cast<C*>(smem_raw) + N;
   const C zero = cmake<C>(0.0, 0.0);
   C* t = T + b * fa.ldt + (int64_t)z * fa.ncolp;
-  const int nl = fa.nxa;
-  const unsigned long long m0 = fa.act[0], m1 = fa.act[1], m2 = fa.act[2], m3 = fa.act[3];
-  auto active = [=](int slot) {
-    const unsigned long long w = slot < 64 ? m0 : slot < 128 ? m1 : slot < 192 ? m2 : m3;
-    return ((w >> (slot & 63)) & 1ull) != 0;
-  };
-  LineMap rows;
-  rows.off = fa.row_off;
+  const int nl = fa.nact, lo = fa.act_lo;
+  C* rows = plane + lo * P;  // row a of the active range
   // y, inverse: F's pass A on the active rows, its inputs read from the column buffer;
   // consecutive threads take consecutive y of one row, so they read consecutive columns
   {
@@ -199,7 +198,7 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
     for (int ka = 1; ka < NA; ++ka) w[ka] = fast::twN<+1>(tw, nb * ka);
     for (int it = threadIdx.x; it < nl * NB; it += blockDim.x) {
       const int a = it / NB;
-      C* row = plane + fa.row_off[a] + nb;
+      C* row = rows + a * P + nb;
       const int32_t* rc = fa.row_col + a * N + nb;
       C v[NA];
 #pragma unroll
@@ -218,7 +217,7 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
   // pitch apart: no bank conflicts); ka = t / nl by the multiplier of fa.nl_magic
   for (int it = threadIdx.x; it < nl * NA; it += blockDim.x) {
     const int ka = nl == 1 ? it : (int)__umulhi((unsigned)it, fa.nl_magic), a = it - ka * nl;
-    C* g = plane + fa.row_off[a] + NB * ka;
+    C* g = rows + a * P + NB * ka;
     C u[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) u[q] = g[q];
@@ -227,16 +226,34 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
     for (int q = 0; q < NB; ++q) g[q] = u[q];
   }
   __syncthreads();
-  // x, inverse: F's pass A on every y line, rows without columns are zero
-  for (int it = threadIdx.x; it < N * NB; it += blockDim.x) {
-    const int nb = it / N, yy = it - nb * N;
-    C* a = plane + yy + nb * fa.pitch;
-    C v[NA];
+  // x, inverse: F's pass A on every y line, slots outside the active range are zero
+  if constexpr (kWarpNb) {
+    const int nb = threadIdx.x / 32, d = nb - lo;
+    C w[NA];
 #pragma unroll
-    for (int na = 0; na < NA; ++na) v[na] = active(NB * na + nb) ? a[NB * na * fa.pitch] : zero;
-    fast::dft<NA, +1>(v);
+    for (int ka = 1; ka < NA; ++ka) w[ka] = fast::twN<+1>(tw, nb * ka);
+#pragma unroll 1
+    for (int yy = threadIdx.x % 32; yy < N; yy += 32) {
+      C* a = plane + yy + nb * P;
+      C v[NA];
 #pragma unroll
-    for (int ka = 0; ka < NA; ++ka) a[NB * ka * fa.pitch] = ka == 0 ? v[0] : v[ka] * fast::twN<+1>(tw, nb * ka);
+      for (int na = 0; na < NA; ++na) v[na] = (unsigned)(d + NB * na) < (unsigned)nl ? a[NB * na * P] : zero;
+      fast::dft<NA, +1>(v);
+      a[0] = v[0];
+#pragma unroll
+      for (int ka = 1; ka < NA; ++ka) a[NB * ka * P] = v[ka] * w[ka];
+    }
+  } else {
+    for (int it = threadIdx.x; it < N * NB; it += blockDim.x) {
+      const int nb = it / N, yy = it - nb * N, d = nb - lo;
+      C* a = plane + yy + nb * P;
+      C v[NA];
+#pragma unroll
+      for (int na = 0; na < NA; ++na) v[na] = (unsigned)(d + NB * na) < (unsigned)nl ? a[NB * na * P] : zero;
+      fast::dft<NA, +1>(v);
+#pragma unroll
+      for (int ka = 0; ka < NA; ++ka) a[NB * ka * P] = ka == 0 ? v[0] : v[ka] * fast::twN<+1>(tw, nb * ka);
+    }
   }
   __syncthreads();
   {
@@ -244,11 +261,11 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
     const R* v = Vs + (int64_t)z * N * N;
     for (int it = threadIdx.x; it < N * NA; it += blockDim.x) {
       const int ka = it / N, yy = it - ka * N;
-      C* a = plane + yy + NB * ka * fa.pitch;
+      C* a = plane + yy + NB * ka * P;
       const R* vv = v + (NB * ka) * N + yy;
       C u[NB];
 #pragma unroll
-      for (int nb = 0; nb < NB; ++nb) u[nb] = a[nb * fa.pitch];
+      for (int nb = 0; nb < NB; ++nb) u[nb] = a[nb * P];
       fast::dft<NB, +1>(u);
 #pragma unroll
       for (int kb = 0; kb < NB; ++kb) {
@@ -259,27 +276,42 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
       fast::dft<NB, -1>(u);
 #pragma unroll
       for (int nb = 0; nb < NB; ++nb)
-        a[nb * fa.pitch] = (ka == 0 || nb == 0) ? u[nb] : u[nb] * fast::twN<-1>(tw, nb * ka);
+        a[nb * P] = (ka == 0 || nb == 0) ? u[nb] : u[nb] * fast::twN<-1>(tw, nb * ka);
     }
   }
   __syncthreads();
   // x, forward: G's pass A, storing only the rows the y pass reads
-  for (int it = threadIdx.x; it < N * NB; it += blockDim.x) {
-    const int nb = it / N, yy = it - nb * N;
-    C* a = plane + yy + nb * fa.pitch;
-    C v[NA];
+  if constexpr (kWarpNb) {
+    const int nb = threadIdx.x / 32, d = nb - lo;
+#pragma unroll 1
+    for (int yy = threadIdx.x % 32; yy < N; yy += 32) {
+      C* a = plane + yy + nb * P;
+      C v[NA];
 #pragma unroll
-    for (int ka = 0; ka < NA; ++ka) v[ka] = a[NB * ka * fa.pitch];
-    fast::dft<NA, -1>(v);
+      for (int ka = 0; ka < NA; ++ka) v[ka] = a[NB * ka * P];
+      fast::dft<NA, -1>(v);
 #pragma unroll
-    for (int na = 0; na < NA; ++na)
-      if (active(NB * na + nb)) a[NB * na * fa.pitch] = v[na];
+      for (int na = 0; na < NA; ++na)
+        if ((unsigned)(d + NB * na) < (unsigned)nl) a[NB * na * P] = v[na];
+    }
+  } else {
+    for (int it = threadIdx.x; it < N * NB; it += blockDim.x) {
+      const int nb = it / N, yy = it - nb * N, d = nb - lo;
+      C* a = plane + yy + nb * P;
+      C v[NA];
+#pragma unroll
+      for (int ka = 0; ka < NA; ++ka) v[ka] = a[NB * ka * P];
+      fast::dft<NA, -1>(v);
+#pragma unroll
+      for (int na = 0; na < NA; ++na)
+        if ((unsigned)(d + NB * na) < (unsigned)nl) a[NB * na * P] = v[na];
+    }
   }
   __syncthreads();
   // y, forward: G's pass B, then G's pass A storing the columns to the column buffer
   for (int it = threadIdx.x; it < nl * NA; it += blockDim.x) {
     const int ka = nl == 1 ? it : (int)__umulhi((unsigned)it, fa.nl_magic), a = it - ka * nl;
-    C* g = plane + fa.row_off[a] + NB * ka;
+    C* g = rows + a * P + NB * ka;
     C u[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) u[q] = g[q];
@@ -290,7 +322,7 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
   __syncthreads();
   for (int it = threadIdx.x; it < nl * NB; it += blockDim.x) {
     const int a = it / NB, nb = it - a * NB;  // consecutive columns per warp, as above
-    const C* row = plane + fa.row_off[a] + nb;
+    const C* row = rows + a * P + nb;
     const int32_t* rc = fa.row_col + a * N + nb;
     C v[NA];
 #pragma unroll

@@ -194,8 +194,10 @@ struct SphereFFT {
   DevBuf<int32_t> pw_z;        // sorted sphere point -> z
   DevBuf<int32_t> col_off_nat; // column -> slot(x) * pitch + y, slot(x) = (x + n1/2) mod n1
   DevBuf<int32_t> rows_nat;    // slot(x) * pitch of the active rows, consecutive slots
-  DevBuf<int32_t> row_col;     // active row a, natural y -> column index, or -1 (nxa x n2)
-  unsigned long long act_mask[4] = {0, 0, 0, 0};  // bit slot(x) set for the active rows
+  // the pruned plane pass works on the slot range [act_lo, act_lo + nact) that covers every
+  // active row (for a sphere the active rows are that range)
+  int act_lo = 0, nact = 0;
+  DevBuf<int32_t> row_col;     // row act_lo + a, natural y -> column index, or -1 (nact x n2)
 };
 
 // Workspace grown on demand (never shrinks while the context lives).
