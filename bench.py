@@ -340,6 +340,39 @@ def run_extra(args):
                 "unit": "TFLOP/s", "value": out["tensor"]["tflops_fp64_equivalent"], "dtype": "f64",
                 "steps": args.steps, "config": {"workload": "C = A^H B, m = %d, n = %d, k = %d, 14 moduli" % (m, n, k)},
                 "engines": out, "max_rel_diff": diff}
+    elif args.task == "gemm_mixed":
+        # the mixed form's tensor-core complex GEMM on the filter's two big shapes at paw96
+        # (P^H Z: m = n_proj, n = bands, k = N_pw; P W: m = N_pw, n = bands, k = n_proj), or
+        # on --gemm-mnk as a P^H Z-type product
+        g = ChebFI(0)
+        gen = torch.Generator(device="cuda").manual_seed(6)
+        shapes = [("PhY", True, 2048, 2048, 60005), ("PW", False, 60005, 2048, 2048)]
+        if args.gemm_mnk_set:
+            shapes = [("custom", True, *args.gemm_mnk)]
+        out = {}
+        for name, conj, m, n, k in shapes:
+            A = torch.randn(((m, k) if conj else (k, m)), dtype=torch.complex64, device="cuda", generator=gen).T
+            B = torch.randn((n, k), dtype=torch.complex64, device="cuda", generator=gen).T
+            C = torch.zeros((n, m), dtype=torch.complex64, device="cuda").T
+            ms = _timed(lambda: g.gemm_mixed(A, B, conjA=conj, C=C), args.steps, args.warmup)
+            # the GEMM kernel alone (the call also builds the operand planes)
+            g.profile(True)
+            for _ in range(args.steps):
+                g.gemm_mixed(A, B, conjA=conj, C=C)
+            torch.cuda.synchronize()
+            tot = g.profile_totals()
+            g.profile(False)
+            kms = tot["gemm_mixed"][0] / tot["gemm_mixed"][1]
+            out[name] = {"m": m, "n": n, "k": k, "ms_call": ms, "ms_kernel": kms,
+                         "tflops": 8.0 * m * n * k / (kms / 1e3) / 1e12,
+                         "tflops_executed_bf16": 3 * 3 * 2.0 * m * n * k / (kms / 1e3) / 1e12,
+                         "kernels_ms": {kk: round(v[0] / args.steps, 3) for kk, v in tot.items()}}
+            del A, B, C
+        first = next(iter(out.values()))
+        line = {"metric": "mixed complex GEMM TFLOP/s (complex flops 8mnk)", "unit": "TFLOP/s",
+                "value": first["tflops"], "dtype": "bf16x3+f32", "steps": args.steps, "warmup": args.warmup,
+                "config": {"workload": "tensor-core complex GEMM, three real products of bf16 pairs"},
+                "shapes": out}
     elif args.task == "filter_only":
         # the filter alone (no Rayleigh-Ritz) on a named cell: the command behind the
         # per-kernel counter captures of small cases
@@ -440,13 +473,16 @@ def main():
     ap.add_argument("--ref-bands", type=int, default=64)
     ap.add_argument("--nbands", type=int, default=None, help="override the band count (testing only)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic cell (paw96 is the benchmark workload)")
-    ap.add_argument("--gemm-mnk", type=int, nargs=3, default=[2048, 2048, 8192], help="gemm64: m n k")
+    ap.add_argument("--gemm-mnk", type=int, nargs=3, default=None, help="gemm64 / gemm_mixed: m n k")
     ap.add_argument("--gate-sweeps", type=int, default=120, help="gate: most FP64 sweeps before giving up")
     ap.add_argument("--task", default="filter", choices=["filter", "backward", "refine", "kpoints", "locking", "gate", "filter_only",
-                             "gemm64"],
+                             "gemm64", "gemm_mixed"],
                     help="filter: the benchmark; backward / refine: the differentiation and the "
                          "refinement-Woodbury measurements (their own JSON line)")
     args = ap.parse_args()
+    args.gemm_mnk_set = args.gemm_mnk is not None
+    if args.gemm_mnk is None:
+        args.gemm_mnk = [2048, 2048, 8192]
     if args.impl == "reference":
         return run_reference(args)
     if args.task != "filter":

@@ -289,6 +289,18 @@ int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n
                      const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                      void* stream);
 
+/* Complex GEMM of the mixed form's projector products (Section 5.1: P^H psi and P W) on the
+ * tensor cores: C = alpha op(A) B + beta C, C m x n, inner dimension k >= 1; op(A) = A (m x k,
+ * lda >= m) or A^H (A k x m, lda >= k) when conjA; B k x n (ldb >= k).  A, B, C: device,
+ * complex64 (interleaved FP32) column-major; C must not overlap A or B.  The operands are
+ * split into bf16 pairs (x = hi + lo, about 16 significant bits) and the product is formed by
+ * three real products of the planes (Re, Im, Re -+ Im) x (Re, Im, Re + Im) -- Gauss's form,
+ * three quarters of the real products of a real embedding -- each with the three bf16 terms
+ * hi hi + hi lo + lo hi, FP32 accumulation in the tensor memory in chunks of 512 along k.
+ * Needs no cell or projectors. */
+int chebfi_gemm_mixed(chebfi_ctx* ctx, int conjA, int64_t m, int64_t n, int64_t k, float alpha, const void* A,
+                      int64_t lda, const void* B, int64_t ldb, float beta, void* C, int64_t ldc, void* stream);
+
 /* Dense Hermitian eigensolver of the Rayleigh-Ritz step (Algorithm 2; ELPA in the paper):
  *  CHEBFI_EIG_JACOBI: FP64 cyclic Jacobi (rounds of n/2 disjoint rotations).
  *  CHEBFI_EIG_REFINED: FP32 cyclic Jacobi for approximate eigenvectors, then the iterative

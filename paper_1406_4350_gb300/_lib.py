@@ -73,6 +73,8 @@ SIGNATURES = {
     "chebfi_set_fp64_gemm": (c_int, [c_void_p, c_int, c_int, P_int]),
     "chebfi_gemm_fp64": (c_int, [c_void_p, c_int, c_int, c_int64, c_int64, c_int64, c_double, c_void_p, c_int64,
                                  c_void_p, c_int64, c_double, c_void_p, c_int64, c_void_p]),
+    "chebfi_gemm_mixed": (c_int, [c_void_p, c_int, c_int64, c_int64, c_int64, ctypes.c_float, c_void_p, c_int64,
+                                  c_void_p, c_int64, ctypes.c_float, c_void_p, c_int64, c_void_p]),
     "chebfi_set_eigensolver": (c_int, [c_void_p, c_int]),
     "chebfi_eigensolver_steps": (c_int, [c_void_p]),
     "chebfi_selftest_bounded_wait": (c_int, [c_void_p, c_int, c_double, P_int, P_double]),

@@ -341,6 +341,30 @@ class ChebFI:
                                               c, ldc, _stream()))
         return C
 
+    def gemm_mixed(self, A, B, conjA: bool = False, alpha: float = 1.0, beta: float = 0.0, C=None):
+        """C = alpha op(A) B + beta C for column-major complex64 CUDA matrices, on the tensor
+        cores (bf16 pairs, three real products; the mixed form's projector GEMMs)."""
+        def mat(X):
+            if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.complex64 and X.dim() == 2):
+                raise TypeError("expected a 2-D complex64 CUDA tensor")
+            if X.shape[0] > 1 and X.shape[1] > 1 and X.stride(0) != 1:
+                raise ValueError("matrices must be column-major")
+            ld = X.stride(1) if X.shape[1] > 1 else X.shape[0]
+            return ctypes.c_void_p(X.data_ptr()), int(max(ld, X.shape[0], 1))
+        m = A.shape[1] if conjA else A.shape[0]
+        k = A.shape[0] if conjA else A.shape[1]
+        n = B.shape[1]
+        if B.shape[0] != k:
+            raise ValueError("inner dimensions differ")
+        if C is None:
+            C = torch.zeros((n, m), dtype=torch.complex64, device=A.device).T
+        a, lda = mat(A)
+        b, ldb = mat(B)
+        c, ldc = mat(C)
+        self._check(self.lib.chebfi_gemm_mixed(self.h, int(conjA), m, n, k, alpha, a, lda, b, ldb, beta, c, ldc,
+                                               _stream()))
+        return C
+
     def solve_stats(self):
         """(sweeps performed, band-H-applications of the filters) of the last solve."""
         sw = ctypes.c_int(0)

@@ -304,15 +304,31 @@ cplx<R>* filter_sorted(chebfi_ctx* ctx, FilterBufs<R> b, int64_t nb0, int degree
   return active ? b.Ya : cur;
 }
 
-// bf16 (hi, lo) embeddings of P^H, P, G and M for the tensor-core GEMMs (first use only).
-void ensure_tc(chebfi_ctx* ctx, cudaStream_t st) {
-  if (ctx->tc_ready || ctx->nproj == 0) return;
+// bf16 (hi, lo) operands of the tensor-core GEMMs, built on first use: the real embeddings
+// of G and M, of P^H (the P^H Z product) and, with P_too, of P (the batched k-points' P W);
+// and the (Re, Im, Re + Im) planes of P for the three-multiplication P W of a single problem.
+// P^H Z keeps the real embedding: its two operands are both long streams, and the three
+// products of the plane form re-read them from DRAM several times more (measured), which
+// costs more than the quarter of the tensor work it saves; P W's W fits in L2.
+void ensure_tc(chebfi_ctx* ctx, cudaStream_t st, bool P_too = false) {
+  if (ctx->nproj == 0) return;
   const int64_t npw = ctx->npw, nq = ctx->nproj;
-  embed_ph(npw, nq, ctx->d_P.p, npw, ctx->tcA1, st);
-  embed_n(npw, nq, ctx->d_P.p, npw, ctx->tcA2, st);
-  embed_n(nq, nq, ctx->d_G.p, nq, ctx->tcAG, st);
-  if (ctx->paw) embed_n(nq, nq, ctx->d_M.p, nq, ctx->tcAM, st);
-  ctx->tc_ready = true;
+  if (!ctx->tc_ready) {
+    embed_n(nq, nq, ctx->d_G.p, nq, ctx->tcAG, st);
+    if (ctx->paw) embed_n(nq, nq, ctx->d_M.p, nq, ctx->tcAM, st);
+    embed_ph(npw, nq, ctx->d_P.p, npw, ctx->tcA1, st);
+    ctx->tc_ready = true;
+  }
+  if (P_too && !ctx->tcP_ready) {
+    embed_n(npw, nq, ctx->d_P.p, npw, ctx->tcA2, st);
+    ctx->tcP_ready = true;
+  }
+}
+
+void ensure_tc3(chebfi_ctx* ctx, cudaStream_t st) {
+  if (ctx->tc3_ready || ctx->nproj == 0) return;
+  embed3_n(ctx->npw, ctx->nproj, ctx->d_P.p, ctx->npw, ctx->tcP3, st);
+  ctx->tc3_ready = true;
 }
 
 // Mixed form of the filter: FP32 iterates and FFT, projector GEMMs on the tensor cores
@@ -329,6 +345,7 @@ float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb0, int degr
   const int64_t ldzb = (2 * npw + 7) / 8 * 8;
   if (nq > 0) {
     ensure_tc(ctx, st);
+    ensure_tc3(ctx, st);
     w.Zb.ld = ldzb;
     w.Zb.alloc((size_t)ldzb * nb);
     if (p0) {
@@ -376,9 +393,9 @@ float2* filter_mixed(chebfi_ctx* ctx, FilterBufs<float> b, int64_t nb0, int degr
                 2 * nq, status, st, "tc_gemm_small", &ctx->w.tcws);
       }
       // Y_{k+1} = T + a P W
-      split_block(nq, nb, b.pw, nq, w.Sb, st);
-      tc_gemm(ctx->tcA2.view(), w.Sb.view(), 2 * npw, nb, 2 * nq, (float)a, 1.f, (float*)prev, 2 * npw, (float*)prev,
-              2 * npw, status, st, "tc_gemm_PW", &ctx->w.tcws);
+      split3_block(nq, nb, b.pw, nq, w.W3, st);
+      tc_cgemm3(ctx->tcP3, w.W3, false, npw, nb, nq, (float)a, 1.f, prev, npw, prev, npw, status, st, "tc_gemm_PW",
+                &ctx->w.tcws);
       cheb_combine<float>(nq, nb, (float)a, b.pz, nq, (float)c, pcur, nq, (float)bp, k == 0 ? nullptr : pprev, nq,
                           pprev, nq, st);
     }
@@ -1068,7 +1085,7 @@ void filter_backward(chebfi_ctx* ctx, int64_t nb, int n, double lo, double hi, i
 
 }  // namespace
 
-void ensure_tc_operands(chebfi_ctx* ctx, cudaStream_t st) { ensure_tc(ctx, st); }
+void ensure_tc_operands(chebfi_ctx* ctx, cudaStream_t st) { ensure_tc(ctx, st, true); }
 
 }  // namespace chebfi
 
@@ -1323,6 +1340,7 @@ int chebfi_set_projectors(chebfi_ctx* ctx, int64_t nproj, const void* P, int64_t
   ctx->bound_rigorous = -1.0;
   ctx->has_proj = false;
   ctx->ozPh.nmod = ctx->ozP.nmod = 0;  // residues of the previous P are stale
+  ctx->tc_ready = ctx->tcP_ready = ctx->tc3_ready = false;  // and so are its bf16 embeddings
   if (nproj == 0) {
     ctx->has_proj = true;
     return CHEBFI_OK;
@@ -1469,6 +1487,7 @@ int chebfi_apply_H(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t
       // local part in FP32, projector products on the tensor cores
       const int64_t nq = ctx->nproj;
       ensure_tc(ctx, st);
+      ensure_tc3(ctx, st);
       LocalEpi<float> ep;
       ep.Y = w.fYa.p;
       ep.ldy = npw;
@@ -1481,9 +1500,9 @@ int chebfi_apply_H(chebfi_ctx* ctx, const void* Y, void* HY, int64_t nb, int64_t
       tc_gemm(ctx->tcA1.view(), w.Zb.view(), 2 * nq, nb, 2 * npw, 1.f, 0.f, nullptr, 0, (float*)w.fpa.p, 2 * nq,
               ctx->d_status.p, st, "tc_gemm_PhY", &ctx->w.tcws);
       blockdiag_apply<float>(ctx, ctx->d_Dblkf.p, w.fpa.p, nq, w.fpb.p, nq, nb, st);
-      split_block(nq, nb, w.fpb.p, nq, w.Sb, st);
-      tc_gemm(ctx->tcA2.view(), w.Sb.view(), 2 * npw, nb, 2 * nq, 1.f, 1.f, (float*)w.fZ.p, 2 * npw, (float*)w.fZ.p,
-              2 * npw, ctx->d_status.p, st, "tc_gemm_PW", &ctx->w.tcws);
+      split3_block(nq, nb, w.fpb.p, nq, w.W3, st);
+      tc_cgemm3(ctx->tcP3, w.W3, false, npw, nb, nq, 1.f, 1.f, w.fZ.p, npw, w.fZ.p, npw, ctx->d_status.p, st,
+                "tc_gemm_PW", &ctx->w.tcws);
     } else {
       apply_H_sorted<float>(ctx, w.fYa.p, w.fZ.p, w.fpa.p, w.fpb.p, w.fT1.p, nb, st);
     }
@@ -2007,6 +2026,23 @@ int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n
   }
   gemm64(ctx, conjA != 0, conjB != 0, m, n, k, alpha, (const double2*)A, lda, (const double2*)B, ldb, beta,
          (double2*)C, ldc, st, &ctx->w.splitk, "gemm_fp64");
+  API_END(ctx)
+}
+
+int chebfi_gemm_mixed(chebfi_ctx* ctx, int conjA, int64_t m, int64_t n, int64_t k, float alpha, const void* A,
+                      int64_t lda, const void* B, int64_t ldb, float beta, void* C, int64_t ldc, void* stream) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(m >= 0 && n >= 0 && k >= 1, CHEBFI_ERR_ARG, "need m, n >= 0 and k >= 1");
+  if (m == 0 || n == 0) return CHEBFI_OK;
+  CHEBFI_REQUIRE(A && B && C, CHEBFI_ERR_ARG, "null A, B or C");
+  CHEBFI_REQUIRE(lda >= (conjA ? k : m) && ldb >= k && ldc >= m, CHEBFI_ERR_ARG, "leading dimension too small");
+  cudaStream_t st = S(stream);
+  Work& w = ctx->w;
+  if (conjA) embed3f(true, k, m, (const float2*)A, lda, w.gA3, st);
+  else embed3f(false, m, k, (const float2*)A, lda, w.gA3, st);
+  split3_block(k, n, (const float2*)B, ldb, w.gB3, st);
+  tc_cgemm3(w.gA3, w.gB3, conjA != 0, m, n, k, alpha, beta, (const float2*)C, ldc, (float2*)C, ldc, ctx->d_status.p,
+            st, "gemm_mixed", &w.tcws);
   API_END(ctx)
 }
 

@@ -164,16 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_zfwd(const cplx<R>* __restrict__ T
     zj.x = v.x * ep.inv_n3 + k * yj.x;
     zj.y = v.y * ep.inv_n3 + k * yj.y;
     if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
-    if (ep.Zhi) {
-      const float zr = (float)zj.x, zi = (float)zj.y;
-      const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi);
-      __nv_bfloat16* ph = ep.Zhi + b * ep.ldzb + 2 * j;
-      __nv_bfloat16* pl = ep.Zlo + b * ep.ldzb + 2 * j;
-      ph[0] = hr;
-      ph[1] = hi_;
-      pl[0] = __float2bfloat16_rn(zr - __bfloat162float(hr));
-      pl[1] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
-    }
+    if (ep.Zhi) epi_split_z(ep, b, j, (float)zj.x, (float)zj.y);
     if (ep.T) {
       // three-term update without its nonlocal part: T = a (Z - c Y) - bprev Yprev
       cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
@@ -321,7 +312,7 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
     if (e.Yprev) e.Yprev = ep.Yprev + b0 * ep.ldt;
     e.inv_n3 = (R)(1.0 / ((double)N * N * N));
     const double epi = sph * (1.0 + (e.Z ? 1.0 : 0.0) + (e.T ? 1.0 : 0.0) + (e.Yprev ? 1.0 : 0.0)) +
-                       (e.Zhi ? (double)ctx->npw * nbc * 8.0 : 0.0);
+                       (e.Zhi ? (double)ctx->npw * nbc * (e.zplane ? 12.0 : 8.0) : 0.0);
     CHEBFI_LAUNCH_W("k_zfwd", st, col + epi, k_zfwd_f<R, N><<<gz, kThreads, zbytes, st>>>(T, fa, tw, K, e));
   }
 }
@@ -417,7 +408,7 @@ void local_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
     e.inv_n3 = (R)(1.0 / ((double)s.n1 * s.n2 * s.n3));
     // column buffer in, Y in, and the epilogue's sphere reads and writes
     const double epi = sph * (1.0 + (e.Z ? 1.0 : 0.0) + (e.T ? 1.0 : 0.0) + (e.Yprev ? 1.0 : 0.0)) +
-                       (e.Zhi ? (double)ctx->npw * nbc * 8.0 : 0.0);
+                       (e.Zhi ? (double)ctx->npw * nbc * (e.zplane ? 12.0 : 8.0) : 0.0);
     CHEBFI_LAUNCH_W("k_zfwd", st, col + epi, k_zfwd<R><<<gz, kThreads, zbytes, st>>>(T, sa, pz, K, e));
   }
 }

@@ -337,7 +337,7 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
 }
 
 // columns [c0, c0 + kCBF) of block b: forward z transform, back to the sphere, + K psi and
-// the epilogue (Z, its bf16 pair, and the Chebyshev combination T = a (Z - c Y) - b Yprev)
+// the epilogue (Z, its bf16 planes, and the Chebyshev combination T = a (Z - c Y) - b Yprev)
 template <typename R, int N3>
 __device__ __forceinline__ void zfwd_body(const cplx<R>* __restrict__ T, const FastArgs& fa,
                                           const cplx<R>* __restrict__ twz, const R* __restrict__ K,
@@ -365,16 +365,7 @@ __device__ __forceinline__ void zfwd_body(const cplx<R>* __restrict__ T, const F
     zj.x = v.x * ep.inv_n3 + k * yj.x;
     zj.y = v.y * ep.inv_n3 + k * yj.y;
     if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
-    if (ep.Zhi) {
-      const float zr = (float)zj.x, zi = (float)zj.y;
-      const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi);
-      __nv_bfloat16* ph = ep.Zhi + b * ep.ldzb + 2 * j;
-      __nv_bfloat16* pl = ep.Zlo + b * ep.ldzb + 2 * j;
-      ph[0] = hr;
-      ph[1] = hi_;
-      pl[0] = __float2bfloat16_rn(zr - __bfloat162float(hr));
-      pl[1] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
-    }
+    if (ep.Zhi) epi_split_z(ep, b, j, (float)zj.x, (float)zj.y);
     if (ep.T) {
       cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
       if (ep.Yprev) tp = ep.Yprev[b * ep.ldt + j];

@@ -124,6 +124,20 @@ struct SplitBF16Buf {
   SplitBF16 view() const { return SplitBF16{hi.p, lo.p, ld}; }
 };
 
+// Three bf16 (hi, lo) K-major planes of one complex operand for the three-multiplication
+// complex GEMM (gemm_tc.cu): plane q of row r starts at q * plane + r * ld elements.
+struct SplitBF16x3 {
+  DevBuf<__nv_bfloat16> hi, lo;
+  int64_t ld = 0, plane = 0;
+  void alloc(int64_t rows, int64_t k) {
+    ld = (k + 7) / 8 * 8;
+    plane = ld * rows;
+    hi.alloc((size_t)(3 * plane));
+    lo.alloc((size_t)(3 * plane));
+  }
+  SplitBF16 view(int q) const { return SplitBF16{hi.p + q * plane, lo.p + q * plane, ld}; }
+};
+
 // One problem of a grouped tensor-core GEMM (gemm_tc.cu): D = alpha' A B + beta C with FP32
 // column-major C / D, A and B given by the four bf16 tensor maps maps[4 map .. 4 map + 3]
 // (A hi, A lo, B hi, B lo; boxes of 128 rows); alpha' = alpha, times the launch's alpha_mul
@@ -220,6 +234,8 @@ struct Work {
   DevBuf<double2> splitk;
   DevBuf<float2> fsplitk;
   SplitBF16Buf Zb, Sb;  // bf16 pairs of Z (or Y) and of the projection-space operands
+  SplitBF16x3 W3;       // (re, im, re + im) planes of W for the three-multiplication P W
+  SplitBF16x3 gA3, gB3; // operand planes of chebfi_gemm_mixed
   DevBuf<float> tcws;   // K-split partial sums of the tensor-core GEMMs
   DevBuf<double2> gpool;          // filter backward: checkpoints, segment, adjoint iterates
   DevBuf<float2> fgT, fgR, fgG;   // FP32 backward: column buffer and real-space grids of the V gradient
@@ -295,8 +311,11 @@ struct chebfi_ctx {
   chebfi::DevBuf<float> d_Dblkf;
   chebfi::DevBuf<int> d_status;               // device error flag
   // mixed form: bf16 (hi, lo) real embeddings of P^H, P, G and M, built on first use
-  bool tc_ready = false;
+  bool tc_ready = false, tcP_ready = false;
   chebfi::SplitBF16Buf tcA1, tcA2, tcAG, tcAM;
+  // (Re, Im, Re + Im) planes of P for the three-multiplication P W
+  chebfi::SplitBF16x3 tcP3;
+  bool tc3_ready = false;
   chebfi::Work w;
   // FP64 complex GEMMs: engine choice (chebfi_set_fp64_gemm), modulus count of the
   // tensor-core emulation, its workspace, and the residues of P^H and P (built on first use)

@@ -19,14 +19,40 @@ template <typename R> struct LocalEpi {
   int64_t ldy = 0;
   cplx<R>* Z = nullptr;
   int64_t ldz = 0;
+  // bf16 (hi, lo) pair of Z: interleaved (re, im) at Zhi + b * ldzb + 2 j (zplane = 0), or the
+  // planes (re, im, re + im) of the three-multiplication product at Zhi + q * zplane + b * ldzb + j
   __nv_bfloat16* Zhi = nullptr;
   __nv_bfloat16* Zlo = nullptr;
-  int64_t ldzb = 0;
+  int64_t ldzb = 0, zplane = 0;
   cplx<R>* T = nullptr;
   const cplx<R>* Yprev = nullptr;
   int64_t ldt = 0;
   R a = 0, c = 0, bprev = 0, inv_n3 = 0;
 };
+#ifdef __CUDACC__
+// element j of band b of Z into the epilogue's bf16 planes
+template <typename R>
+__device__ __forceinline__ void epi_split_z(const LocalEpi<R>& ep, int64_t b, int64_t j, float zr, float zi) {
+  if (ep.zplane == 0) {
+    const int64_t o = b * ep.ldzb + 2 * j;
+    const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi);
+    ep.Zhi[o] = hr;
+    ep.Zhi[o + 1] = hi_;
+    ep.Zlo[o] = __float2bfloat16_rn(zr - __bfloat162float(hr));
+    ep.Zlo[o + 1] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
+    return;
+  }
+  const int64_t o = b * ep.ldzb + j;
+  const float zs = zr + zi;
+  const __nv_bfloat16 hr = __float2bfloat16_rn(zr), hi_ = __float2bfloat16_rn(zi), hs = __float2bfloat16_rn(zs);
+  ep.Zhi[o] = hr;
+  ep.Zhi[o + ep.zplane] = hi_;
+  ep.Zhi[o + 2 * ep.zplane] = hs;
+  ep.Zlo[o] = __float2bfloat16_rn(zr - __bfloat162float(hr));
+  ep.Zlo[o + ep.zplane] = __float2bfloat16_rn(zi - __bfloat162float(hi_));
+  ep.Zlo[o + 2 * ep.zplane] = __float2bfloat16_rn(zs - __bfloat162float(hs));
+}
+#endif
 size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb);
 // Derivative of (V_loc psi) with respect to V_loc for a real loss whose gradient at the
 // output is g: gV(x, y, z) = (1/N^3) sum_b Re(conj(g_b(r)) psi_b(r)) with psi_b, g_b the
@@ -79,6 +105,20 @@ void embed_ph(int64_t npw, int64_t nq, const double2* P, int64_t ldp, SplitBF16B
 void embed_n(int64_t m, int64_t k, const double2* A, int64_t lda, SplitBF16Buf& out, cudaStream_t st);
 // complex FP32 block (m x nb) -> K-major bf16 pair with 2m reals per column
 void split_block(int64_t m, int64_t nb, const float2* x, int64_t ldx, SplitBF16Buf& out, cudaStream_t st);
+// The three planes of the three-multiplication products: of P (Re, Im, Re + Im; rows =
+// plane waves, K = projectors) and of a complex FP32 block (re, im, re + im; rows = its
+// columns).
+void embed3_n(int64_t npw, int64_t nq, const double2* P, int64_t ldp, SplitBF16x3& out, cudaStream_t st);
+void split3_block(int64_t m, int64_t nb, const float2* x, int64_t ldx, SplitBF16x3& out, cudaStream_t st);
+// the planes of a complex FP32 matrix A (rows x cols): of A^H (conj) or of A
+void embed3f(bool conj, int64_t rows, int64_t cols, const float2* A, int64_t lda, SplitBF16x3& out, cudaStream_t st);
+// Complex D = alpha op(A) B + beta C (M x N, column-major, interleaved FP32; C may be D) by
+// three real tensor-core products of the planes (Gauss's form); conjA: op(A) = A^H with A's
+// planes (Re, Im, Re - Im) of A^T, else op(A) = A with planes (Re, Im, Re + Im) of A (embed3f,
+// embed3_n).  K-split partial sums in ws.
+void tc_cgemm3(const SplitBF16x3& A, const SplitBF16x3& B, bool conjA, int64_t M, int64_t N, int64_t K, float alpha,
+               float beta, const float2* C, int64_t ldc, float2* D, int64_t ldd, int* status, cudaStream_t st,
+               const char* tag, DevBuf<float>* ws);
 
 // ---------------------------------------------------------------- FP64-accurate GEMM on tensor cores (ozaki.cu)
 // Residues of op(X) (nrows x K complex; row r is column r of X when rows_are_columns, else
