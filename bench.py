@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -638,6 +639,17 @@ def main():
     bf16 = peaks.get("bf16_tflops_sustained", 1713.1)
     hbm = peaks.get("hbm_gbs", 6762.3)
     nmod = 14
+    # the plane pass's arithmetic: per band and z plane, 96-point line transforms along y on
+    # the rows of the active x range (inverse and forward) and along x on every y line
+    # (inverse and forward), 5 N log2 N flops each (the usual FFT count), and the real
+    # V_loc(r) times complex psi(r) product, 2 flops a point; its launch's recorded work is
+    # the column buffer in and out, 2 N ncol per band (elements)
+    Ng = int(cell.grid[0])
+    xs = (cell.miller[:, 0].astype(np.int64) + Ng // 2) % Ng
+    nact = int(xs.max() - xs.min() + 1)
+    ncol = len(np.unique(cell.miller[:, 0].astype(np.int64) * 100003 + cell.miller[:, 1]))
+    plane_flops_band = Ng * ((2 * nact + 2 * Ng) * 5.0 * Ng * math.log2(Ng) + 2.0 * Ng * Ng)
+    plane_elems_band = 2.0 * Ng * ncol
 
     def roofline(phase, name):
         ms_tot, cnt, work = prof_acc[phase][name]
@@ -655,6 +667,21 @@ def main():
             out.update(bound="tensor", unit="TFLOP/s", achieved=ach * nmod, peak=bf16, frac=ach * nmod / bf16,
                        fp64_equivalent_tflops=ach, fp64_equivalent_over_fp64_peak=ach / fp64_peak,
                        peak_source="bf16_tflops_sustained (measured); executed = %d moduli x the FP64 flops" % nmod)
+        elif name == "k_plane":
+            # bound by its FP32 (FP64 in the FP64 phase) arithmetic, not by HBM: the FFT flops
+            # per launch over the measured peak of its precision; the HBM fraction beside it
+            esz = 16.0 if phase == "rr" or prec == F64 else 8.0
+            bands = work / cnt / (plane_elems_band * esz)
+            flops = plane_flops_band * bands
+            pk = fp64_peak if esz == 16.0 else fp32_peak
+            ach = flops / avg_s / 1e12
+            out.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=pk, frac=ach / pk,
+                       peak_source=("%s FMA rate measured in this run (chebfi_probe_fma_rate); FFT flops "
+                                    "5 N log2 N per 96-point line, %d active rows of 96" %
+                                    ("FP64" if esz == 16.0 else "FP32", nact)),
+                       hbm={"achieved_gbs": work / cnt / avg_s / 1e9, "peak": hbm,
+                            "frac": work / cnt / avg_s / 1e9 / hbm},
+                       flops_per_launch=flops)
         elif name == "k_jac_sweep":
             ach = work / cnt / avg_s / 1e12
             out.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp32_peak, frac=ach / fp32_peak,
@@ -682,6 +709,9 @@ def main():
         if work <= 0:
             continue
         r_ = roofline("filter", k)
+        if k == "k_plane":  # the larger of its two bounds
+            ideal += max(r_["flops_per_launch"] * cnt / (r_["peak"] * 1e12), work / (hbm * 1e9))
+            continue
         scale = 1e12 if r_["unit"] == "TFLOP/s" else 1e9
         ideal += work / (r_["peak"] * scale)
     filt_mean_s = statistics.mean(filt_ms) / 1e3
