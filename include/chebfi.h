@@ -308,7 +308,10 @@ int chebfi_gemm_mixed(chebfi_ctx* ctx, int conjA, int64_t m, int64_t n, int64_t 
  *    lambda_i = S_ii / G_ii, E_ij = (S_ij - lambda_j G_ij) / (lambda_j - lambda_i),
  *    E_ii = (1 - G_ii) / 2, X <- X (I + E) -- until max |E| <= 1e-10; pairs too close
  *    for the formula are only orthogonalised and their cluster's block of X^H A X is then
- *    diagonalised by FP64 Jacobi.  Falls back to CHEBFI_EIG_JACOBI if it does not converge.
+ *    diagonalised by FP64 Jacobi.  A nearly diagonal A (a converging solve's later sweeps)
+ *    skips the FP32 Jacobi: the refinement starts from the identity when its first step (G =
+ *    I, S = A, no GEMM) has max |E| <= 0.01.  Falls back to CHEBFI_EIG_JACOBI if it does not
+ *    converge.
  *  CHEBFI_EIG_AUTO (initial): REFINED from 512 bands up, JACOBI below. */
 enum { CHEBFI_EIG_AUTO = 0, CHEBFI_EIG_JACOBI = 1, CHEBFI_EIG_REFINED = 2 };
 int chebfi_set_eigensolver(chebfi_ctx* ctx, int mode);

@@ -542,8 +542,9 @@ void rq_sorted(chebfi_ctx* ctx, const double2* Y, int64_t nb, double* rq, cudaSt
 // ELPA): A (n x n, ld n) -> ascending eigenvalues w and orthonormal eigenvectors X (ld n).
 // FP64 cyclic Jacobi for small n; from n = 512 up (or when selected) the FP32 Jacobi gives
 // approximate vectors, which the iterative refinement of Ogita & Aishima (2018) brings to
-// FP64 accuracy with FP64 GEMMs (quadratic convergence, 2-4 steps); pairs too close for its
-// formula end in a dense FP64 Jacobi of their cluster's block.  A is destroyed.
+// FP64 accuracy with FP64 GEMMs (quadratic convergence, 2-4 steps), or, for a nearly
+// diagonal A, the refinement starts from the identity; pairs too close for its formula end
+// in a dense FP64 Jacobi of their cluster's block.  A is destroyed.
 void eigh_rr(chebfi_ctx* ctx, int64_t n, double2* A, double* w, double2* X, cudaStream_t st) {
   Work& wk = ctx->w;
   int* status = ctx->d_status.p;
@@ -569,32 +570,61 @@ void eigh_rr(chebfi_ctx* ctx, int64_t n, double2* A, double* w, double2* X, cuda
   wk.enp.alloc(1);
   wk.epairs.alloc(kCap);
   DevBuf<double2>* ws = &wk.splitk;
-  // stage 1: FP32 Jacobi on a copy
-  convert(n, n, A, n, wk.e32a.p, n, st);
-  jacobi_eigh_f32(n, wk.e32a.p, n, wk.e32w.p, wk.e32b.p, n, status, st, &wk.small5);
-  convert(n, n, wk.e32b.p, n, X, n, st);
-  // stage 2: refinement in FP64
   double2 *Xc = X, *Xn = wk.eX.p;
   bool conv = false;
   int npairs = 0;
-  for (int it = 0; it < 8 && !conv; ++it) {
-    gemm64(ctx, true, false, n, n, n, 1.0, Xc, n, Xc, n, 0.0, wk.eG.p, n, st, ws, "gemm_eig", true);
-    mirror_lower(n, wk.eG.p, n, st);
-    gemm64(ctx, false, false, n, n, n, 1.0, A, n, Xc, n, 0.0, wk.eAX.p, n, st, ws, "gemm_eig");
-    gemm64(ctx, true, false, n, n, n, 1.0, Xc, n, wk.eAX.p, n, 0.0, wk.eS.p, n, st, ws, "gemm_eig", true);
-    mirror_lower(n, wk.eS.p, n, st);
-    oa_step(n, wk.eG.p, wk.eS.p, wk.elam.p, wk.eM.p, wk.estats.p, wk.enp.p, wk.epairs.p, kCap, st);
+  ctx->eig_iters = 0;
+  // refinement in FP64 from the vectors in Xc, at most `iters` steps
+  auto refine = [&](int iters) {
+    for (int it = 0; it < iters && !conv; ++it) {
+      gemm64(ctx, true, false, n, n, n, 1.0, Xc, n, Xc, n, 0.0, wk.eG.p, n, st, ws, "gemm_eig", true);
+      mirror_lower(n, wk.eG.p, n, st);
+      gemm64(ctx, false, false, n, n, n, 1.0, A, n, Xc, n, 0.0, wk.eAX.p, n, st, ws, "gemm_eig");
+      gemm64(ctx, true, false, n, n, n, 1.0, Xc, n, wk.eAX.p, n, 0.0, wk.eS.p, n, st, ws, "gemm_eig", true);
+      mirror_lower(n, wk.eS.p, n, st);
+      oa_step(n, wk.eG.p, wk.eS.p, wk.elam.p, wk.eM.p, wk.estats.p, wk.enp.p, wk.epairs.p, kCap, st);
+      unsigned long long hs[2];
+      CHEBFI_CUDA(cudaMemcpyAsync(hs, wk.estats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+      CHEBFI_CUDA(cudaMemcpyAsync(&npairs, wk.enp.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      gemm64(ctx, false, false, n, n, n, 1.0, Xc, n, wk.eM.p, n, 0.0, Xn, n, st, ws, "gemm_eig");
+      std::swap(Xc, Xn);
+      CHEBFI_CUDA(cudaStreamSynchronize(st));
+      double emax;
+      std::memcpy(&emax, &hs[1], sizeof(double));
+      ++ctx->eig_iters;
+      // after an update of size emax the vectors are accurate to O(emax^2): below rounding
+      conv = std::isfinite(emax) && emax <= 1e-10;
+    }
+  };
+  // Fast path: when A is already nearly diagonal (the later sweeps of a converging solve,
+  // whose Ritz vectors barely turn), the identity is a good enough first approximation.
+  // Its refinement step needs no GEMM (G = I, S = A, X = I + E); when that step is small
+  // (max |E| <= kFastE) and finds few close pairs, refine from there and skip stage 1.
+  constexpr double kFastE = 0.01;
+  {
+    set_identity(n, wk.eG.p, n, st);
+    oa_step(n, wk.eG.p, A, wk.elam.p, X, wk.estats.p, wk.enp.p, wk.epairs.p, kCap, st);
     unsigned long long hs[2];
     CHEBFI_CUDA(cudaMemcpyAsync(hs, wk.estats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
     CHEBFI_CUDA(cudaMemcpyAsync(&npairs, wk.enp.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    gemm64(ctx, false, false, n, n, n, 1.0, Xc, n, wk.eM.p, n, 0.0, Xn, n, st, ws, "gemm_eig");
-    std::swap(Xc, Xn);
     CHEBFI_CUDA(cudaStreamSynchronize(st));
     double emax;
     std::memcpy(&emax, &hs[1], sizeof(double));
-    ctx->eig_iters = it + 1;
-    // after an update of size emax the vectors are accurate to O(emax^2): below rounding
-    conv = std::isfinite(emax) && emax <= 1e-10;
+    if (std::isfinite(emax) && emax <= kFastE && npairs <= n) {
+      ctx->eig_iters = 1;
+      conv = emax <= 1e-10;
+      refine(5);
+    }
+  }
+  if (!conv) {
+    // stage 1: FP32 Jacobi on a copy; stage 2: refinement from its vectors
+    convert(n, n, A, n, wk.e32a.p, n, st);
+    jacobi_eigh_f32(n, wk.e32a.p, n, wk.e32w.p, wk.e32b.p, n, status, st, &wk.small5);
+    convert(n, n, wk.e32b.p, n, X, n, st);
+    Xc = X;
+    Xn = wk.eX.p;
+    ctx->eig_iters = 0;
+    refine(8);
   }
   if (!conv || npairs > kCap) {
     // not converged (or too many near-equal pairs): the FP64 Jacobi of the original matrix

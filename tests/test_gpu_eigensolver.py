@@ -60,6 +60,35 @@ def test_refined_rayleigh_ritz_matches_oracle():
     assert np.abs(G - np.eye(G.shape[0])).max() <= 1e-11
 
 
+def test_refined_eigensolver_near_convergence_skips_the_fp32_stage():
+    """Ritz vectors turned by 1e-6: the projected matrix is nearly diagonal, the refinement
+    starts from the identity and no FP32 Jacobi sweep of the whole matrix runs (only cluster
+    blocks may be diagonalised); Ritz values as the oracle's on the same block."""
+    from paper_1406_4350_gb300._lib import EIG_REFINED
+    cell = config_cell("paw48", nbands=37)
+    op = PWOperator.from_cell(cell)
+    g = _ctx(cell)
+    g.set_eigensolver(EIG_REFINED)
+    lo = float(ch.rayleigh_quotients(op, cell.Y0).max())
+    hi = ch.upper_bound(op, "rigorous")
+    ref = ch.filter_reuse(op, cell.Y0, 10, lo, hi)
+    Y = _F(ref)
+    g.rayleigh_ritz(Y)
+    rng = np.random.default_rng(9)
+    Y2 = _np(Y) + 1e-6 * (rng.normal(size=ref.shape) + 1j * rng.normal(size=ref.shape))
+    w_ref, _ = ch.rayleigh_ritz(op, Y2)
+    Yg = _F(Y2)
+    g.profile(True)
+    ev, _ = g.rayleigh_ritz(Yg)
+    tot = g.profile_totals()
+    g.profile(False)
+    n = Y2.shape[1]
+    jac_work = sum(v[2] for k, v in tot.items() if k.startswith("k_jac"))
+    assert jac_work < 33.0 * n ** 3  # less than one sweep of the full matrix
+    assert 1 <= g.eigensolver_steps <= 6
+    assert np.abs(_np(ev) - w_ref).max() <= 1e-9
+
+
 def test_refined_eigensolver_resolves_exactly_degenerate_shells():
     """V = 0, no projectors: the plane waves of the first four shells (27 of them) mixed by a
     random unitary span an invariant subspace with eigenvalues 0, (2 pi^2/L^2) x {1 (6-fold),
