@@ -611,7 +611,8 @@ def main():
         tot = g.profile_totals()
         g.profile(False)
         fp_s = aggregate(ms / 1e3, 0.0, 0.0, world)[1]  # slowest rank
-        fp64 = {"value": nb * DEGREE * args.fp64_steps / fp_s, "unit": UNIT, "ms_per_filter": ms / args.fp64_steps, "dtype": "f64",
+        fp64 = {"value": nb * DEGREE * args.fp64_steps / fp_s, "unit": UNIT, "ms_per_filter": ms / args.fp64_steps,
+                "dtype": "f64 (FFT in double-float pairs on the FP32 units; GEMMs FP64-accurate modular)",
                 "kernels_ms": {k: round(v[0] / args.fp64_steps, 3) for k, v in
                                sorted(tot.items(), key=lambda kv: -kv[1][0])[:8]}}
         del Yc

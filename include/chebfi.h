@@ -289,6 +289,19 @@ int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n
                      const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                      void* stream);
 
+/* Arithmetic of the FFT passes of the FP64 path (the FP64 form's filter, apply_H and the
+ * H application of Rayleigh-Ritz in every form) on the compile-time grids (cubic 24, 32, 48,
+ * 64, 72, 96):
+ *  CHEBFI_FFT64_DOUBLE_FLOAT (initial): double-float arithmetic on the FP32 units -- each
+ *    value the unevaluated sum of two floats (48-bit significand, float's exponent range),
+ *    the error-free TwoSum / Fast2Sum / FMA-TwoProd transformations of Knuth and Dekker; a
+ *    transform keeps about 2^-44 of its line's norm; GB300's FP64 units run at ~1/64 of the
+ *    FP32 rate, so this is several times faster;
+ *  CHEBFI_FFT64_NATIVE: FP64 arithmetic on the FP64 units.
+ * Blocks, V_loc and the results stay FP64 in memory either way.  Other grids use FP64. */
+enum { CHEBFI_FFT64_NATIVE = 0, CHEBFI_FFT64_DOUBLE_FLOAT = 1 };
+int chebfi_set_fft64(chebfi_ctx* ctx, int mode);
+
 /* Complex GEMM of the mixed form's projector products (Section 5.1: P^H psi and P W) on the
  * tensor cores: C = alpha op(A) B + beta C, C m x n, inner dimension k >= 1; op(A) = A (m x k,
  * lda >= m) or A^H (A k x m, lda >= k) when conjA; B k x n (ldb >= k).  A, B, C: device,

@@ -19,6 +19,7 @@ OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_FILTER_OV
 F64, F32, MIXED = 0, 1, 2
 GEMM_AUTO, GEMM_CUDA_CORES, GEMM_TENSOR = 0, 1, 2
 EIG_AUTO, EIG_JACOBI, EIG_REFINED = 0, 1, 2
+FFT64_NATIVE, FFT64_DOUBLE_FLOAT = 0, 1
 BOUND_PAPER, BOUND_RIGOROUS = 0, 1
 
 
@@ -76,6 +77,7 @@ SIGNATURES = {
     "chebfi_gemm_mixed": (c_int, [c_void_p, c_int, c_int64, c_int64, c_int64, ctypes.c_float, c_void_p, c_int64,
                                   c_void_p, c_int64, ctypes.c_float, c_void_p, c_int64, c_void_p]),
     "chebfi_set_eigensolver": (c_int, [c_void_p, c_int]),
+    "chebfi_set_fft64": (c_int, [c_void_p, c_int]),
     "chebfi_eigensolver_steps": (c_int, [c_void_p]),
     "chebfi_selftest_bounded_wait": (c_int, [c_void_p, c_int, c_double, P_int, P_double]),
     "chebfi_probe_fma_rate": (c_int, [c_void_p, c_int, P_double, P_double]),

@@ -307,6 +307,11 @@ class ChebFI:
         self._check(self.lib.chebfi_probe_fma_rate(self.h, prec, ctypes.byref(tf), ctypes.byref(ms)))
         return tf.value, ms.value
 
+    def set_fft64(self, mode: int):
+        """Arithmetic of the FP64 path's FFT passes: FFT64_DOUBLE_FLOAT (initial; pairs of
+        floats on the FP32 units) or FFT64_NATIVE (the FP64 units)."""
+        self._check(self.lib.chebfi_set_fft64(self.h, mode))
+
     def set_eigensolver(self, mode: int):
         """Dense eigensolver of Rayleigh-Ritz: EIG_AUTO, EIG_JACOBI (FP64) or EIG_REFINED (FP32
         Jacobi + FP64 refinement)."""

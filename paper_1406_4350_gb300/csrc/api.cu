@@ -1347,8 +1347,14 @@ int chebfi_set_vloc(chebfi_ctx* ctx, const double* vloc, int on_device) {
           vs[((size_t)pz * n1 + px) * n2 + py] = v;
           vsf[((size_t)pz * n1 + px) * n2 + py] = (float)v;
         }
+    std::vector<float2> vsdf(n);
+    for (size_t i = 0; i < (size_t)n; ++i) {
+      const float h = (float)vs[i];
+      vsdf[i] = make_float2(h, (float)(vs[i] - (double)h));
+    }
     ctx->d_vs.upload(vs.data(), n);
     ctx->d_vsf.upload(vsf.data(), n);
+    ctx->d_vsdf.upload(vsdf.data(), n);
   }
   CHEBFI_CUDA(cudaDeviceSynchronize());
   ctx->vmax = vmax;
@@ -2056,6 +2062,14 @@ int chebfi_gemm_fp64(chebfi_ctx* ctx, int conjA, int conjB, int64_t m, int64_t n
   }
   gemm64(ctx, conjA != 0, conjB != 0, m, n, k, alpha, (const double2*)A, lda, (const double2*)B, ldb, beta,
          (double2*)C, ldc, st, &ctx->w.splitk, "gemm_fp64");
+  API_END(ctx)
+}
+
+int chebfi_set_fft64(chebfi_ctx* ctx, int mode) {
+  API_BEGIN(ctx)
+  CHEBFI_REQUIRE(mode == CHEBFI_FFT64_NATIVE || mode == CHEBFI_FFT64_DOUBLE_FLOAT, CHEBFI_ERR_ARG,
+                 "fft64 mode must be CHEBFI_FFT64_NATIVE or CHEBFI_FFT64_DOUBLE_FLOAT");
+  ctx->fft64 = mode;
   API_END(ctx)
 }
 

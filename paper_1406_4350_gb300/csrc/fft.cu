@@ -13,6 +13,7 @@
 //   zfwd  : forward FFT along z, pick the sphere points, scale by 1/(N1 N2 N3), add K psi,
 //           and apply the caller's epilogue (plain, or the Chebyshev three-term update).
 #include <cmath>
+#include <type_traits>
 
 #include "fft_core.cuh"
 #include "fft_fast.cuh"
@@ -230,8 +231,11 @@ __global__ void k_density_accum(int n1, int n2, int n3, int64_t nbc, const cplx<
 using fk::FastArgs;
 using fk::kCBF;
 
+// R: the arithmetic of the transforms (float, double, or dfl, the double-float form of the
+// FP64 path); blocks, the kinetic diagonal and the epilogue's operands are stored in
+// SphT<R> (double for dfl), the column buffer and the planes in cplx<R>.
 template <typename R, int N3>
-__global__ void __launch_bounds__(kThreads) k_zinv_f(const cplx<R>* __restrict__ Y, int64_t ldy,
+__global__ void __launch_bounds__(kThreads) k_zinv_f(const cplx<typename SphT<R>::type>* __restrict__ Y, int64_t ldy,
                                                      cplx<R>* __restrict__ T, FastArgs fa, const cplx<R>* __restrict__ twz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fk::zinv_body<R, N3>(Y, ldy, T, fa, twz, blockIdx.x * kCBF, blockIdx.y, smem_raw);
@@ -247,8 +251,9 @@ __global__ void __launch_bounds__(kThreads) k_plane_f(cplx<R>* __restrict__ T, c
 
 template <typename R, int N3>
 __global__ void __launch_bounds__(kThreads) k_zfwd_f(const cplx<R>* __restrict__ T, FastArgs fa,
-                                                     const cplx<R>* __restrict__ twz, const R* __restrict__ K,
-                                                     LocalEpi<R> ep) {
+                                                     const cplx<R>* __restrict__ twz,
+                                                     const typename SphT<R>::type* __restrict__ K,
+                                                     LocalEpi<typename SphT<R>::type> ep) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fk::zfwd_body<R, N3>(T, fa, twz, K, ep, blockIdx.x * kCBF, blockIdx.y, smem_raw);
 }
@@ -264,9 +269,15 @@ size_t local_workspace_elems(const chebfi_ctx* ctx, int64_t nb) {
   return (size_t)ctx->grid[2] * ncolp * (size_t)nb;
 }
 
+template <typename R> const R* vtable(const chebfi_ctx* c);
+template <> const float* vtable<float>(const chebfi_ctx* c) { return c->d_vsf.p; }
+template <> const double* vtable<double>(const chebfi_ctx* c) { return c->d_vs.p; }
+template <> const dfl* vtable<dfl>(const chebfi_ctx* c) { return reinterpret_cast<const dfl*>(c->d_vsdf.p); }
+
 template <typename R, int N>
-void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T, LocalEpi<R> ep,
-                 cudaStream_t st, const R* K) {
+void fast_launch(chebfi_ctx* ctx, const cplx<typename SphT<R>::type>* Y, int64_t ldy, int64_t nb, cplx<R>* T,
+                 LocalEpi<typename SphT<R>::type> ep, cudaStream_t st, const typename SphT<R>::type* K) {
+  using S = typename SphT<R>::type;
   const SphereFFT& s = ctx->sph;
   FastArgs fa;
   fa.ncol = s.ncol;
@@ -287,8 +298,8 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
   fa.nl_magic = s.nact > 1 ? (unsigned)(((1ull << 32) + s.nact - 1) / (unsigned long long)s.nact) : 0u;
   CHEBFI_REQUIRE(s.nxa >= 1 && s.nact >= 1, CHEBFI_ERR_STATE, "sphere without columns");
   CHEBFI_REQUIRE(s.pitch == N + 1, CHEBFI_ERR_STATE, "plane pitch of the compile-time path");
-  const cplx<R>* tw = sizeof(R) == 8 ? (const cplx<R>*)ctx->ax[0].tw64.p : (const cplx<R>*)ctx->ax[0].tw32.p;
-  const R* Vs = sizeof(R) == 8 ? (const R*)ctx->d_vs.p : (const R*)ctx->d_vsf.p;
+  const cplx<R>* tw = nullptr;  // the passes read their twiddles from constant tables
+  const R* Vs = vtable<R>(ctx);
   const size_t zbytes = (size_t)(N + kCBF * s.zpitch) * sizeof(cplx<R>);
   const size_t pbytes = (size_t)(N + N * s.pitch) * sizeof(cplx<R>);
   fk::init_twiddles();
@@ -301,7 +312,7 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
     const double esz = sizeof(cplx<R>), col = (double)N * s.ncol * nbc * esz, sph = (double)ctx->npw * nbc * esz;
     CHEBFI_LAUNCH_W("k_zinv", st, sph + col, k_zinv_f<R, N><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, fa, tw));
     CHEBFI_LAUNCH_W("k_plane", st, 2.0 * col, k_plane_f<R, N><<<dim3(N, nbc), kThreads, pbytes, st>>>(T, Vs, fa, tw));
-    LocalEpi<R> e = ep;
+    LocalEpi<S> e = ep;
     e.Y = ep.Y + b0 * ep.ldy;
     if (e.Z) e.Z = ep.Z + b0 * ep.ldz;
     if (e.Zhi) {
@@ -310,7 +321,7 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
     }
     if (e.T) e.T = ep.T + b0 * ep.ldt;
     if (e.Yprev) e.Yprev = ep.Yprev + b0 * ep.ldt;
-    e.inv_n3 = (R)(1.0 / ((double)N * N * N));
+    e.inv_n3 = (S)(1.0 / ((double)N * N * N));
     const double epi = sph * (1.0 + (e.Z ? 1.0 : 0.0) + (e.T ? 1.0 : 0.0) + (e.Yprev ? 1.0 : 0.0)) +
                        (e.Zhi ? (double)ctx->npw * nbc * (e.zplane ? 12.0 : 8.0) : 0.0);
     CHEBFI_LAUNCH_W("k_zfwd", st, col + epi, k_zfwd_f<R, N><<<gz, kThreads, zbytes, st>>>(T, fa, tw, K, e));
@@ -319,8 +330,8 @@ void fast_launch(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cpl
 
 // Compile-time-length path for cubic grids of the supported sizes; false = not taken.
 template <typename R>
-bool fast_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T, LocalEpi<R> ep,
-                cudaStream_t st, const R* K) {
+bool fast_dispatch(chebfi_ctx* ctx, const cplx<typename SphT<R>::type>* Y, int64_t ldy, int64_t nb, cplx<R>* T,
+                   LocalEpi<typename SphT<R>::type> ep, cudaStream_t st, const typename SphT<R>::type* K) {
   switch (ctx->grid[0]) {
     case 24: fast_launch<R, 24>(ctx, Y, ldy, nb, T, ep, st, K); return true;
     case 32: fast_launch<R, 32>(ctx, Y, ldy, nb, T, ep, st, K); return true;
@@ -330,6 +341,18 @@ bool fast_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx
     case 96: fast_launch<R, 96>(ctx, Y, ldy, nb, T, ep, st, K); return true;
     default: return false;
   }
+}
+// The FP64 path runs its transforms in double-float on the FP32 units unless the FP64 units
+// are asked for (chebfi_set_fft64); the column buffer's complex doubles then hold
+// double-float values, 16 bytes each as well.
+template <typename R>
+bool fast_apply(chebfi_ctx* ctx, const cplx<R>* Y, int64_t ldy, int64_t nb, cplx<R>* T, LocalEpi<R> ep,
+                cudaStream_t st, const R* K) {
+  if constexpr (std::is_same<R, double>::value) {
+    if (ctx->fft64 == CHEBFI_FFT64_DOUBLE_FLOAT)
+      return fast_dispatch<dfl>(ctx, Y, ldy, nb, reinterpret_cast<cdf*>(T), ep, st, K);
+  }
+  return fast_dispatch<R>(ctx, Y, ldy, nb, T, ep, st, K);
 }
 
 bool fast_fft_supported(int n1, int n2, int n3) {

@@ -19,6 +19,9 @@
 
 namespace chebfi {
 
+__host__ __device__ __forceinline__ float half_of(float v) { return 0.5f * v; }
+__host__ __device__ __forceinline__ double half_of(double v) { return 0.5 * v; }
+
 // r-point DFT out_p = sum_q x_q w^{pq}, w = exp(SIGN 2 pi i / r), in place.
 template <int SIGN, typename C>
 __host__ __device__ __forceinline__ void small_dft(C* x, int r) {
@@ -31,8 +34,13 @@ __host__ __device__ __forceinline__ void small_dft(C* x, int r) {
     C a = x[0] + x[2], b = x[0] - x[2], c = x[1] + x[3], d = x[1] - x[3];
     // w d with w = SIGN i
     C wd;
-    wd.x = -(R)SIGN * d.y;
-    wd.y = (R)SIGN * d.x;
+    if (SIGN > 0) {
+      wd.x = -d.y;
+      wd.y = d.x;
+    } else {
+      wd.x = d.y;
+      wd.y = -d.x;
+    }
     x[0] = a + c;
     x[2] = a - c;
     x[1] = b + wd;
@@ -41,11 +49,13 @@ __host__ __device__ __forceinline__ void small_dft(C* x, int r) {
     const R h = (R)0.86602540378443864676;  // sqrt(3)/2
     C s = x[1] + x[2], d = x[1] - x[2];
     C t;
-    t.x = x[0].x - (R)0.5 * s.x;
-    t.y = x[0].y - (R)0.5 * s.y;
+    t.x = x[0].x - half_of(s.x);
+    t.y = x[0].y - half_of(s.y);
     C u;  // SIGN i sqrt(3)/2 d
-    u.x = -(R)SIGN * h * d.y;
-    u.y = (R)SIGN * h * d.x;
+    u.x = h * d.y;
+    u.y = h * d.x;
+    if (SIGN > 0) u.x = -u.x;
+    else u.y = -u.y;
     x[0] = x[0] + s;
     x[1] = t + u;
     x[2] = t - u;
@@ -61,10 +71,17 @@ __host__ __device__ __forceinline__ void small_dft(C* x, int r) {
     // u1 = SIGN i (s1 b1 + s2 b2), u2 = SIGN i (s2 b1 - s1 b2)
     R v1x = s1 * b1.x + s2 * b2.x, v1y = s1 * b1.y + s2 * b2.y;
     R v2x = s2 * b1.x - s1 * b2.x, v2y = s2 * b1.y - s1 * b2.y;
-    u1.x = -(R)SIGN * v1y;
-    u1.y = (R)SIGN * v1x;
-    u2.x = -(R)SIGN * v2y;
-    u2.y = (R)SIGN * v2x;
+    if (SIGN > 0) {
+      u1.x = -v1y;
+      u1.y = v1x;
+      u2.x = -v2y;
+      u2.y = v2x;
+    } else {
+      u1.x = v1y;
+      u1.y = -v1x;
+      u2.x = v2y;
+      u2.y = -v2x;
+    }
     x[0] = x[0] + a1 + a2;
     x[1] = t1 + u1;
     x[4] = t1 - u1;

@@ -106,6 +106,21 @@ template <int L, int SIGN, typename C> __host__ __device__ __forceinline__ void 
         const int e = (nb * ka) % L;
         if (e == 0) {
           y[ka * B + nb] = t[ka];
+        } else if ((4 * e) % L == 0) {  // a quarter turn: w = (SIGN i)^q, a rotation
+          const int q = (((4 * e) / L) * (SIGN > 0 ? 1 : 3)) % 4;
+          const C v = t[ka];
+          C r;
+          if (q == 1) {
+            r.x = -v.y;
+            r.y = v.x;
+          } else if (q == 2) {
+            r.x = -v.x;
+            r.y = -v.y;
+          } else {
+            r.x = v.y;
+            r.y = -v.x;
+          }
+          y[ka * B + nb] = r;
         } else {
           const C w = cmake<C>(SmallTw<L>::c(e), SIGN * SmallTw<L>::s(e));
           y[ka * B + nb] = t[ka] * w;

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "fft_fast.cuh"
 #include "internal.cuh"
 #include "kernels.cuh"
@@ -56,6 +57,7 @@ template <> struct TwOff<96> { static constexpr int v = 240; };
 constexpr int kTwTotal = 336;
 static __constant__ float2 c_twf[kTwTotal];
 static __constant__ double2 c_twd[kTwTotal];
+static __constant__ float4 c_twdf[kTwTotal];  // double-float: (re.h, re.l, im.h, im.l)
 
 template <typename R, int N> struct ConstTw;
 template <int N> struct ConstTw<float, N> {
@@ -63,6 +65,12 @@ template <int N> struct ConstTw<float, N> {
 };
 template <int N> struct ConstTw<double, N> {
   __device__ __forceinline__ double2 operator()(int e) const { return c_twd[TwOff<N>::v + e]; }
+};
+template <int N> struct ConstTw<dfl, N> {
+  __device__ __forceinline__ cdf operator()(int e) const {
+    const float4 w = c_twdf[TwOff<N>::v + e];
+    return cdf{dfl(w.x, w.y), dfl(w.z, w.w)};
+  }
 };
 
 // Fill this translation unit's tables on the current device (once per device; not inside a
@@ -75,21 +83,26 @@ static inline void init_twiddles() {
   const int lens[6] = {24, 32, 48, 64, 72, 96};
   std::vector<float2> f;
   std::vector<double2> d;
+  std::vector<float4> df;
   for (int n : lens)
     for (int k = 0; k < n; ++k) {
       const double a = 2.0 * M_PI * (double)k / (double)n;
       d.push_back(make_double2(std::cos(a), -std::sin(a)));
       f.push_back(make_float2((float)d.back().x, (float)d.back().y));
+      const dfl re(d.back().x), im(d.back().y);
+      df.push_back(make_float4(re.h, re.l, im.h, im.l));
     }
   CHEBFI_CUDA(cudaMemcpyToSymbol(c_twf, f.data(), sizeof(float2) * f.size()));
   CHEBFI_CUDA(cudaMemcpyToSymbol(c_twd, d.data(), sizeof(double2) * d.size()));
+  CHEBFI_CUDA(cudaMemcpyToSymbol(c_twdf, df.data(), sizeof(float4) * df.size()));
   done[dev] = true;
 }
 
 // sphere block b, columns [c0, c0 + kCBF) -> inverse z transform -> column buffer T
 template <typename R, int N3>
-__device__ __forceinline__ void zinv_body(const cplx<R>* __restrict__ Y, int64_t ldy, cplx<R>* __restrict__ T,
-                                          const FastArgs& fa, const cplx<R>* __restrict__ twz, int c0, int64_t b,
+__device__ __forceinline__ void zinv_body(const cplx<typename SphT<R>::type>* __restrict__ Y, int64_t ldy,
+                                          cplx<R>* __restrict__ T, const FastArgs& fa,
+                                          const cplx<R>* __restrict__ twz, int c0, int64_t b,
                                           unsigned char* smem_raw) {
   (void)twz;
   const ConstTw<R, N3> tw;
@@ -99,9 +112,9 @@ __device__ __forceinline__ void zinv_body(const cplx<R>* __restrict__ Y, int64_t
   for (int i = threadIdx.x; i < kCBF * fa.zpitch; i += blockDim.x) lines[i] = zero;
   __syncthreads();
   const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
-  const cplx<R>* y = Y + b * ldy;
+  const auto* y = Y + b * ldy;
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
-    lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]] = y[j];
+    lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]] = to_compute<cplx<R>>(y[j]);
   __syncthreads();
   LineMap lm;
   lm.stride = fa.zpitch;
@@ -340,8 +353,11 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
 // the epilogue (Z, its bf16 planes, and the Chebyshev combination T = a (Z - c Y) - b Yprev)
 template <typename R, int N3>
 __device__ __forceinline__ void zfwd_body(const cplx<R>* __restrict__ T, const FastArgs& fa,
-                                          const cplx<R>* __restrict__ twz, const R* __restrict__ K,
-                                          const LocalEpi<R>& ep, int c0, int64_t b, unsigned char* smem_raw) {
+                                          const cplx<R>* __restrict__ twz,
+                                          const typename SphT<R>::type* __restrict__ K,
+                                          const LocalEpi<typename SphT<R>::type>& ep, int c0, int64_t b,
+                                          unsigned char* smem_raw) {
+  using CS = cplx<typename SphT<R>::type>;
   (void)twz;
   const ConstTw<R, N3> tw;
   cplx<R>* lines = reinterpret_cast<cplx<R>*>(smem_raw) + N3;
@@ -356,23 +372,25 @@ __device__ __forceinline__ void zfwd_body(const cplx<R>* __restrict__ T, const F
   lm.stride = fa.zpitch;
   fast::lines_G<N3, -1>(lines, nc, lm, 1, tw);
   const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
-  const cplx<R>* y = ep.Y + b * ep.ldy;
+  const CS* y = ep.Y + b * ep.ldy;
+  const R inv_n3 = to_compute<R>(ep.inv_n3), ea = to_compute<R>(ep.a), ec = to_compute<R>(ep.c),
+          eb = to_compute<R>(ep.bprev);
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const cplx<R> v = lines[(fa.pw_line[j] - c0) * fa.zpitch + fa.pw_z[j]];
-    const cplx<R> yj = y[j];
-    const R k = K[j];
+    const cplx<R> yj = to_compute<cplx<R>>(y[j]);
+    const R k = to_compute<R>(K[j]);
     cplx<R> zj;
-    zj.x = v.x * ep.inv_n3 + k * yj.x;
-    zj.y = v.y * ep.inv_n3 + k * yj.y;
-    if (ep.Z) ep.Z[b * ep.ldz + j] = zj;
-    if (ep.Zhi) epi_split_z(ep, b, j, (float)zj.x, (float)zj.y);
+    zj.x = v.x * inv_n3 + k * yj.x;
+    zj.y = v.y * inv_n3 + k * yj.y;
+    if (ep.Z) ep.Z[b * ep.ldz + j] = to_store<CS>(zj);
+    if (ep.Zhi) epi_split_z(ep, b, j, to_f32(zj.x), to_f32(zj.y));
     if (ep.T) {
       cplx<R> tp = cmake<cplx<R>>(0.0, 0.0);
-      if (ep.Yprev) tp = ep.Yprev[b * ep.ldt + j];
+      if (ep.Yprev) tp = to_compute<cplx<R>>(ep.Yprev[b * ep.ldt + j]);
       cplx<R> o;
-      o.x = ep.a * (zj.x - ep.c * yj.x) - ep.bprev * tp.x;
-      o.y = ep.a * (zj.y - ep.c * yj.y) - ep.bprev * tp.y;
-      ep.T[b * ep.ldt + j] = o;
+      o.x = ea * (zj.x - ec * yj.x) - eb * tp.x;
+      o.y = ea * (zj.y - ec * yj.y) - eb * tp.y;
+      ep.T[b * ep.ldt + j] = to_store<CS>(o);
     }
   }
 }

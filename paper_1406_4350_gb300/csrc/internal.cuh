@@ -292,6 +292,8 @@ struct chebfi_ctx {
   bool fast_fft = false;         // cubic grid of a compiled size: two-pass FFT kernels
   chebfi::DevBuf<double> d_vs;   // V_loc in split order [z'][x'][y'] for those kernels
   chebfi::DevBuf<float> d_vsf;
+  chebfi::DevBuf<float2> d_vsdf;               // the same table as double-float pairs (h, l)
+  int fft64 = CHEBFI_FFT64_DOUBLE_FLOAT;       // arithmetic of the FP64 path's transforms
   double vmax = 0.0;
 
   int64_t nproj = 0;

@@ -80,6 +80,33 @@ def test_apply_H_S_Sinv_fp64(name):
     _close(_np(g.apply_Sinv(Y)), op.apply_Sinv(cell.Y0), TOL64)
 
 
+@pytest.mark.parametrize("name", ["nc24", "paw48_37"])
+def test_fp64_fft_double_float_and_native(name):
+    """The FP64 path's FFT in double-float (initial) and on the FP64 units: both within the FP64
+    tolerance of the oracle for apply_H and a degree-8 filter, and within 1e-12 of each other."""
+    from paper_1406_4350_gb300._lib import FFT64_DOUBLE_FLOAT, FFT64_NATIVE
+    cell = CELLS[name]()
+    op = PWOperator.from_cell(cell)
+    g = _ctx(cell)
+    lo = float(ch.rayleigh_quotients(op, cell.Y0).max())
+    hi = ch.upper_bound(op, "rigorous")
+    ref_f = ch.filter_reuse(op, cell.Y0, 8, lo, hi)
+    out = {}
+    for mode in (FFT64_DOUBLE_FLOAT, FFT64_NATIVE):
+        g.set_fft64(mode)
+        h = _np(g.apply_H(_F(cell.Y0)))
+        _close(h, op.apply_H(cell.Y0), TOL64)
+        Y = _F(cell.Y0)
+        g.cheb_filter(Y, 8, lo, hi)
+        f = _np(Y)
+        _close(f, ref_f, TOL64)
+        out[mode] = (h, f)
+    _close(out[FFT64_DOUBLE_FLOAT][0], out[FFT64_NATIVE][0], 1e-12)
+    _close(out[FFT64_DOUBLE_FLOAT][1], out[FFT64_NATIVE][1], 1e-12)
+    with pytest.raises(Exception):
+        g.set_fft64(7)
+
+
 @pytest.mark.parametrize("name", ["tiny_paw", "nc24", "paw48_37"])
 def test_apply_H_fp32(name):
     from paper_1406_4350_gb300 import F32
