@@ -241,12 +241,17 @@ __global__ void __launch_bounds__(kThreads) k_zinv_f(const cplx<typename SphT<R>
   fk::zinv_body<R, N3>(Y, ldy, T, fa, twz, blockIdx.x * kCBF, blockIdx.y, smem_raw);
 }
 
+// threads of a plane block: the double-float plane (16 bytes a point, one block per SM)
+// takes 16 warps to keep its FP32 pipes fed, the others 8 with three blocks per SM
+template <typename R> struct PlaneThreads { static constexpr int v = kThreads; };
+template <> struct PlaneThreads<dfl> { static constexpr int v = 2 * kThreads; };
+
 template <typename R, int N>
-__global__ void __launch_bounds__(kThreads) k_plane_f(cplx<R>* __restrict__ T, const R* __restrict__ Vs, FastArgs fa,
-                                                      const cplx<R>* __restrict__ twxy) {
+__global__ void __launch_bounds__(PlaneThreads<R>::v) k_plane_f(cplx<R>* __restrict__ T, const R* __restrict__ Vs,
+                                                                FastArgs fa, const cplx<R>* __restrict__ twxy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   (void)twxy;
-  fk::plane_body_pruned<R, N>(T, Vs, fa, blockIdx.x, blockIdx.y, smem_raw);
+  fk::plane_body_pruned<R, N, PlaneThreads<R>::v>(T, Vs, fa, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 template <typename R, int N3>
@@ -311,7 +316,8 @@ void fast_launch(chebfi_ctx* ctx, const cplx<typename SphT<R>::type>* Y, int64_t
     dim3 gz((s.ncol + kCBF - 1) / kCBF, nbc);
     const double esz = sizeof(cplx<R>), col = (double)N * s.ncol * nbc * esz, sph = (double)ctx->npw * nbc * esz;
     CHEBFI_LAUNCH_W("k_zinv", st, sph + col, k_zinv_f<R, N><<<gz, kThreads, zbytes, st>>>(Y + b0 * ldy, ldy, T, fa, tw));
-    CHEBFI_LAUNCH_W("k_plane", st, 2.0 * col, k_plane_f<R, N><<<dim3(N, nbc), kThreads, pbytes, st>>>(T, Vs, fa, tw));
+    CHEBFI_LAUNCH_W("k_plane", st, 2.0 * col,
+                    k_plane_f<R, N><<<dim3(N, nbc), PlaneThreads<R>::v, pbytes, st>>>(T, Vs, fa, tw));
     LocalEpi<S> e = ep;
     e.Y = ep.Y + b0 * ep.ldy;
     if (e.Z) e.Z = ep.Z + b0 * ep.ldz;

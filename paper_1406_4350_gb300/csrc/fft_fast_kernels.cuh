@@ -186,14 +186,14 @@ __device__ __forceinline__ void plane_body(cplx<R>* __restrict__ T, const R* __r
 // the last y pass stores the columns straight to the column buffer (no gather).  Same
 // arithmetic, in the same order.  The row pitch is the compile-time N + 1 (odd: the
 // row-wise passes meet no bank conflicts), so every shared-memory offset of a pass is an
-// immediate; where NB warps tile the block (N = 64, 96) each warp of an x pass keeps one nb
-// and its twiddles in registers.
-template <typename R, int N>
+// immediate; where the block's NT / 32 warps are a multiple of NB (N = 64, 96) each warp of
+// an x pass keeps one nb and its twiddles in registers.
+template <typename R, int N, int NT = kThreadsF>
 __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const R* __restrict__ Vs,
                                                   const FastArgs& fa, int z, int64_t b, unsigned char* smem_raw) {
   using C = cplx<R>;
-  constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB, P = N + 1;
-  constexpr bool kWarpNb = N % 32 == 0 && NB * 32 == kThreadsF;
+  constexpr int NA = fast::Plan<N>::NA, NB = fast::Plan<N>::NB, P = N + 1, W = NT / 32;
+  constexpr bool kWarpNb = N % 32 == 0 && W % NB == 0;
   const ConstTw<R, N> tw;
   C* plane = reinterpret_cast<C*>(smem_raw) + N;
   const C zero = cmake<C>(0.0, 0.0);
@@ -241,12 +241,12 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
   __syncthreads();
   // x, inverse: F's pass A on every y line, slots outside the active range are zero
   if constexpr (kWarpNb) {
-    const int nb = threadIdx.x / 32, d = nb - lo;
+    const int warp = threadIdx.x / 32, nb = warp % NB, d = nb - lo;
     C w[NA];
 #pragma unroll
     for (int ka = 1; ka < NA; ++ka) w[ka] = fast::twN<+1>(tw, nb * ka);
 #pragma unroll 1
-    for (int yy = threadIdx.x % 32; yy < N; yy += 32) {
+    for (int yy = threadIdx.x % 32 + 32 * (warp / NB); yy < N; yy += 32 * (W / NB)) {
       C* a = plane + yy + nb * P;
       C v[NA];
 #pragma unroll
@@ -295,9 +295,9 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
   __syncthreads();
   // x, forward: G's pass A, storing only the rows the y pass reads
   if constexpr (kWarpNb) {
-    const int nb = threadIdx.x / 32, d = nb - lo;
+    const int warp = threadIdx.x / 32, nb = warp % NB, d = nb - lo;
 #pragma unroll 1
-    for (int yy = threadIdx.x % 32; yy < N; yy += 32) {
+    for (int yy = threadIdx.x % 32 + 32 * (warp / NB); yy < N; yy += 32 * (W / NB)) {
       C* a = plane + yy + nb * P;
       C v[NA];
 #pragma unroll
