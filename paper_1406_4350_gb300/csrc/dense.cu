@@ -415,7 +415,7 @@ void jacobi_eigh_t(int64_t n0, cplx<R>* A, int64_t lda, R* w, cplx<R>* V, int64_
   CHEBFI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   CHEBFI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CHEBFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_sweep<R>, 256, 0));
-  const int coop_blocks = std::min(sms * std::min(per_sm, 4), 1024);
+  const int coop_blocks = sms * std::min(per_sm, 8);
   set_identity_t<R>(n0, Vtmp, n0, st);
   const int max_sweeps = 40;
   const unsigned parts = (unsigned)std::min<int64_t>(kParts, std::max<int64_t>(1, n0 * n0 / 4096));
