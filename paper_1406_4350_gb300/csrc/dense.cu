@@ -226,6 +226,9 @@ __device__ __forceinline__ void rot2(C& a, C& b, R c, R s, C ph) {
   b = nb;
 }
 
+// items of one round: h x h blocks of A, n rows x h column pairs of V
+__host__ __device__ inline int64_t jac_items(int64_t h, int64_t n) { return h * h + n * h; }
+
 // One round of rotations in one pass: item (t1, t2) maps the 2 x 2 block of A on rows
 // {p1, q1} and columns {p2, q2} to U1^H A U2 (the pairs are disjoint, so every element of A
 // belongs to exactly one block); the remaining items apply V <- V U2 on columns {p2, q2}.
@@ -307,7 +310,7 @@ __global__ void k_jac_sweep(int64_t n0, int64_t n, cplx<R>* A, int64_t lda, cplx
   for (int64_t round = 0; round < n - 1; ++round) {
     for (int64_t t = tid; t < h; t += nthreads) jac_params_item<R>(t, n0, n, round, A, lda, rot, pairs);
     grid_barrier(bar, bar + 1, gridDim.x, status);
-    for (int64_t i = tid; i < h * h + n0 * h; i += nthreads) jac_apply_item<R>(i, h, n0, A, lda, V, ldv, rot, pairs);
+    for (int64_t i = tid; i < jac_items(h, n0); i += nthreads) jac_apply_item<R>(i, h, n0, A, lda, V, ldv, rot, pairs);
     grid_barrier(bar, bar + 1, gridDim.x, status);
   }
 }
@@ -458,7 +461,7 @@ void jacobi_eigh_t(int64_t n0, cplx<R>* A, int64_t lda, R* w, cplx<R>* V, int64_
                       k_jac_params<R><<<nblk(n / 2), 256, 0, st>>>(n0, n, round, A, lda, rot, pairs));
         const int64_t h = n / 2;
         CHEBFI_LAUNCH("k_jac_apply", st,
-                      k_jac_apply<R><<<nblk(h * h + n0 * h), 256, 0, st>>>(h, n0, A, lda, Vtmp, n0, rot, pairs));
+                      k_jac_apply<R><<<nblk(jac_items(h, n0)), 256, 0, st>>>(h, n0, A, lda, Vtmp, n0, rot, pairs));
       }
     }
   }
@@ -495,12 +498,14 @@ __global__ void k_oa_update(int64_t n, const double2* __restrict__ G, int64_t ld
                             double2* __restrict__ M, int64_t ldm, unsigned long long* __restrict__ emax,
                             int* __restrict__ npairs, int2* __restrict__ pairs, int cap) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  const int64_t i = idx % n, j = idx / n;
-  const double2 g = G[i + j * ldg];
+  const bool in = idx < n * n;
+  const int64_t i = in ? idx % n : 0, j = in ? idx / n : 0;
+  const double2 g = in ? G[i + j * ldg] : make_double2(1.0, 0.0);
   double2 e;
-  double mag;
-  if (i == j) {
+  double mag = 0.0;
+  if (!in) {
+    e = make_double2(0.0, 0.0);
+  } else if (i == j) {
     e = make_double2(0.5 * (1.0 - g.x), 0.0);
     mag = fabs(e.x);
   } else {
@@ -520,8 +525,16 @@ __global__ void k_oa_update(int64_t n, const double2* __restrict__ G, int64_t ld
     }
     mag = hypot(e.x, e.y);
   }
-  atomicMax(emax, (unsigned long long)__double_as_longlong(mag));
-  M[i + j * ldm] = make_double2((i == j ? 1.0 : 0.0) + e.x, e.y);
+  // max |E| over the warp first (the bits of non-negative doubles order like their values,
+  // a NaN above all), then one atomic per warp: one per element serialises on the word
+  unsigned long long bits = (unsigned long long)__double_as_longlong(mag);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = other > bits ? other : bits;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(emax, bits);
+  if (in) M[i + j * ldm] = make_double2((i == j ? 1.0 : 0.0) + e.x, e.y);
 }
 
 // ascending order of w (stable), columns of X permuted alike
