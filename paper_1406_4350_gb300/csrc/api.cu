@@ -201,6 +201,35 @@ void gemm64(chebfi_ctx* ctx, bool conjA, bool conjB, int64_t M, int64_t N, int64
   oz_gemm(*a, z.B, alpha, beta, C, ldc, lower, z.R, ctx->d_status.p, st, tag);
 }
 
+// A = L L^H (A's lower triangle becomes L, its upper triangle zero) and Li = L^{-1}, by
+// halving: with A = [A11 .; A21 A22],
+//   L11, Li11 from A11;  L21 = A21 Li11^H;  A22 <- A22 - L21 L21^H;  L22, Li22 from A22;
+//   Li21 = -Li22 L21 Li11,
+// so all but the leaves (n <= 256: the blocked kernels) are FP64-accurate GEMMs on the
+// tensor cores.  T: scratch of n^2 / 2 complex values.
+void chol_inv(chebfi_ctx* ctx, int64_t n, double2* A, int64_t lda, double2* Li, int64_t ldi, double2* T,
+              cudaStream_t st) {
+  DevBuf<double2>* ws = &ctx->w.splitk;
+  if (n <= 256) {
+    cholesky(n, A, lda, ctx->d_status.p, st, ws);
+    set_identity(n, Li, ldi, st);
+    trsm_lower(n, n, A, lda, Li, ldi, st, ws);
+    return;
+  }
+  const int64_t n1 = (n / 2 + 31) / 32 * 32, n2 = n - n1;
+  double2 *A21 = A + n1, *A22 = A + n1 + n1 * lda, *Li11 = Li, *Li21 = Li + n1, *Li22 = Li + n1 + n1 * ldi;
+  const size_t z = sizeof(double2);
+  chol_inv(ctx, n1, A, lda, Li11, ldi, T, st);
+  gemm64(ctx, false, true, n2, n1, n1, 1.0, A21, lda, Li11, ldi, 0.0, T, n2, st, ws, "gemm_chol");
+  CHEBFI_CUDA(cudaMemcpy2DAsync(A21, lda * z, T, n2 * z, n2 * z, n1, cudaMemcpyDeviceToDevice, st));
+  gemm64(ctx, false, true, n2, n2, n1, -1.0, A21, lda, A21, lda, 1.0, A22, lda, st, ws, "gemm_chol");
+  chol_inv(ctx, n2, A22, lda, Li22, ldi, T, st);
+  gemm64(ctx, false, false, n2, n1, n1, 1.0, A21, lda, Li11, ldi, 0.0, T, n2, st, ws, "gemm_chol");
+  gemm64(ctx, false, false, n2, n1, n2, -1.0, Li22, ldi, T, n2, 0.0, Li21, ldi, st, ws, "gemm_chol");
+  CHEBFI_CUDA(cudaMemset2DAsync(A + n1 * lda, lda * z, 0, n1 * z, n2, st));   // upper blocks
+  CHEBFI_CUDA(cudaMemset2DAsync(Li + n1 * ldi, ldi * z, 0, n1 * z, n2, st));
+}
+
 // the GEMM of the form's precision: FP64 through gemm64, FP32 on the CUDA cores
 template <typename R>
 void cgemm(chebfi_ctx* ctx, bool conjA, bool conjB, int64_t M, int64_t N, int64_t K, double alpha, const cplx<R>* A,
@@ -713,9 +742,7 @@ void rr_on_Ya(chebfi_ctx* ctx, int64_t nb, double* evals, double* resid, cudaStr
   scale_sym(nb, Hs, nb, w.dvec1.p, st);
   scale_sym(nb, Ss, nb, w.dvec1.p, st);
   // S~ = L L^H, C = L^{-1} H~ L^{-H}
-  cholesky(nb, Ss, nb, ctx->d_status.p, st, ws);
-  set_identity(nb, Li, nb, st);
-  trsm_lower(nb, nb, Ss, nb, Li, nb, st, ws);
+  chol_inv(ctx, nb, Ss, nb, Li, nb, X, st);
   gemm64(ctx, false, false, nb, nb, nb, 1.0, Li, nb, Hs, nb, 0.0, X, nb, st, ws, "gemm_rr");
   gemm64(ctx, false, true, nb, nb, nb, 1.0, X, nb, Li, nb, 0.0, Hs, nb, st, ws, "gemm_rr");
   hermitize(nb, Hs, nb, st);
@@ -754,6 +781,7 @@ void ortho_on_Ya(chebfi_ctx* ctx, int64_t nb, cudaStream_t st) {
   w.pb.alloc(np);
   w.small2.alloc(ns);
   w.small3.alloc(ns);
+  w.small4.alloc(ns);
   DevBuf<double2>* ws = &w.splitk;
   double2 *Ss = w.small2.p, *Li = w.small3.p, *Y = w.Ya.p;
   scan_nonfinite(npw, nb, Y, npw, ctx->d_status.p, st);
@@ -764,10 +792,8 @@ void ortho_on_Ya(chebfi_ctx* ctx, int64_t nb, cudaStream_t st) {
     gemm64(ctx, true, false, nb, nb, nq, 1.0, w.pa.p, nq, w.pb.p, nq, 1.0, Ss, nb, st, ws);
   }
   hermitize(nb, Ss, nb, st);
-  cholesky(nb, Ss, nb, ctx->d_status.p, st, ws);
+  chol_inv(ctx, nb, Ss, nb, Li, nb, w.small4.p, st);
   check_status(ctx, st, "orthonormalise");
-  set_identity(nb, Li, nb, st);
-  trsm_lower(nb, nb, Ss, nb, Li, nb, st, ws);
   gemm64(ctx, false, true, npw, nb, nb, 1.0, Y, npw, Li, nb, 0.0, w.tmp.p, npw, st, ws);
   std::swap(w.Ya.p, w.tmp.p);
   std::swap(w.Ya.n, w.tmp.n);
