@@ -579,6 +579,311 @@ __global__ void k_scatter_vals(int k, const int* __restrict__ idx, const double*
   if (b < k) dst[idx[b]] = src[b];
 }
 
+// ------------------------------------------------------------------ blocked Jacobi (FP32)
+// The two-sided cyclic Jacobi method on blocks: the n columns form n / 32 blocks, paired by
+// the round-robin tournament (n / 32 - 1 rounds per sweep, n / 64 disjoint pairs per round).
+// For a pair (I, J) the 64 x 64 subproblem A[IJ, IJ] is diagonalised in shared memory by the
+// scalar method (same rotations as above) giving a unitary W, then A <- W^H A W on rows and
+// columns I u J and V <- V W: each round is one pass over A and V as small dense products
+// instead of 63 passes of scalar rotations, which the scalar method spends in grid barriers
+// and load latency.
+namespace bj {
+constexpr int B = 32, S2 = 64, PS = S2 + 1;  // block, subproblem, shared pitch
+
+__device__ __forceinline__ int player(int pos, int round, int m) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1);
+}
+__device__ __forceinline__ void blocks_of(int pair, int round, int nbk, int& I, int& J) {
+  I = player(pair, round, nbk);
+  J = player(nbk - 1 - pair, round, nbk);
+  if (I > J) {
+    const int t = I;
+    I = J;
+    J = t;
+  }
+}
+__device__ __forceinline__ int gidx(int l, int I, int J) { return l < B ? I * B + l : J * B + (l - B); }
+
+// One CTA per pair: gather the subproblem, diagonalise it (up to `sweeps` cyclic sweeps, or
+// until its off-diagonal part is below tol of its norm), write the rotation W (64 x 64,
+// column-major) to Wout[pair].
+__global__ void __launch_bounds__(256) k_bj_solve(const float2* __restrict__ A, int64_t lda, int nbk, int round,
+                                                  float2* __restrict__ Wout, int sweeps, float tol) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* S = reinterpret_cast<float2*>(smem);  // S[i + PS j] = element (i, j)
+  float2* W = S + S2 * PS;
+  RotT<float>* rot = reinterpret_cast<RotT<float>*>(W + S2 * PS);
+  int* pq = reinterpret_cast<int*>(rot + S2 / 2);
+  __shared__ float red[2][256];
+  int I, J;
+  blocks_of(blockIdx.x, round, nbk, I, J);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < S2 * S2; e += blockDim.x) {
+    const int i = e % S2, j = e / S2;
+    S[i + PS * j] = A[gidx(i, I, J) + (int64_t)gidx(j, I, J) * lda];
+    W[i + PS * j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int sw = 0; sw < sweeps; ++sw) {
+    float o = 0.f, t = 0.f;
+    for (int e = tid; e < S2 * S2; e += blockDim.x) {
+      const int i = e % S2, j = e / S2;
+      const float2 v = S[i + PS * j];
+      const float m = v.x * v.x + v.y * v.y;
+      t += m;
+      if (i != j) o += m;
+    }
+    red[0][tid] = o;
+    red[1][tid] = t;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (tid < h) {
+        red[0][tid] += red[0][tid + h];
+        red[1][tid] += red[1][tid + h];
+      }
+      __syncthreads();
+    }
+    const bool done = red[0][0] <= tol * tol * red[1][0];
+    __syncthreads();
+    if (done) break;
+    for (int r = 0; r < S2 - 1; ++r) {
+      if (tid < S2 / 2) {
+        int p = player(tid, r, S2), q = player(S2 - 1 - tid, r, S2);
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        RotT<float> rr;
+        rr.c = 1.f;
+        rr.s = 0.f;
+        rr.ph = make_float2(1.f, 0.f);
+        const float2 h = S[p + PS * q];
+        const float g = hypotf(h.x, h.y);
+        const float app = S[p + PS * p].x, aqq = S[q + PS * q].x;
+        if (g > JacEps<float>::tiny && g > JacEps<float>::v * sqrtf(fabsf(app * aqq))) {
+          const float zeta = (aqq - app) / (2.f * g);
+          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+          rr.c = 1.f / sqrtf(1.f + tt * tt);
+          rr.s = tt * rr.c;
+          rr.ph = make_float2(h.x / g, h.y / g);
+        }
+        rot[tid] = rr;
+        pq[2 * tid] = p;
+        pq[2 * tid + 1] = q;
+      }
+      __syncthreads();
+      // 2 x 2 blocks of S: U1^H S U2
+      for (int it = tid; it < (S2 / 2) * (S2 / 2); it += blockDim.x) {
+        const int t1 = it % (S2 / 2), t2 = it / (S2 / 2);
+        const RotT<float> r1 = rot[t1], r2 = rot[t2];
+        if (r1.s == 0.f && r2.s == 0.f) continue;
+        const int p1 = pq[2 * t1], q1 = pq[2 * t1 + 1], p2 = pq[2 * t2], q2 = pq[2 * t2 + 1];
+        float2 m00 = S[p1 + PS * p2], m10 = S[q1 + PS * p2], m01 = S[p1 + PS * q2], m11 = S[q1 + PS * q2];
+        if (r1.s != 0.f) {
+          rot2(m00, m10, r1.c, r1.s, r1.ph);
+          rot2(m01, m11, r1.c, r1.s, r1.ph);
+        }
+        if (r2.s != 0.f) {
+          const float2 c2 = conjg(r2.ph);
+          rot2(m00, m01, r2.c, r2.s, c2);
+          rot2(m10, m11, r2.c, r2.s, c2);
+        }
+        S[p1 + PS * p2] = m00;
+        S[q1 + PS * p2] = m10;
+        S[p1 + PS * q2] = m01;
+        S[q1 + PS * q2] = m11;
+      }
+      // W <- W U on columns {p, q}
+      for (int it = tid; it < S2 * (S2 / 2); it += blockDim.x) {
+        const int i = it % S2, tt = it / S2;
+        const RotT<float> rr = rot[tt];
+        if (rr.s == 0.f) continue;
+        const int p = pq[2 * tt], q = pq[2 * tt + 1];
+        float2 a = W[i + PS * p], b = W[i + PS * q];
+        rot2(a, b, rr.c, rr.s, conjg(rr.ph));
+        W[i + PS * p] = a;
+        W[i + PS * q] = b;
+      }
+      __syncthreads();
+    }
+  }
+  float2* wo = Wout + (int64_t)blockIdx.x * S2 * S2;
+  for (int e = tid; e < S2 * S2; e += blockDim.x) wo[e] = W[(e % S2) + PS * (e / S2)];
+}
+
+// columns I u J of M (A or V; blockIdx.z) times W: a CTA takes 64 rows, in place
+__global__ void __launch_bounds__(256) k_bj_cols(float2* A, int64_t lda, float2* V, int64_t ldv, int nbk, int round,
+                                                 const float2* __restrict__ Win, int64_t nrows) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* W = reinterpret_cast<float2*>(smem);  // W[l + PS c]
+  float2* X = W + S2 * PS;                       // X[row + PS l]
+  int I, J;
+  blocks_of(blockIdx.y, round, nbk, I, J);
+  float2* M = blockIdx.z == 0 ? A : V;
+  const int64_t ld = blockIdx.z == 0 ? lda : ldv;
+  const int64_t r0 = (int64_t)blockIdx.x * S2;
+  const float2* w = Win + (int64_t)blockIdx.y * S2 * S2;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < S2 * S2; e += blockDim.x) {
+    const int a = e % S2, b = e / S2;
+    W[a + PS * b] = w[e];
+    const int64_t r = r0 + a;
+    X[a + PS * b] = r < nrows ? M[r + (int64_t)gidx(b, I, J) * ld] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // thread: rows ri + 16 k (k < 4), columns ci + 16 m (m < 4)
+  const int ri = tid % 16, ci = tid / 16;
+  float2 acc[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[k][m] = make_float2(0.f, 0.f);
+  for (int l = 0; l < S2; ++l) {
+    float2 x[4], y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = X[ri + 16 * k + PS * l];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) y[m] = W[l + PS * (ci + 16 * m)];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        acc[k][m].x = fmaf(x[k].x, y[m].x, fmaf(-x[k].y, y[m].y, acc[k][m].x));
+        acc[k][m].y = fmaf(x[k].x, y[m].y, fmaf(x[k].y, y[m].x, acc[k][m].y));
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t r = r0 + ri + 16 * k;
+    if (r >= nrows) continue;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) M[r + (int64_t)gidx(ci + 16 * m, I, J) * ld] = acc[k][m];
+  }
+}
+
+// rows I u J of A: W^H times them; a CTA takes 64 columns, in place
+__global__ void __launch_bounds__(256) k_bj_rows(float2* A, int64_t lda, int nbk, int round,
+                                                 const float2* __restrict__ Win, int64_t ncols) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* W = reinterpret_cast<float2*>(smem);  // W[l + PS c]
+  float2* Z = W + S2 * PS;                       // Z[l + PS col]
+  int I, J;
+  blocks_of(blockIdx.y, round, nbk, I, J);
+  const int64_t c0 = (int64_t)blockIdx.x * S2;
+  const float2* w = Win + (int64_t)blockIdx.y * S2 * S2;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < S2 * S2; e += blockDim.x) {
+    const int a = e % S2, b = e / S2;
+    W[a + PS * b] = w[e];
+    const int64_t c = c0 + b;
+    Z[a + PS * b] = c < ncols ? A[gidx(a, I, J) + c * lda] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // thread: output rows li + 16 k, columns cj + 16 m; out(l, col) = sum_k conj(W(k, l)) Z(k, col)
+  const int li = tid % 16, cj = tid / 16;
+  float2 acc[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[k][m] = make_float2(0.f, 0.f);
+  for (int q = 0; q < S2; ++q) {
+    float2 wv[4], z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) wv[k] = W[q + PS * (li + 16 * k)];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) z[m] = Z[q + PS * (cj + 16 * m)];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {  // conj(wv) z
+        acc[k][m].x = fmaf(wv[k].x, z[m].x, fmaf(wv[k].y, z[m].y, acc[k][m].x));
+        acc[k][m].y = fmaf(wv[k].x, z[m].y, fmaf(-wv[k].y, z[m].x, acc[k][m].y));
+      }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int64_t c = c0 + cj + 16 * m;
+    if (c >= ncols) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) A[gidx(li + 16 * k, I, J) + c * lda] = acc[k][m];
+  }
+}
+
+// zero-padded copy with pad values on the extra diagonal entries
+__global__ void k_bj_pad(int64_t n0, int64_t np, const float2* __restrict__ A, int64_t lda, float2* __restrict__ Ap,
+                         float pad) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= np * np) return;
+  const int64_t i = e % np, j = e / np;
+  Ap[e] = (i < n0 && j < n0) ? A[i + j * lda] : make_float2(i == j ? pad : 0.f, 0.f);
+}
+}  // namespace bj
+
+// The blocked FP32 Jacobi (bj:: kernels) on A (n0 x n0, destroyed): ascending w and V
+// (ld ldv).  The matrix is padded to a multiple of 64 with decoupled diagonal entries above
+// every eigenvalue (2 ||A||_F + 1), which no rotation touches and the sort puts last.
+bool block_jacobi_f32(int64_t n0, float2* A, int64_t lda, float* w, float2* V, int64_t ldv, cudaStream_t st,
+                      DevBuf<double2>* ws, double tol_conv, double tol_stall) {
+  if (n0 < 128) return false;
+  const int64_t np = (n0 + bj::S2 - 1) / bj::S2 * bj::S2;
+  const int nbk = (int)(np / bj::B), npairs = nbk / 2;
+  constexpr int kParts = 256;
+  // workspace in float2 slots: Ap, Vp, Vs (np^2 each), W (npairs x 64^2), wp (np / 2 + 1),
+  // norm partials and sums (2 kParts + 2 doubles)
+  const size_t nn = (size_t)np * np, nw = (size_t)npairs * bj::S2 * bj::S2;
+  const size_t total = 3 * nn + nw + np / 2 + 1 + 2 * kParts + 2;
+  ws->alloc(total / 2 + 1);
+  float2* Ap = reinterpret_cast<float2*>(ws->p);
+  float2* Vp = Ap + nn;
+  float2* Vs = Vp + nn;
+  float2* Wb = Vs + nn;
+  float* wp = reinterpret_cast<float*>(Wb + nw);
+  double* part = reinterpret_cast<double*>(Wb + nw + np / 2 + 1);
+  double* nrm = part + 2 * kParts;
+  auto norms = [&](const float2* M, int64_t n, int64_t ld, double& off, double& tot) {
+    const unsigned parts = (unsigned)std::min<int64_t>(kParts, std::max<int64_t>(1, n * n / 4096));
+    CHEBFI_LAUNCH("k_offnorm", st, k_offnorm_part<float><<<parts, 256, 0, st>>>(n, M, ld, part));
+    CHEBFI_LAUNCH("k_offnorm", st, k_offnorm_sum<<<1, 32, 0, st>>>((int)parts, part, nrm));
+    double hn[2];
+    CHEBFI_CUDA(cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    CHEBFI_CUDA(cudaStreamSynchronize(st));
+    off = std::sqrt(hn[0]);
+    tot = std::sqrt(hn[1]);
+  };
+  double off = 0.0, tot = 0.0, tot_p = 0.0;
+  norms(A, n0, lda, off, tot);  // ||A||_F: the sweeps keep it (unitary similarity), so it is the scale
+  if (!std::isfinite(tot)) return false;  // the scalar path reports it
+  CHEBFI_LAUNCH("k_bj_pad", st, bj::k_bj_pad<<<nblk((int64_t)nn), 256, 0, st>>>(n0, np, A, lda, Ap, (float)(2.0 * tot + 1.0)));
+  set_identity_t<float>(np, Vp, np, st);
+  const size_t s_solve = (size_t)2 * bj::S2 * bj::PS * sizeof(float2) + bj::S2 / 2 * sizeof(RotT<float>) + bj::S2 * sizeof(int);
+  const size_t s_mul = (size_t)2 * bj::S2 * bj::PS * sizeof(float2);
+  CHEBFI_CUDA(cudaFuncSetAttribute(bj::k_bj_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_solve));
+  CHEBFI_CUDA(cudaFuncSetAttribute(bj::k_bj_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_mul));
+  CHEBFI_CUDA(cudaFuncSetAttribute(bj::k_bj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_mul));
+  const unsigned tiles = (unsigned)(np / bj::S2);
+  double prev_off = INFINITY;
+  for (int sweep = 0; sweep <= 40; ++sweep) {
+    norms(Ap, np, np, off, tot_p);  // the pads add nothing off the diagonal
+    if (!std::isfinite(tot_p)) break;
+    if (off <= tol_conv * tot || off == 0.0 || (sweep > 2 && off > 0.5 * prev_off && off <= tol_stall * tot)) break;
+    if (sweep == 40) break;
+    prev_off = off;
+    // rounds of the block tournament; work: the subproblems' rotations and the two products
+    for (int round = 0; round < nbk - 1; ++round) {
+      CHEBFI_LAUNCH("k_bj_solve", st, bj::k_bj_solve<<<npairs, 256, s_solve, st>>>(Ap, np, nbk, round, Wb, 6, 1e-7f));
+      CHEBFI_LAUNCH_W("k_bj_update", st, 3.0 * 8.0 * (double)np * bj::S2 * bj::S2 * npairs,
+                      bj::k_bj_cols<<<dim3(tiles, npairs, 2), 256, s_mul, st>>>(Ap, np, Vp, np, nbk, round, Wb, np));
+      CHEBFI_LAUNCH("k_bj_update", st, bj::k_bj_rows<<<dim3(tiles, npairs), 256, s_mul, st>>>(Ap, np, nbk, round, Wb, np));
+    }
+  }
+  CHEBFI_LAUNCH("k_eig_sort", st, k_eig_sort<float><<<(unsigned)np, 128, 0, st>>>(np, Ap, np, Vp, np, wp, Vs, np));
+  CHEBFI_CUDA(cudaMemcpyAsync(w, wp, sizeof(float) * n0, cudaMemcpyDeviceToDevice, st));
+  CHEBFI_CUDA(cudaMemcpy2DAsync(V, ldv * sizeof(float2), Vs, np * sizeof(float2), n0 * sizeof(float2), n0,
+                                cudaMemcpyDeviceToDevice, st));
+  return true;
+}
+
 }  // namespace
 
 void oa_step(int64_t n, const double2* G, const double2* S, double* lam, double2* M, unsigned long long* stats,
@@ -643,7 +948,9 @@ void jacobi_eigh(int64_t n0, double2* A, int64_t lda, double* w, double2* V, int
 
 void jacobi_eigh_f32(int64_t n0, float2* A, int64_t lda, float* w, float2* V, int64_t ldv, int* status,
                      cudaStream_t st, DevBuf<double2>* ws) {
-  // a first stage only: stop at the FP32 rounding level and never report a sweep limit
+  // a first stage only: stop at the FP32 rounding level and never report a sweep limit; the
+  // blocked method from 128 bands up
+  if (block_jacobi_f32(n0, A, lda, w, V, ldv, st, ws, 4e-7, 1e-5)) return;
   jacobi_eigh_t<float>(n0, A, lda, w, V, ldv, status, st, ws, 4e-7, 1e-5, false);
 }
 
