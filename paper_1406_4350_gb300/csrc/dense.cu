@@ -604,17 +604,17 @@ __device__ __forceinline__ void blocks_of(int pair, int round, int nbk, int& I, 
 }
 __device__ __forceinline__ int gidx(int l, int I, int J) { return l < B ? I * B + l : J * B + (l - B); }
 
-// One CTA per pair: gather the subproblem, diagonalise it (up to `sweeps` cyclic sweeps, or
-// until its off-diagonal part is below tol of its norm), write the rotation W (64 x 64,
-// column-major) to Wout[pair].
-__global__ void __launch_bounds__(256) k_bj_solve(const float2* __restrict__ A, int64_t lda, int nbk, int round,
+// One CTA of 1024 threads per pair: gather the subproblem, diagonalise it (up to `sweeps`
+// cyclic sweeps, or until its off-diagonal part is below tol of its norm), write the
+// rotation W (64 x 64, column-major) to Wout[pair].
+__global__ void __launch_bounds__(1024) k_bj_solve(const float2* __restrict__ A, int64_t lda, int nbk, int round,
                                                   float2* __restrict__ Wout, int sweeps, float tol) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* S = reinterpret_cast<float2*>(smem);  // S[i + PS j] = element (i, j)
   float2* W = S + S2 * PS;
   RotT<float>* rot = reinterpret_cast<RotT<float>*>(W + S2 * PS);
   int* pq = reinterpret_cast<int*>(rot + S2 / 2);
-  __shared__ float red[2][256];
+  __shared__ float red[2][1024];
   int I, J;
   blocks_of(blockIdx.x, round, nbk, I, J);
   const int tid = threadIdx.x;
@@ -871,7 +871,7 @@ bool block_jacobi_f32(int64_t n0, float2* A, int64_t lda, float* w, float2* V, i
     prev_off = off;
     // rounds of the block tournament; work: the subproblems' rotations and the two products
     for (int round = 0; round < nbk - 1; ++round) {
-      CHEBFI_LAUNCH("k_bj_solve", st, bj::k_bj_solve<<<npairs, 256, s_solve, st>>>(Ap, np, nbk, round, Wb, 2, 1e-7f));
+      CHEBFI_LAUNCH("k_bj_solve", st, bj::k_bj_solve<<<npairs, 1024, s_solve, st>>>(Ap, np, nbk, round, Wb, 2, 1e-7f));
       CHEBFI_LAUNCH_W("k_bj_update", st, 3.0 * 8.0 * (double)np * bj::S2 * bj::S2 * npairs,
                       bj::k_bj_cols<<<dim3(tiles, npairs, 2), 256, s_mul, st>>>(Ap, np, Vp, np, nbk, round, Wb, np));
       CHEBFI_LAUNCH("k_bj_update", st, bj::k_bj_rows<<<dim3(tiles, npairs), 256, s_mul, st>>>(Ap, np, nbk, round, Wb, np));
