@@ -871,7 +871,7 @@ bool block_jacobi_f32(int64_t n0, float2* A, int64_t lda, float* w, float2* V, i
     prev_off = off;
     // rounds of the block tournament; work: the subproblems' rotations and the two products
     for (int round = 0; round < nbk - 1; ++round) {
-      CHEBFI_LAUNCH("k_bj_solve", st, bj::k_bj_solve<<<npairs, 1024, s_solve, st>>>(Ap, np, nbk, round, Wb, 2, 1e-7f));
+      CHEBFI_LAUNCH("k_bj_solve", st, bj::k_bj_solve<<<npairs, 1024, s_solve, st>>>(Ap, np, nbk, round, Wb, 1, 1e-7f));
       CHEBFI_LAUNCH_W("k_bj_update", st, 3.0 * 8.0 * (double)np * bj::S2 * bj::S2 * npairs,
                       bj::k_bj_cols<<<dim3(tiles, npairs, 2), 256, s_mul, st>>>(Ap, np, Vp, np, nbk, round, Wb, np));
       CHEBFI_LAUNCH("k_bj_update", st, bj::k_bj_rows<<<dim3(tiles, npairs), 256, s_mul, st>>>(Ap, np, nbk, round, Wb, np));
