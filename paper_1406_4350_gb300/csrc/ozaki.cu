@@ -302,28 +302,34 @@ __device__ __forceinline__ long long scaled_int(double x, int s) {
   return (b >> 63) ? -q : q;
 }
 
-// symmetric residue of v = hi 2^32 + lo modulo kMods[I]: in [-128, 127] for 256, else |r| <= (m-1)/2
-template <int I> __device__ __forceinline__ int sres(int hi, unsigned lo) {
-  constexpr int m = kMods[I];
-  if constexpr (m == 256) {
-    return (int)(signed char)(lo & 255u);
-  } else {
-    constexpr int c32 = (int)((1ull << 32) % (unsigned long long)m);
-    int t = (hi % m) * c32 + (int)(lo % (unsigned)m);
-    t %= m;
-    if (t > m / 2) t -= m;
-    else if (t < -(m / 2)) t += m;
-    return t;
+// Symmetric residues of v modulo kMods[I], from 19-bit limbs of |v| (|v| <= 2^57):
+// |v| = a 2^38 + b 2^19 + c, so
+// |v| mod m = (a (2^38 mod m) + b (2^19 mod m) + c) mod m with every term below 2^28 -- one
+// 32-bit remainder by a constant per modulus; then the symmetric representative (|r| <= m/2)
+// and v's sign.  Any representative with |r| <= 128 serves the products' exactness.
+template <int I> __device__ __forceinline__ int sres_limbs(unsigned a, unsigned b, unsigned c, bool neg) {
+  constexpr unsigned m = (unsigned)kMods[I];
+  constexpr unsigned c38 = (unsigned)((1ull << 38) % m), c19 = (unsigned)((1ull << 19) % m);
+  unsigned x = (a * c38 + b * c19 + c) % m;
+  int r = (int)x;
+  if (x > m / 2) r -= (int)m;
+  return neg ? -r : r;
+}
+
+template <int I> __device__ __forceinline__ void residues_limbs(unsigned a, unsigned b, unsigned c, bool neg, int nmod,
+                                                                int* r) {
+  if constexpr (I < kOzMaxMod) {
+    if (I < nmod) {
+      r[I] = sres_limbs<I>(a, b, c, neg);
+      residues_limbs<I + 1>(a, b, c, neg, nmod, r);
+    }
   }
 }
 
-template <int I> __device__ __forceinline__ void residues(long long v, int nmod, int* r) {
-  if constexpr (I < kOzMaxMod) {
-    if (I < nmod) {
-      r[I] = sres<I>((int)(v >> 32), (unsigned)(unsigned long long)v);
-      residues<I + 1>(v, nmod, r);
-    }
-  }
+__device__ __forceinline__ void residues(long long v, int nmod, int* r) {
+  const bool neg = v < 0;
+  const unsigned long long u = (unsigned long long)(neg ? -v : v);
+  residues_limbs<0>((unsigned)(u >> 38), (unsigned)((u >> 19) & 0x7FFFFu), (unsigned)(u & 0x7FFFFu), neg, nmod, r);
 }
 
 __device__ __forceinline__ __nv_bfloat162 bf2(int a, int b) {
@@ -336,8 +342,8 @@ __device__ __forceinline__ __nv_bfloat162 bf2(int a, int b) {
 __device__ __forceinline__ void put_entry(double2 a, int s, int nmod, bool doubled, __nv_bfloat16* out,
                                           int64_t mstride, int64_t ld, int64_t r, int64_t k) {
   int rr[kOzMaxMod], ri[kOzMaxMod];
-  residues<0>(s == kOzBadShift ? 0ll : scaled_int(a.x, s), nmod, rr);
-  residues<0>(s == kOzBadShift ? 0ll : scaled_int(a.y, s), nmod, ri);
+  residues(s == kOzBadShift ? 0ll : scaled_int(a.x, s), nmod, rr);
+  residues(s == kOzBadShift ? 0ll : scaled_int(a.y, s), nmod, ri);
 #pragma unroll
   for (int i = 0; i < kOzMaxMod; ++i) {
     if (i < nmod) {
