@@ -405,7 +405,7 @@ struct CrtArgs {
 // C_int from its residues: t_i = r_i y_i mod m_i, S = sum t_i (M / m_i) = C_int (mod M),
 // C_int = S - M round(S / M) with S / M = sum t_i / m_i (FP32 suffices: |C_int| <= M / 8
 // keeps S / M at least 3/8 away from a half-integer).  128-bit integers, exact.
-__device__ __forceinline__ double crt_value(const signed char* r, int64_t rs, const CrtArgs& c) {
+__device__ __forceinline__ __int128 crt_value(const signed char* r, int64_t rs, const CrtArgs& c) {
   __int128 S = 0;
   float f = 0.f;
 #pragma unroll
@@ -420,9 +420,36 @@ __device__ __forceinline__ double crt_value(const signed char* r, int64_t rs, co
   }
   const int k = (int)rintf(f);
   S -= (__int128)k * (__int128)(((unsigned __int128)c.M[1] << 64) | c.M[0]);
-  const long long hi = (long long)(S >> 64);
-  const unsigned long long lo = (unsigned long long)S;
-  return fma((double)hi, 18446744073709551616.0, (double)lo);
+  return S;
+}
+
+// S 2^-sh as the nearest double (ties to even), by integer operations on the bits: GB300's
+// FP64 pipe is its slowest, and a conversion plus a scaling there per value bound this
+// kernel.  Results outside the normal range go through ldexp.
+__device__ __forceinline__ double scaled_double(__int128 S, int sh) {
+  if (S == 0) return 0.0;
+  const bool neg = S < 0;
+  unsigned __int128 u = neg ? (unsigned __int128)(-S) : (unsigned __int128)S;
+  const unsigned long long h = (unsigned long long)(u >> 64), l = (unsigned long long)u;
+  const int lz = h ? __clzll((long long)h) : 64 + __clzll((long long)l);
+  u <<= lz;  // leading one at bit 127
+  const unsigned long long top = (unsigned long long)(u >> 64), rest = (unsigned long long)u;
+  unsigned long long mant = top >> 11;  // 53 bits, bit 52 set
+  const unsigned long long rb = top & 0x7FFull;
+  if (rb > 0x400ull || (rb == 0x400ull && (rest != 0 || (mant & 1ull)))) ++mant;
+  int e = 127 - lz;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e;
+  }
+  e -= sh;
+  if (e < -1022 || e > 1023) {  // subnormal or overflow: the library's ldexp
+    const double v = __longlong_as_double((long long)((1023ull << 52) | (mant & ((1ull << 52) - 1))));
+    return ldexp(neg ? -v : v, e);
+  }
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) | ((unsigned long long)(e + 1023) << 52) | (mant & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
 }
 
 // C[m, n] = alpha 2^-(sa_m + sb_n) C_int[m, n] + beta C[m, n]; one thread per complex entry
@@ -434,15 +461,15 @@ __global__ void k_oz_recon(int64_t M, int64_t N, const signed char* __restrict__
   const int64_t m = idx % M, n = idx / M;
   if (lower && m < n) return;
   const signed char* base = R + n * (2 * M) + 2 * m;
-  double re = crt_value(base, rstride, crt), im = crt_value(base + 1, rstride, crt);
   const int s1 = sa[m], s2 = sb[n];
+  double re, im;
   if (s1 == kOzBadShift || s2 == kOzBadShift) {
     re = im = __longlong_as_double(0x7FF8000000000000ll);
   } else {
-    re = ldexp(re, -(s1 + s2));
-    im = ldexp(im, -(s1 + s2));
+    re = scaled_double(crt_value(base, rstride, crt), s1 + s2);
+    im = scaled_double(crt_value(base + 1, rstride, crt), s1 + s2);
   }
-  double2 v = make_double2(alpha * re, alpha * im);
+  double2 v = alpha == 1.0 ? make_double2(re, im) : make_double2(alpha * re, alpha * im);
   double2* c = C + m + n * ldc;
   if (beta != 0.0) {
     const double2 o = *c;
