@@ -268,17 +268,28 @@ __global__ void k_oz_norm_cols(int64_t nrows, int64_t K, const double2* __restri
   if (threadIdx.x == 0) shift[r] = shift_for(red[0], E);
 }
 
-// rows of op(X) are the rows of X (strided): one thread per row, the warp reads along rows
-__global__ void k_oz_norm_rows(int64_t nrows, int64_t K, const double2* __restrict__ X, int64_t ldx, int E,
-                               int* __restrict__ shift) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
+// rows of op(X) are the rows of X (strided): 32 rows per block, eight threads per row
+// summing every eighth column, their partial sums added in a fixed order
+__global__ void __launch_bounds__(256) k_oz_norm_rows(int64_t nrows, int64_t K, const double2* __restrict__ X,
+                                                      int64_t ldx, int E, int* __restrict__ shift) {
+  __shared__ double part[8][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int64_t r = (int64_t)blockIdx.x * 32 + tx;
   double s = 0.0;
-  for (int64_t k = 0; k < K; ++k) {
-    const double2 v = X[r + k * ldx];
-    s = fma(v.x, v.x, fma(v.y, v.y, s));
+  if (r < nrows) {
+    for (int64_t k = ty; k < K; k += 8) {
+      const double2 v = X[r + k * ldx];
+      s = fma(v.x, v.x, fma(v.y, v.y, s));
+    }
   }
-  shift[r] = shift_for(s, E);
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && r < nrows) {
+    double t = part[0][tx];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) t += part[j][tx];
+    shift[r] = shift_for(t, E);
+  }
 }
 
 // round(x 2^s) for |x 2^s| <= 2^62 by integer operations on the bits (ties to even)
@@ -316,80 +327,132 @@ template <int I> __device__ __forceinline__ int sres_limbs(unsigned a, unsigned 
   return neg ? -r : r;
 }
 
-template <int I> __device__ __forceinline__ void residues_limbs(unsigned a, unsigned b, unsigned c, bool neg, int nmod,
-                                                                int* r) {
-  if constexpr (I < kOzMaxMod) {
-    if (I < nmod) {
-      r[I] = sres_limbs<I>(a, b, c, neg);
-      residues_limbs<I + 1>(a, b, c, neg, nmod, r);
-    }
-  }
-}
-
-__device__ __forceinline__ void residues(long long v, int nmod, int* r) {
+// the 19-bit limbs of |v| and v's sign
+struct Limbs {
+  unsigned a, b, c;
+  bool neg;
+};
+__device__ __forceinline__ Limbs limbs_of(long long v) {
   const bool neg = v < 0;
   const unsigned long long u = (unsigned long long)(neg ? -v : v);
-  residues_limbs<0>((unsigned)(u >> 38), (unsigned)((u >> 19) & 0x7FFFFu), (unsigned)(u & 0x7FFFFu), neg, nmod, r);
+  return Limbs{(unsigned)(u >> 38), (unsigned)((u >> 19) & 0x7FFFFu), (unsigned)(u & 0x7FFFFu), neg};
 }
 
-__device__ __forceinline__ __nv_bfloat162 bf2(int a, int b) {
-  return __halves2bfloat162(__int2bfloat16_rn(a), __int2bfloat16_rn(b));
+// the float bits of a small integer (|n| < 2^22) without a conversion instruction: 1.5 2^23 + n
+// has n in its low mantissa bits, and subtracting 1.5 2^23 is exact
+__device__ __forceinline__ unsigned small_int_float_bits(int n) {
+  return (unsigned)__float_as_int(__fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f));
+}
+// two residues (|r| <= 128, exact in bf16) as a bf16 pair: the high halves of their float bits
+__device__ __forceinline__ unsigned bf16_pair(unsigned lo_bits, unsigned hi_bits) {
+  return __byte_perm(lo_bits, hi_bits, 0x7632);
 }
 
-// Writes the residues of one complex entry a = op(X)[r][k] (after the optional conjugation)
-// into every modulus' matrix: plain (row r: Re, Im) or doubled (row 2r: Re, -Im; row 2r+1:
-// Im, Re).  out[mod * mstride + row * ld + 2k].
-__device__ __forceinline__ void put_entry(double2 a, int s, int nmod, bool doubled, __nv_bfloat16* out,
-                                          int64_t mstride, int64_t ld, int64_t r, int64_t k) {
-  int rr[kOzMaxMod], ri[kOzMaxMod];
-  residues(s == kOzBadShift ? 0ll : scaled_int(a.x, s), nmod, rr);
-  residues(s == kOzBadShift ? 0ll : scaled_int(a.y, s), nmod, ri);
+// Writes the residues of NE consecutive complex entries a_e = op(X)[r][k + e] (after the
+// optional conjugation) for moduli I.. into their matrices, one modulus at a time so that no
+// residue outlives its store: plain (row r: Re, Im) or doubled (row 2r: Re, -Im; row 2r+1:
+// Im, Re).  o0 / o1 point at entry k of those rows in modulus I's matrix.
+template <int I, int NE>
+__device__ __forceinline__ void put_mods(const Limbs (&re)[NE], const Limbs (&im)[NE], int nmod, bool doubled,
+                                         __nv_bfloat16* o0, __nv_bfloat16* o1, int64_t mstride) {
+  if constexpr (I < kOzMaxMod) {
+    if (I < nmod) {
+      unsigned fr[NE], fi[NE];
 #pragma unroll
-  for (int i = 0; i < kOzMaxMod; ++i) {
-    if (i < nmod) {
-      __nv_bfloat16* o = out + (int64_t)i * mstride + 2 * k;
-      if (doubled) {
-        *reinterpret_cast<__nv_bfloat162*>(o + (2 * r) * ld) = bf2(rr[i], -ri[i]);
-        *reinterpret_cast<__nv_bfloat162*>(o + (2 * r + 1) * ld) = bf2(ri[i], rr[i]);
-      } else {
-        *reinterpret_cast<__nv_bfloat162*>(o + r * ld) = bf2(rr[i], ri[i]);
+      for (int e = 0; e < NE; ++e) {
+        fr[e] = small_int_float_bits(sres_limbs<I>(re[e].a, re[e].b, re[e].c, re[e].neg));
+        fi[e] = small_int_float_bits(sres_limbs<I>(im[e].a, im[e].b, im[e].c, im[e].neg));
       }
+      if constexpr (NE == 2) {
+        if (doubled) {
+          *reinterpret_cast<uint2*>(o0) =
+              make_uint2(bf16_pair(fr[0], fi[0] ^ 0x80000000u), bf16_pair(fr[1], fi[1] ^ 0x80000000u));
+          *reinterpret_cast<uint2*>(o1) = make_uint2(bf16_pair(fi[0], fr[0]), bf16_pair(fi[1], fr[1]));
+        } else {
+          *reinterpret_cast<uint2*>(o0) = make_uint2(bf16_pair(fr[0], fi[0]), bf16_pair(fr[1], fi[1]));
+        }
+      } else {
+        if (doubled) {
+          *reinterpret_cast<unsigned*>(o0) = bf16_pair(fr[0], fi[0] ^ 0x80000000u);
+          *reinterpret_cast<unsigned*>(o1) = bf16_pair(fi[0], fr[0]);
+        } else {
+          *reinterpret_cast<unsigned*>(o0) = bf16_pair(fr[0], fi[0]);
+        }
+      }
+      put_mods<I + 1, NE>(re, im, nmod, doubled, o0 + mstride, o1 + mstride, mstride);
     }
   }
 }
 
-// rows of op(X) = columns of X: grid (k blocks, rows)
-__global__ void k_oz_res_cols(int64_t K, const double2* __restrict__ X, int64_t ldx, const int* __restrict__ shift,
-                              int conj, int doubled, int nmod, __nv_bfloat16* __restrict__ out, int64_t mstride,
-                              int64_t ld) {
+// the residues of entries a[0..NE) = op(X)[r][k..k+NE) with row shift s
+template <int NE>
+__device__ __forceinline__ void put_entries(const double2 (&a)[NE], int s, int nmod, bool doubled,
+                                            __nv_bfloat16* __restrict__ out, int64_t mstride, int64_t ld, int64_t r,
+                                            int64_t k) {
+  Limbs re[NE], im[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    re[e] = limbs_of(s == kOzBadShift ? 0ll : scaled_int(a[e].x, s));
+    im[e] = limbs_of(s == kOzBadShift ? 0ll : scaled_int(a[e].y, s));
+  }
+  __nv_bfloat16* o0 = out + (doubled ? 2 * r : r) * ld + 2 * k;
+  put_mods<0, NE>(re, im, nmod, doubled, o0, o0 + ld, mstride);
+}
+
+// rows of op(X) = columns of X: grid (k blocks, rows); two consecutive entries per thread
+// (ld and the modulus stride are multiples of 8 bf16 values, so the pairs' 8-byte stores
+// are aligned)
+__global__ void __launch_bounds__(256) k_oz_res_cols(int64_t K, const double2* __restrict__ X, int64_t ldx,
+                                                     const int* __restrict__ shift, int conj, int doubled, int nmod,
+                                                     __nv_bfloat16* __restrict__ out, int64_t mstride, int64_t ld) {
   const int64_t r = blockIdx.y;
+  const int64_t k = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (k >= K) return;
   const int s = shift[r];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
-    double2 a = X[k + r * ldx];
-    if (conj) a.y = -a.y;
-    put_entry(a, s, nmod, doubled != 0, out, mstride, ld, r, k);
+  const double2* x = X + r * ldx;
+  if (k + 1 < K) {
+    double2 a[2] = {x[k], x[k + 1]};
+    if (conj) {
+      a[0].y = -a[0].y;
+      a[1].y = -a[1].y;
+    }
+    put_entries<2>(a, s, nmod, doubled != 0, out, mstride, ld, r, k);
+  } else {
+    double2 a[1] = {x[k]};
+    if (conj) a[0].y = -a[0].y;
+    put_entries<1>(a, s, nmod, doubled != 0, out, mstride, ld, r, k);
   }
 }
 
-// rows of op(X) = rows of X: 32 x 32 tiles through shared memory so that both the reads
-// (along rows of X) and the writes (along k) are coalesced
-__global__ void k_oz_res_rows(int64_t nrows, int64_t K, const double2* __restrict__ X, int64_t ldx,
-                              const int* __restrict__ shift, int conj, int doubled, int nmod,
-                              __nv_bfloat16* __restrict__ out, int64_t mstride, int64_t ld) {
-  __shared__ double2 t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+// rows of op(X) = rows of X: 32-row x 64-k tiles through shared memory so that both the
+// reads (along rows of X) and the writes (along k, two entries per thread) are coalesced
+__global__ void __launch_bounds__(256) k_oz_res_rows(int64_t nrows, int64_t K, const double2* __restrict__ X,
+                                                     int64_t ldx, const int* __restrict__ shift, int conj,
+                                                     int doubled, int nmod, __nv_bfloat16* __restrict__ out,
+                                                     int64_t mstride, int64_t ld) {
+  __shared__ double2 t[32][65];  // [row][k], odd pitch
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 256 threads: 8 rows of 32
-  for (int j = ty; j < 32; j += 8) {
+  for (int j = ty; j < 64; j += 8) {
     const int64_t r = r0 + tx, k = k0 + j;
-    t[j][tx] = (r < nrows && k < K) ? X[r + k * ldx] : make_double2(0.0, 0.0);
+    t[tx][j] = (r < nrows && k < K) ? X[r + k * ldx] : make_double2(0.0, 0.0);
   }
   __syncthreads();
   for (int j = ty; j < 32; j += 8) {
-    const int64_t r = r0 + j, k = k0 + tx;
-    if (r < nrows && k < K) {
-      double2 a = t[tx][j];
-      if (conj) a.y = -a.y;
-      put_entry(a, shift[r], nmod, doubled != 0, out, mstride, ld, r, k);
+    const int64_t r = r0 + j, k = k0 + 2 * tx;
+    if (r >= nrows || k >= K) continue;
+    const int s = shift[r];
+    if (k + 1 < K) {
+      double2 a[2] = {t[j][2 * tx], t[j][2 * tx + 1]};
+      if (conj) {
+        a[0].y = -a[0].y;
+        a[1].y = -a[1].y;
+      }
+      put_entries<2>(a, s, nmod, doubled != 0, out, mstride, ld, r, k);
+    } else {
+      double2 a[1] = {t[j][2 * tx]};
+      if (conj) a[0].y = -a[0].y;
+      put_entries<1>(a, s, nmod, doubled != 0, out, mstride, ld, r, k);
     }
   }
 }
@@ -398,29 +461,74 @@ __global__ void k_oz_res_rows(int64_t nrows, int64_t K, const double2* __restric
 struct CrtArgs {
   int nmod;
   float m[kOzMaxMod], inv[kOzMaxMod], y[kOzMaxMod];  // y_i = (M / m_i)^-1 mod m_i
-  unsigned long long Mi[kOzMaxMod][2];              // M / m_i as (lo, hi)
-  unsigned long long M[2];
+  int L[kOzMaxMod][4];                               // M / m_i in 30-bit limbs, least significant first
+  int ML[4];                                         // M in 30-bit limbs
 };
 
-// C_int from its residues: t_i = r_i y_i mod m_i, S = sum t_i (M / m_i) = C_int (mod M),
-// C_int = S - M round(S / M) with S / M = sum t_i / m_i (FP32 suffices: |C_int| <= M / 8
-// keeps S / M at least 3/8 away from a half-integer).  128-bit integers, exact.
-__device__ __forceinline__ __int128 crt_value(const signed char* r, int64_t rs, const CrtArgs& c) {
-  __int128 S = 0;
-  float f = 0.f;
+// M < 2^120 for every modulus count: four 30-bit limbs hold M and each M / m_i
+constexpr bool mods_fit_limbs() {
+  unsigned __int128 M = 1;
+  for (int i = 0; i < kOzMaxMod; ++i) M *= (unsigned)kMods[i];
+  return (M >> 120) == 0;
+}
+static_assert(mods_fit_limbs(), "CRT modulus too large for four 30-bit limbs");
+
+// 1.5 2^23: for |x| < 2^22, x + kMagic rounds x to an integer held in the low mantissa bits
+constexpr float kMagic = 12582912.0f;
+
+// one modulus' term of the CRT sum for residue r: t = r y_i mod m_i (symmetric, exact in
+// float), its share t / m_i of S / M added to f.  The float conversions go through kMagic
+// (one integer and one float addition each) instead of conversion instructions.
+__device__ __forceinline__ int crt_term(int r, float y, float m, float inv, float& f) {
+  const float p = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + r), kMagic), y);  // r y, exact (< 2^15)
+  const float q = __fsub_rn(__fmaf_rn(p, inv, kMagic), kMagic);                     // round(p / m_i)
+  const float t = __fmaf_rn(-m, q, p);                                               // exact, |t| <= m_i / 2 + 1
+  f = __fmaf_rn(t, inv, f);
+  return __float_as_int(__fadd_rn(t, kMagic)) - 0x4B400000;
+}
+
+// sum_j a_j 2^(30 j) in 128-bit two's complement (the true sum fits)
+__device__ __forceinline__ __int128 limb_sum(const long long (&a)[4]) {
+  using u128 = unsigned __int128;
+  const u128 u = (u128)(__int128)a[0] + ((u128)(__int128)a[1] << 30) + ((u128)(__int128)a[2] << 60) +
+                 ((u128)(__int128)a[3] << 90);
+  return (__int128)u;
+}
+
+// C_int of the two adjacent values (Re, Im) at r[0], r[1] of every modulus' residue matrix
+// (modulus stride rs): t_i = r_i y_i mod m_i, S = sum t_i (M / m_i) = C_int (mod M), and
+// C_int = S - M round(S / M) with S / M = sum t_i / m_i (FP32 suffices: |C_int| <= M / 8 keeps
+// S / M at least 3/8 away from a half-integer).  The products t_i (M / m_i) accumulate per
+// 30-bit limb of M / m_i in 64-bit integers (one 32 x 32 -> 64-bit multiply-add each, sums
+// below 2^43), combined once into 128 bits: exact.
+// NM moduli (a compile-time count, so that all NM loads are in flight at once).
+template <int NM>
+__device__ __forceinline__ void crt_pair(const signed char* r, int64_t rs, const CrtArgs& c, __int128& S0,
+                                         __int128& S1) {
+  unsigned v[NM];
 #pragma unroll
-  for (int i = 0; i < kOzMaxMod; ++i) {
-    if (i < c.nmod) {
-      const float p = (float)r[i * rs] * c.y[i];
-      const float t = fmaf(-c.m[i], rintf(p * c.inv[i]), p);  // exact, |t| <= m_i / 2 + m_i
-      f = fmaf(t, c.inv[i], f);
-      const __int128 Mi = (__int128)(((unsigned __int128)c.Mi[i][1] << 64) | c.Mi[i][0]);
-      S += (__int128)(int)t * Mi;
+  for (int i = 0; i < NM; ++i) v[i] = *reinterpret_cast<const unsigned short*>(r + i * rs);
+  long long a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+  float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    const int t0 = crt_term((int)(signed char)(v[i] & 0xFFu), c.y[i], c.m[i], c.inv[i], f0);
+    const int t1 = crt_term((int)(signed char)(v[i] >> 8), c.y[i], c.m[i], c.inv[i], f1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      a0[j] += (long long)t0 * (long long)c.L[i][j];
+      a1[j] += (long long)t1 * (long long)c.L[i][j];
     }
   }
-  const int k = (int)rintf(f);
-  S -= (__int128)k * (__int128)(((unsigned __int128)c.M[1] << 64) | c.M[0]);
-  return S;
+  const int k0 = __float_as_int(__fadd_rn(f0, kMagic)) - 0x4B400000;
+  const int k1 = __float_as_int(__fadd_rn(f1, kMagic)) - 0x4B400000;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    a0[j] -= (long long)k0 * (long long)c.ML[j];
+    a1[j] -= (long long)k1 * (long long)c.ML[j];
+  }
+  S0 = limb_sum(a0);
+  S1 = limb_sum(a1);
 }
 
 // S 2^-sh as the nearest double (ties to even), by integer operations on the bits: GB300's
@@ -452,31 +560,36 @@ __device__ __forceinline__ double scaled_double(__int128 S, int sh) {
   return __longlong_as_double((long long)bits);
 }
 
-// C[m, n] = alpha 2^-(sa_m + sb_n) C_int[m, n] + beta C[m, n]; one thread per complex entry
-__global__ void k_oz_recon(int64_t M, int64_t N, const signed char* __restrict__ R, int64_t rstride,
+// C[m, n] = alpha 2^-(sa_m + sb_n) C_int[m, n] + beta C[m, n]; one thread per complex entry,
+// grid (m blocks, columns n strided); NM = crt.nmod
+template <int NM>
+__global__ void __launch_bounds__(256) k_oz_recon(int64_t M, int64_t N, const signed char* __restrict__ R, int64_t rstride,
                            const int* __restrict__ sa, const int* __restrict__ sb, double alpha, double beta,
                            double2* C, int64_t ldc, int lower, const __grid_constant__ CrtArgs crt) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= M * N) return;
-  const int64_t m = idx % M, n = idx / M;
-  if (lower && m < n) return;
-  const signed char* base = R + n * (2 * M) + 2 * m;
-  const int s1 = sa[m], s2 = sb[n];
-  double re, im;
-  if (s1 == kOzBadShift || s2 == kOzBadShift) {
-    re = im = __longlong_as_double(0x7FF8000000000000ll);
-  } else {
-    re = scaled_double(crt_value(base, rstride, crt), s1 + s2);
-    im = scaled_double(crt_value(base + 1, rstride, crt), s1 + s2);
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int s1 = sa[m];
+  for (int64_t n = blockIdx.y; n < N; n += gridDim.y) {
+    if (lower && m < n) continue;
+    const int s2 = sb[n];
+    double re, im;
+    if (s1 == kOzBadShift || s2 == kOzBadShift) {
+      re = im = __longlong_as_double(0x7FF8000000000000ll);
+    } else {
+      __int128 S0, S1;
+      crt_pair<NM>(R + n * (2 * M) + 2 * m, rstride, crt, S0, S1);
+      re = scaled_double(S0, s1 + s2);
+      im = scaled_double(S1, s1 + s2);
+    }
+    double2 v = alpha == 1.0 ? make_double2(re, im) : make_double2(alpha * re, alpha * im);
+    double2* c = C + m + n * ldc;
+    if (beta != 0.0) {
+      const double2 o = *c;
+      v.x = fma(beta, o.x, v.x);
+      v.y = fma(beta, o.y, v.y);
+    }
+    *c = v;
   }
-  double2 v = alpha == 1.0 ? make_double2(re, im) : make_double2(alpha * re, alpha * im);
-  double2* c = C + m + n * ldc;
-  if (beta != 0.0) {
-    const double2 o = *c;
-    v.x = fma(beta, o.x, v.x);
-    v.y = fma(beta, o.y, v.y);
-  }
-  *c = v;
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -523,11 +636,9 @@ const ModSet& modset(int n) {
     s.crt.m[i] = (float)m;
     s.crt.inv[i] = 1.0f / (float)m;
     s.crt.y[i] = (float)y;
-    s.crt.Mi[i][0] = (unsigned long long)Mi;
-    s.crt.Mi[i][1] = (unsigned long long)(Mi >> 64);
+    for (int j = 0; j < 4; ++j) s.crt.L[i][j] = (int)((Mi >> (30 * j)) & ((1u << 30) - 1));
   }
-  s.crt.M[0] = (unsigned long long)M;
-  s.crt.M[1] = (unsigned long long)(M >> 64);
+  for (int j = 0; j < 4; ++j) s.crt.ML[j] = (int)((M >> (30 * j)) & ((1u << 30) - 1));
   s.E = std::min(62, (int)std::floor((l2 - 3.0) / 2.0));
   s.n = n;
   return s;
@@ -554,17 +665,17 @@ void oz_prepare(const double2* X, int64_t ldx, int64_t nrows, int64_t K, bool ro
   if (nrows == 0 || K == 0) return;
   if (rows_are_columns) {
     CHEBFI_LAUNCH("k_oz_norm", st, oz::k_oz_norm_cols<<<(unsigned)nrows, 256, 0, st>>>(nrows, K, X, ldx, ms.E, out.shift.p));
-    const unsigned kb = (unsigned)std::min<int64_t>((K + 255) / 256, 64);
+    const unsigned kb = (unsigned)((K + 511) / 512);  // one pair of entries per thread
     CHEBFI_REQUIRE(nrows <= 65535, CHEBFI_ERR_ARG, "too many rows for the residue kernel");
     CHEBFI_LAUNCH("k_oz_res", st,
                   oz::k_oz_res_cols<<<dim3(kb, (unsigned)nrows), 256, 0, st>>>(K, X, ldx, out.shift.p, conj ? 1 : 0,
                                                                                doubled ? 1 : 0, nmod, out.res.p,
                                                                                out.mstride, out.ld));
   } else {
-    CHEBFI_LAUNCH("k_oz_norm", st, oz::k_oz_norm_rows<<<oz::nblk(nrows, 128), 128, 0, st>>>(nrows, K, X, ldx, ms.E, out.shift.p));
-    CHEBFI_REQUIRE((K + 31) / 32 <= 65535, CHEBFI_ERR_ARG, "inner dimension too large for the residue kernel");
+    CHEBFI_LAUNCH("k_oz_norm", st, oz::k_oz_norm_rows<<<oz::nblk(nrows, 32), 256, 0, st>>>(nrows, K, X, ldx, ms.E, out.shift.p));
+    CHEBFI_REQUIRE((K + 63) / 64 <= 65535, CHEBFI_ERR_ARG, "inner dimension too large for the residue kernel");
     CHEBFI_LAUNCH("k_oz_res", st,
-                  oz::k_oz_res_rows<<<dim3((unsigned)((nrows + 31) / 32), (unsigned)((K + 31) / 32)), 256, 0, st>>>(
+                  oz::k_oz_res_rows<<<dim3((unsigned)((nrows + 31) / 32), (unsigned)((K + 63) / 64)), 256, 0, st>>>(
                       nrows, K, X, ldx, out.shift.p, conj ? 1 : 0, doubled ? 1 : 0, nmod, out.res.p, out.mstride,
                       out.ld));
   }
@@ -616,9 +727,23 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double alpha, double beta, 
   (void)tag;  // every modular GEMM is timed under one name, so its engine is unambiguous
   CHEBFI_LAUNCH_W("k_oz_gemm", st, 2.0 * (double)a.M * (double)a.N * (double)a.K * tiles_done,
                   oz::k_oz_gemm<<<(unsigned)std::min<int64_t>(units, sms), oz::THREADS, oz::SMEM_BYTES, st>>>(ta, tb, a));
-  CHEBFI_LAUNCH("k_oz_recon", st,
-                oz::k_oz_recon<<<oz::nblk(M * N), 256, 0, st>>>(M, N, R.p, a.rstride, A.shift.p, B.shift.p, alpha, beta,
-                                                                C, ldc, lower ? 1 : 0, ms.crt));
+  const dim3 rgrid(oz::nblk(M), (unsigned)std::min<int64_t>(N, 65535));
+  auto recon = [&](auto kernel) {
+    CHEBFI_LAUNCH("k_oz_recon", st,
+                  kernel<<<rgrid, 256, 0, st>>>(M, N, R.p, a.rstride, A.shift.p, B.shift.p, alpha, beta, C, ldc,
+                                                lower ? 1 : 0, ms.crt));
+  };
+  static_assert(kOzMinMod == 8 && kOzMaxMod == 15, "one reconstruction kernel per modulus count");
+  switch (nmod) {
+    case 8: recon(oz::k_oz_recon<8>); break;
+    case 9: recon(oz::k_oz_recon<9>); break;
+    case 10: recon(oz::k_oz_recon<10>); break;
+    case 11: recon(oz::k_oz_recon<11>); break;
+    case 12: recon(oz::k_oz_recon<12>); break;
+    case 13: recon(oz::k_oz_recon<13>); break;
+    case 14: recon(oz::k_oz_recon<14>); break;
+    default: recon(oz::k_oz_recon<15>); break;
+  }
 }
 
 }  // namespace chebfi
