@@ -539,15 +539,21 @@ def main():
             a[1] += cnt
             a[2] += wk
 
+    # P^H Y of the block that Rayleigh-Ritz has just rotated: that step forms it anyway (for
+    # S Y in the residuals), and the next filter starts from it instead of recomputing it,
+    # as in chebfi_solve (Algorithm 2's loop); the first warm-up filter computes its own
+    proj_full = torch.empty((nb, nq), dtype=torch.complex128, device="cuda:%d" % local).T if nq > 0 else None
+    proj = None
+
     def step(p, timed=None):
-        nonlocal lo, Y
+        nonlocal lo, Y, proj
         st = torch.cuda.current_stream()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         if timed is not None:
             g.profile(True)
         e0.record(st)
         torch.cuda.nvtx.range_push("filter")
-        g.cheb_filter(Y, DEGREE, lo, hi, prec=p)
+        g.cheb_filter(Y, DEGREE, lo, hi, prec=p, proj=proj)
         torch.cuda.nvtx.range_pop()
         e1.record(st)
         if timed is not None:
@@ -555,7 +561,9 @@ def main():
             g.profile(True)
         torch.cuda.nvtx.range_push("rr")
         full = gather_bands(Y, nb, world) if world > 1 else Y
-        ev, rs = g.rayleigh_ritz(full)
+        ev, rs = g.rayleigh_ritz(full, proj=proj_full)
+        if proj_full is not None:
+            proj = proj_full[:, b0:b1]
         if world > 1:
             Y = full[:, b0:b1].clone().T.contiguous().T
         torch.cuda.nvtx.range_pop()
@@ -595,19 +603,23 @@ def main():
     # FP64 form of the same filter, same bands
     fp64 = None
     if args.fp64_steps > 0 and prec != F64:
+        # every timed filter starts from the rotated block and its projections, as the
+        # mixed form's do (the block is restored between filters, outside the events)
         Yc = Y.clone()
         st = torch.cuda.current_stream()
-        g.cheb_filter(Yc, DEGREE, lo, hi, prec=F64)
-        Yc.copy_(Y)
+        g.cheb_filter(Yc, DEGREE, lo, hi, prec=F64, proj=proj)
         barrier()
         g.profile(True)
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
+        evs = []
         for _ in range(args.fp64_steps):
-            g.cheb_filter(Yc, DEGREE, lo, hi, prec=F64)
-        c.record(st)
+            Yc.copy_(Y)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            g.cheb_filter(Yc, DEGREE, lo, hi, prec=F64, proj=proj)
+            c.record(st)
+            evs.append((a, c))
         barrier()
-        ms = a.elapsed_time(c)
+        ms = sum(a.elapsed_time(c) for a, c in evs)
         tot = g.profile_totals()
         g.profile(False)
         fp_s = aggregate(ms / 1e3, 0.0, 0.0, world)[1]  # slowest rank
@@ -620,19 +632,31 @@ def main():
     # end to end through the public API with host buffers: chebfi_cheb_filter_host takes the
     # pinned host block, copies it in, filters it and copies it back every step (band chunks
     # whose copies overlap the neighbouring chunks' filters)
+    # (with the rotated block's projections in host memory too, copied in chunk by chunk); the
+    # block is restored between calls outside the events, so that every call filters the
+    # block its projections belong to; one untimed call first (streams, staging buffers)
+    Yh = Y.cpu()
     host = torch.empty((Y.shape[1], npw), dtype=torch.complex128, pin_memory=True).T
-    host.copy_(Y)
-    barrier()
+    host_p = None
+    if proj is not None:
+        host_p = torch.empty((proj.shape[1], nq), dtype=torch.complex128, pin_memory=True).T
+        host_p.copy_(proj)
     st = torch.cuda.current_stream()
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ea.record(st)
-    for _ in range(args.steps):
-        g.cheb_filter_host(host, DEGREE, lo, hi, prec=prec)
-    eb.record(st)
-    torch.cuda.synchronize()
-    e2e_s = ea.elapsed_time(eb) / 1e3
-    _, e2e_s, _ = aggregate(e2e_s, 0.0, 0.0, world)
+    e2e_ms = 0.0
+    for it in range(args.steps + 1):
+        host.copy_(Yh)
+        barrier()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(st)
+        g.cheb_filter_host(host, DEGREE, lo, hi, prec=prec, proj=host_p)
+        eb.record(st)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_ms += ea.elapsed_time(eb)
+    _, e2e_s, _ = aggregate(e2e_ms / 1e3, 0.0, 0.0, world)
     nbytes = npw * (b1 - b0) * 16
+    nbytes_p = nq * (b1 - b0) * 16 if host_p is not None else 0
+    del Yh
 
     # rooflines from the library's per-launch CUDA events and each launch's algorithmic work
     # (flops for GEMMs and the Jacobi sweeps, bytes for the FFT passes)
@@ -738,7 +762,7 @@ def main():
                    "parallelism": "bands split over %d rank(s), block gathered for Rayleigh-Ritz" % world},
         "phases_ms": {"filter": statistics.mean(filt_ms), "rayleigh_ritz": statistics.mean(rr_ms)},
         "fp64_form": fp64,
-        "e2e": {"value": nb * DEGREE * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        "e2e": {"value": nb * DEGREE * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes + nbytes_p,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "roofline": roof,

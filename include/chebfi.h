@@ -181,6 +181,15 @@ int chebfi_apply_Sinv_refined(chebfi_ctx* ctx, const void* X, void* out, int64_t
 int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree,
                        double lambda_lo, double lambda_hi, int prec, void* stream);
 
+/* chebfi_cheb_filter with p_0 = P^H Y given: proj (device, complex128, nproj x nb
+ * column-major, leading dimension ldp >= nproj) as chebfi_rayleigh_ritz_proj returns it for
+ * this Y.  Algorithm 2's filter starts from the block that Rayleigh-Ritz has just rotated,
+ * whose projections that step forms anyway, so the filter's first P^H Y product is saved.
+ * The caller vouches that proj belongs to Y (not checked: a stale proj gives a wrong filter).
+ * proj NULL, or no projectors: exactly chebfi_cheb_filter. */
+int chebfi_cheb_filter_proj(chebfi_ctx* ctx, void* Y, const void* proj, int64_t ldp, int64_t nb, int64_t ld,
+                            int degree, double lambda_lo, double lambda_hi, int prec, void* stream);
+
 /* Locking (Section 5.4), in place on Y: band j filtered to its own degree degrees[j] (host
  * array of nb ints in 0..1000; 0 leaves the band as it is) on [lambda_lo, lambda_hi], i.e.
  * chebfi_cheb_filter applied band by band.  Bands are reordered internally by decreasing
@@ -211,6 +220,14 @@ int chebfi_solve_stats(const chebfi_ctx* ctx, int* sweeps_done, int64_t* band_ap
 int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lambda_lo,
                             double lambda_hi, int prec, int nchunks, void* stream);
 
+/* chebfi_cheb_filter_host with p_0 = P^H Y given in HOST memory (complex128, nproj x nb
+ * column-major, leading dimension ldp >= nproj; page-locked for full copy bandwidth), as
+ * chebfi_cheb_filter_proj takes it on the device: each band chunk's projections are copied in
+ * with the chunk.  proj NULL, or no projectors: exactly chebfi_cheb_filter_host. */
+int chebfi_cheb_filter_host_proj(chebfi_ctx* ctx, void* Y, const void* proj, int64_t ldp, int64_t nb, int64_t ld,
+                                 int degree, double lambda_lo, double lambda_hi, int prec, int nchunks,
+                                 void* stream);
+
 /* S-orthonormalisation by Cholesky-QR (FP64): G_Y = Y^H S Y = L L^H, Y <- Y L^{-H}.
  * Synchronises; CHEBFI_ERR_NOT_SPD if G_Y is not positive definite. */
 int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream);
@@ -221,6 +238,13 @@ int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void
  * or NULL.  Synchronises.  A block holding Inf or NaN is reported as CHEBFI_ERR_NONFINITE. */
 int chebfi_rayleigh_ritz(chebfi_ctx* ctx, void* Y, double* evals, double* resid, int64_t nb,
                          int64_t ld, void* stream);
+
+/* chebfi_rayleigh_ritz that also writes proj = P^H Y of the rotated block (device,
+ * complex128, nproj x nb column-major, leading dimension ldp >= nproj; FP64, the product
+ * p R of the step's own projections and rotation), for chebfi_cheb_filter_proj.  proj NULL
+ * or no projectors: proj is not written.  Synchronises. */
+int chebfi_rayleigh_ritz_proj(chebfi_ctx* ctx, void* Y, double* evals, double* resid, void* proj, int64_t ldp,
+                              int64_t nb, int64_t ld, void* stream);
 
 /* Generalized Rayleigh quotients y^H H y / y^H S y of every band (FP64), device nb doubles
  * (Algorithm 2's first step). */

@@ -65,9 +65,15 @@ SIGNATURES = {
     "chebfi_apply_Sinv": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_cheb_filter": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_double, c_double,
                                    c_int, c_void_p]),
+    "chebfi_cheb_filter_host_proj": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int,
+                                             c_double, c_double, c_int, c_int, c_void_p]),
+    "chebfi_cheb_filter_proj": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_double,
+                                        c_double, c_int, c_void_p]),
     "chebfi_orthonormalise": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_rayleigh_ritz": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64,
                                      c_void_p]),
+    "chebfi_rayleigh_ritz_proj": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64,
+                                          c_int64, c_void_p]),
     "chebfi_rayleigh_quotients": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "chebfi_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64,
                              ctypes.POINTER(Params), c_void_p]),

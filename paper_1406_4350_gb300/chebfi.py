@@ -229,26 +229,50 @@ class ChebFI:
                                                        _stream()))
         return out, its.value
 
-    def cheb_filter(self, Y, degree: int, lambda_lo: float, lambda_hi: float, prec: int = F64):
-        """In place on Y; returns Y."""
+    def cheb_filter(self, Y, degree: int, lambda_lo: float, lambda_hi: float, prec: int = F64, proj=None):
+        """In place on Y; returns Y.  proj: P^H Y (nproj x nb complex128 CUDA tensor, column-major)
+        as rayleigh_ritz(..., proj=...) wrote it for this Y, which saves the filter's first P^H Y."""
         y, nb, ld = _block(Y)
-        self._check(self.lib.chebfi_cheb_filter(self.h, y, nb, ld, degree, lambda_lo, lambda_hi, prec,
-                                                _stream()))
+        if proj is None:
+            self._check(self.lib.chebfi_cheb_filter(self.h, y, nb, ld, degree, lambda_lo, lambda_hi, prec,
+                                                    _stream()))
+            return Y
+        p, pnb, ldp = self._proj_block(proj, nb)
+        self._check(self.lib.chebfi_cheb_filter_proj(self.h, y, p, ldp, nb, ld, degree, lambda_lo, lambda_hi, prec,
+                                                     _stream()))
         return Y
 
-    def cheb_filter_host(self, Y, degree: int, lambda_lo: float, lambda_hi: float, prec: int = F64,
-                         nchunks: int = 0):
-        """chebfi_cheb_filter on a host block (complex128 CPU tensor, column-major, ideally pinned),
-        in place; the copies overlap the filter of neighbouring band chunks.  Returns Y."""
+    def _proj_block(self, proj, nb):
+        p, pnb, ldp = _block(proj)
+        if pnb != nb or proj.shape[0] != self.nproj:
+            raise ValueError("projections must be nproj x nb")
+        return p, pnb, max(ldp, self.nproj)
+
+    @staticmethod
+    def _host_block(Y):
         if not (isinstance(Y, torch.Tensor) and not Y.is_cuda and Y.dtype == torch.complex128 and Y.dim() == 2):
             raise TypeError("expected a 2-D complex128 CPU tensor")
         if Y.shape[1] > 0 and Y.stride(0) != 1:
             raise ValueError("host block must be column-major")
         nb = int(Y.shape[1])
         ld = int(Y.stride(1)) if nb > 1 else max(int(Y.shape[0]), 1)
-        self._check(self.lib.chebfi_cheb_filter_host(self.h, ctypes.c_void_p(Y.data_ptr() if Y.numel() else 0), nb,
-                                                     max(ld, int(Y.shape[0])), degree, lambda_lo, lambda_hi, prec,
-                                                     nchunks, _stream()))
+        return ctypes.c_void_p(Y.data_ptr() if Y.numel() else 0), nb, max(ld, int(Y.shape[0]))
+
+    def cheb_filter_host(self, Y, degree: int, lambda_lo: float, lambda_hi: float, prec: int = F64,
+                         nchunks: int = 0, proj=None):
+        """chebfi_cheb_filter on a host block (complex128 CPU tensor, column-major, ideally pinned),
+        in place; the copies overlap the filter of neighbouring band chunks.  proj: P^H Y as an
+        nproj x nb host tensor (column-major), copied in chunk by chunk.  Returns Y."""
+        y, nb, ld = self._host_block(Y)
+        if proj is None:
+            self._check(self.lib.chebfi_cheb_filter_host(self.h, y, nb, ld, degree, lambda_lo, lambda_hi, prec,
+                                                         nchunks, _stream()))
+            return Y
+        p, pnb, ldp = self._host_block(proj)
+        if pnb != nb or proj.shape[0] != self.nproj:
+            raise ValueError("projections must be nproj x nb")
+        self._check(self.lib.chebfi_cheb_filter_host_proj(self.h, y, p, max(ldp, self.nproj), nb, ld, degree,
+                                                          lambda_lo, lambda_hi, prec, nchunks, _stream()))
         return Y
 
     def orthonormalise(self, Y):
@@ -256,13 +280,20 @@ class ChebFI:
         self._check(self.lib.chebfi_orthonormalise(self.h, y, nb, ld, _stream()))
         return Y
 
-    def rayleigh_ritz(self, Y, residuals: bool = True):
+    def rayleigh_ritz(self, Y, residuals: bool = True, proj=None):
+        """Returns (Ritz values, residual norms or None).  proj: an nproj x nb complex128 CUDA
+        tensor (column-major) that receives P^H Y of the rotated block."""
         y, nb, ld = _block(Y)
         ev = torch.empty(nb, dtype=torch.float64, device=Y.device)
         rs = torch.empty(nb, dtype=torch.float64, device=Y.device) if residuals else None
-        self._check(self.lib.chebfi_rayleigh_ritz(self.h, y, ctypes.c_void_p(ev.data_ptr()),
-                                                  ctypes.c_void_p(rs.data_ptr()) if rs is not None else None,
-                                                  nb, ld, _stream()))
+        rsp = ctypes.c_void_p(rs.data_ptr()) if rs is not None else None
+        if proj is None:
+            self._check(self.lib.chebfi_rayleigh_ritz(self.h, y, ctypes.c_void_p(ev.data_ptr()), rsp, nb, ld,
+                                                      _stream()))
+        else:
+            p, _, ldp = self._proj_block(proj, nb)
+            self._check(self.lib.chebfi_rayleigh_ritz_proj(self.h, y, ctypes.c_void_p(ev.data_ptr()), rsp, p, ldp,
+                                                           nb, ld, _stream()))
         return ev, rs
 
     def rayleigh_quotients(self, Y):

@@ -811,10 +811,10 @@ void scatter_from(chebfi_ctx* ctx, const double2* src, void* Y, int64_t nb, int6
 // Algorithm 2's filter in place on a caller's device block (caller's row order, leading
 // dimension ld), stream-ordered on st.
 void filter_device_block(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lo, double hi,
-                         int prec, cudaStream_t st) {
+                         int prec, cudaStream_t st, const double2* p0 = nullptr) {
   if (prec == CHEBFI_F64) {
     gather_to_Ya(ctx, Y, nb, ld, st);
-    filter_on_Ya(ctx, nb, degree, lo, hi, prec, st);
+    filter_on_Ya(ctx, nb, degree, lo, hi, prec, st, p0);
     scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
     return;
   }
@@ -824,8 +824,8 @@ void filter_device_block(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int d
   const int64_t npw = ctx->npw;
   gather_rows(npw, nb, ctx->d_sorted_to_user.p, (const double2*)Y, ld, w.fYa.p, npw, st);
   FilterBufs<float> b{w.fYa.p, w.fYb.p, w.fZ.p, w.fT1.p, w.fpa.p, w.fpb.p, w.fpz.p, w.fpw.p, w.fpq.p};
-  float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lo, hi, st)
-                                     : filter_sorted<float>(ctx, b, nb, degree, lo, hi, st);
+  float2* out = prec == CHEBFI_MIXED ? filter_mixed(ctx, b, nb, degree, lo, hi, st, nullptr, p0)
+                                     : filter_sorted<float>(ctx, b, nb, degree, lo, hi, st, nullptr, p0);
   scatter_rows(npw, nb, ctx->d_sorted_to_user.p, out, npw, (double2*)Y, ld, st);
 }
 
@@ -1633,6 +1633,30 @@ int chebfi_cheb_filter(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int deg
   API_END(ctx)
 }
 
+int chebfi_cheb_filter_proj(chebfi_ctx* ctx, void* Y, const void* proj, int64_t ldp, int64_t nb, int64_t ld,
+                            int degree, double lambda_lo, double lambda_hi, int prec, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(degree >= 0 && degree <= 1000, CHEBFI_ERR_ARG, "degree out of range");
+  CHEBFI_REQUIRE(std::isfinite(lambda_lo) && std::isfinite(lambda_hi) && lambda_hi > lambda_lo, CHEBFI_ERR_ARG,
+                 "need finite lambda_lo < lambda_hi");
+  CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
+  const int64_t nq = ctx->nproj;
+  CHEBFI_REQUIRE(!proj || nq == 0 || ldp >= nq, CHEBFI_ERR_ARG, "projection leading dimension below nproj");
+  if (nb == 0 || degree == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  const double2* p0 = nq > 0 ? (const double2*)proj : nullptr;
+  if (p0 && ldp != nq) {  // the filter reads p_0 with leading dimension nproj
+    ctx->w.p0.alloc((size_t)nq * nb);
+    CHEBFI_CUDA(cudaMemcpy2DAsync(ctx->w.p0.p, sizeof(double2) * nq, p0, sizeof(double2) * ldp, sizeof(double2) * nq,
+                                  nb, cudaMemcpyDeviceToDevice, st));
+    p0 = ctx->w.p0.p;
+  }
+  filter_device_block(ctx, Y, nb, ld, degree, lambda_lo, lambda_hi, prec, st, p0);
+  API_END(ctx)
+}
+
 int chebfi_cheb_filter_adaptive(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, const int32_t* degrees,
                                 double lambda_lo, double lambda_hi, int prec, void* stream) {
   API_BEGIN(ctx)
@@ -1673,8 +1697,9 @@ int chebfi_solve_stats(const chebfi_ctx* ctx, int* sweeps_done, int64_t* band_ap
   return CHEBFI_OK;
 }
 
-int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lambda_lo,
-                            double lambda_hi, int prec, int nchunks, void* stream) {
+// chebfi_cheb_filter_host[_proj]: proj (host, nproj x nb, leading dimension ldp) or null
+static int filter_host(chebfi_ctx* ctx, void* Y, const void* proj, int64_t ldp, int64_t nb, int64_t ld, int degree,
+                double lambda_lo, double lambda_hi, int prec, int nchunks, void* stream) {
   API_BEGIN(ctx)
   require_ready(ctx);
   CHEBFI_REQUIRE(nb >= 0 && (nb == 0 || Y) && ld >= ctx->npw, CHEBFI_ERR_ARG, "bad host block");
@@ -1683,9 +1708,12 @@ int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, in
                  "need finite lambda_lo < lambda_hi");
   CHEBFI_REQUIRE(prec >= 0 && prec <= 2, CHEBFI_ERR_ARG, "bad precision");
   CHEBFI_REQUIRE(nchunks >= 0, CHEBFI_ERR_ARG, "negative chunk count");
+  const int64_t nq = ctx->nproj;
+  CHEBFI_REQUIRE(!proj || nq == 0 || ldp >= nq, CHEBFI_ERR_ARG, "projection leading dimension below nproj");
   if (nb == 0 || degree == 0) return CHEBFI_OK;
   cudaStream_t st = S(stream);
   const int64_t npw = ctx->npw;
+  const bool with_p = proj && nq > 0;
   // bands are filtered independently, so the block is processed in band chunks: chunk c is
   // copied in while chunk c-1 is filtered and chunk c-2 is copied out (two staging buffers)
   int nc = nchunks > 0 ? nchunks : (nb >= 2048 ? 4 : (nb >= 1024 ? 2 : 1));
@@ -1701,23 +1729,33 @@ int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, in
     }
   }
   const int nbuf = nc > 1 ? 2 : 1;
-  for (int i = 0; i < nbuf; ++i) ctx->stage[i].alloc((size_t)npw * per);
+  for (int i = 0; i < nbuf; ++i) {
+    ctx->stage[i].alloc((size_t)npw * per);
+    if (with_p) ctx->stage_p[i].alloc((size_t)nq * per);
+  }
   // the copies start after whatever the caller queued on st before this call
   CHEBFI_CUDA(cudaEventRecord(ctx->ev_filt[0], st));
   CHEBFI_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->ev_filt[0], 0));
   bool used[2] = {false, false};
   char* host = static_cast<char*>(Y);
+  const char* hproj = static_cast<const char*>(proj);
   for (int c = 0; c < nc; ++c) {
     const int64_t b0 = c * per, nbc = std::min<int64_t>(per, nb - b0);
     if (nbc <= 0) break;
     const int k = c % nbuf;
     double2* dev = ctx->stage[k].p;
-    if (used[k]) CHEBFI_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->ev_out[k], 0));  // chunk c-2 copied out
+    // chunk c-2 copied out and filtered (its projections read)
+    if (used[k]) CHEBFI_CUDA(cudaStreamWaitEvent(ctx->copy_in, ctx->ev_out[k], 0));
     CHEBFI_CUDA(cudaMemcpy2DAsync(dev, sizeof(double2) * npw, host + sizeof(double2) * b0 * ld, sizeof(double2) * ld,
                                   sizeof(double2) * npw, nbc, cudaMemcpyHostToDevice, ctx->copy_in));
+    if (with_p)
+      CHEBFI_CUDA(cudaMemcpy2DAsync(ctx->stage_p[k].p, sizeof(double2) * nq, hproj + sizeof(double2) * b0 * ldp,
+                                    sizeof(double2) * ldp, sizeof(double2) * nq, nbc, cudaMemcpyHostToDevice,
+                                    ctx->copy_in));
     CHEBFI_CUDA(cudaEventRecord(ctx->ev_in[k], ctx->copy_in));
     CHEBFI_CUDA(cudaStreamWaitEvent(st, ctx->ev_in[k], 0));
-    filter_device_block(ctx, dev, nbc, npw, degree, lambda_lo, lambda_hi, prec, st);
+    filter_device_block(ctx, dev, nbc, npw, degree, lambda_lo, lambda_hi, prec, st,
+                        with_p ? ctx->stage_p[k].p : nullptr);
     CHEBFI_CUDA(cudaEventRecord(ctx->ev_filt[k], st));
     CHEBFI_CUDA(cudaStreamWaitEvent(ctx->copy_out, ctx->ev_filt[k], 0));
     CHEBFI_CUDA(cudaMemcpy2DAsync(host + sizeof(double2) * b0 * ld, sizeof(double2) * ld, dev, sizeof(double2) * npw,
@@ -1729,6 +1767,17 @@ int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, in
   for (int k = 0; k < nbuf; ++k)
     if (used[k]) CHEBFI_CUDA(cudaStreamWaitEvent(st, ctx->ev_out[k], 0));
   API_END(ctx)
+}
+
+int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lambda_lo,
+                            double lambda_hi, int prec, int nchunks, void* stream) {
+  return filter_host(ctx, Y, nullptr, 0, nb, ld, degree, lambda_lo, lambda_hi, prec, nchunks, stream);
+}
+
+int chebfi_cheb_filter_host_proj(chebfi_ctx* ctx, void* Y, const void* proj, int64_t ldp, int64_t nb, int64_t ld,
+                                 int degree, double lambda_lo, double lambda_hi, int prec, int nchunks,
+                                 void* stream) {
+  return filter_host(ctx, Y, proj, ldp, nb, ld, degree, lambda_lo, lambda_hi, prec, nchunks, stream);
 }
 
 int chebfi_orthonormalise(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, void* stream) {
@@ -1757,6 +1806,27 @@ int chebfi_rayleigh_ritz(chebfi_ctx* ctx, void* Y, double* evals, double* resid,
   ctx->w.tmp.alloc(ctx->w.Ya.n);
   rr_on_Ya(ctx, nb, evals, resid, st);
   scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  CHEBFI_CUDA(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+int chebfi_rayleigh_ritz_proj(chebfi_ctx* ctx, void* Y, double* evals, double* resid, void* proj, int64_t ldp,
+                              int64_t nb, int64_t ld, void* stream) {
+  API_BEGIN(ctx)
+  require_ready(ctx);
+  require_block(ctx, Y, nb, ld);
+  CHEBFI_REQUIRE(nb == 0 || evals, CHEBFI_ERR_ARG, "null evals");
+  const int64_t nq = ctx->nproj;
+  CHEBFI_REQUIRE(!proj || nq == 0 || ldp >= nq, CHEBFI_ERR_ARG, "projection leading dimension below nproj");
+  if (nb == 0) return CHEBFI_OK;
+  cudaStream_t st = S(stream);
+  gather_to_Ya(ctx, Y, nb, ld, st);
+  ctx->w.tmp.alloc(ctx->w.Ya.n);
+  rr_on_Ya(ctx, nb, evals, resid, st);
+  scatter_from(ctx, ctx->w.Ya.p, Y, nb, ld, st);
+  if (proj && nq > 0)  // P^H Y of the rotated block, formed by the rotation for S Y
+    CHEBFI_CUDA(cudaMemcpy2DAsync(proj, sizeof(double2) * ldp, ctx->w.pc.p, sizeof(double2) * nq,
+                                  sizeof(double2) * nq, nb, cudaMemcpyDeviceToDevice, st));
   CHEBFI_CUDA(cudaStreamSynchronize(st));
   API_END(ctx)
 }

@@ -220,6 +220,7 @@ struct Work {
   DevBuf<float2> fYa, fYb, fZ, fT1, fT2, ftmp;            // FP32 filter iterates
   DevBuf<double2> pa, pb, pc, pz, pw, pq, pt;             // nproj x nb projections (FP64)
   const double2* pc_of = nullptr;  // the block whose P^H Y is held in pc (set by Rayleigh-Ritz)
+  DevBuf<double2> p0;              // a caller's P^H Y_0 repacked to leading dimension nproj
   DevBuf<float2> fpa, fpb, fpz, fpw, fpq, fpt;            // FP32 projections
   DevBuf<double2> small1, small2, small3, small4, small5;  // nb x nb
   // refined eigensolver: FP32 first stage, FP64 refinement matrices, stats, cluster pairs
@@ -331,6 +332,7 @@ struct chebfi_ctx {
   double smin = 1.0;  // lower bound of lambda_min(S), set with bound_rigorous
   // host-block filter: staging buffers, copy streams and their events (created on first use)
   chebfi::DevBuf<double2> stage[2];
+  chebfi::DevBuf<double2> stage_p[2];  // the host filter's projection chunks
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_filt[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   ~chebfi_ctx() {

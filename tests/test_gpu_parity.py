@@ -7,6 +7,7 @@ uses ``2e-5 * max|reference|`` (unit roundoff 6e-8, same growth).  Eigenvalues a
 compared in Hartree: 1e-8 against the exact pencil, 1e-9 against the oracle's own run of
 Algorithm 2 from the same start.
 """
+import ctypes
 import dataclasses
 import os
 
@@ -453,3 +454,89 @@ def test_cheb_filter_host_block_in_chunks(prec, tol, nchunks):
     torch.cuda.synchronize()
     ref = ch.filter_reuse(op, cell.Y0, 5, lo, hi)
     _close(host.numpy(), ref, tol * 5)
+
+
+# ----------------------------------------------------------------------------- projections handed over
+def _proj_buf(nq, nb):
+    return torch.empty((nb, nq), dtype=torch.complex128, device="cuda").T
+
+
+@pytest.mark.parametrize("name", ["tiny_paw", "paw48_37"])
+def test_rayleigh_ritz_returns_projections_of_the_rotated_block(name):
+    """chebfi_rayleigh_ritz_proj writes P^H Y of the rotated block (the rotation's p R): against
+    the oracle's P^H Y of the returned block, and the Ritz pairs unchanged."""
+    cell = CELLS[name]()
+    op = PWOperator.from_cell(cell)
+    g = _ctx(cell)
+    Y = _F(cell.Y0)
+    proj = _proj_buf(cell.nproj, cell.nbands)
+    ev, rs = g.rayleigh_ritz(Y, proj=proj)
+    Yg = _np(Y)
+    _close(_np(proj), op.projections(Yg), TOL64)
+    w_ref, _ = ch.rayleigh_ritz(op, cell.Y0)
+    _close(_np(ev), w_ref, TOL64)
+    # a padded leading dimension
+    proj2 = torch.zeros((cell.nbands, cell.nproj + 5), dtype=torch.complex128, device="cuda").T
+    Y2 = _F(cell.Y0)
+    g.rayleigh_ritz(Y2, proj=proj2[: cell.nproj])
+    _close(_np(proj2[: cell.nproj]), op.projections(_np(Y2)), TOL64)
+    assert float(proj2[cell.nproj:].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prec, tol", [(0, TOL64), (1, TOL32), (2, TOLMIX)])
+@pytest.mark.parametrize("name,degree", [("tiny_paw", 5), ("paw48_37", 6)])
+def test_filter_from_handed_projections_matches_oracle(name, degree, prec, tol):
+    """The filter that starts from the projections Rayleigh-Ritz handed over gives the oracle's
+    filter of the rotated block (Algorithm 2's loop: Rayleigh-Ritz, then the next filter)."""
+    cell = CELLS[name]()
+    op = PWOperator.from_cell(cell)
+    hi = ch.upper_bound(op, "rigorous")
+    g = _ctx(cell)
+    Y = _F(cell.Y0)
+    proj = _proj_buf(cell.nproj, cell.nbands)
+    ev, _ = g.rayleigh_ritz(Y, proj=proj)
+    lo = float(_np(ev).max())
+    Yr = _np(Y)
+    ref = ch.filter_reuse(op, Yr, degree, lo, hi)
+    g.cheb_filter(Y, degree, lo, hi, prec=prec, proj=proj)
+    g.sync_status()
+    _close(_np(Y), ref, tol * degree)
+    # through the host-block path, the projections in host memory, two chunks
+    host = torch.empty((cell.nbands, cell.npw), dtype=torch.complex128, pin_memory=True).T
+    host.copy_(torch.from_numpy(Yr))
+    host_p = torch.empty((cell.nbands, cell.nproj), dtype=torch.complex128, pin_memory=True).T
+    host_p.copy_(proj.cpu())
+    g.cheb_filter_host(host, degree, lo, hi, prec=prec, nchunks=2, proj=host_p)
+    torch.cuda.synchronize()
+    _close(host.numpy(), ref, tol * degree)
+
+
+def test_handed_projections_argument_checks():
+    """A projection leading dimension below nproj is an argument error; projections of the
+    wrong shape are refused by the binding."""
+    from paper_1406_4350_gb300.chebfi import ChebFIError, _block
+    cell = _tiny_paw(nb=3, seed=2)
+    g = _ctx(cell)
+    Y = _F(cell.Y0)
+    proj = _proj_buf(cell.nproj, cell.nbands)
+    y, nb, ld = _block(Y)
+    pp = ctypes.c_void_p(proj.data_ptr())
+    with pytest.raises(ChebFIError, match="projection leading dimension"):
+        g._check(g.lib.chebfi_cheb_filter_proj(g.h, y, pp, cell.nproj - 1, nb, ld, 2, 0.0, 10.0, 0, None))
+    ev = torch.empty(cell.nbands, dtype=torch.float64, device="cuda")
+    with pytest.raises(ChebFIError, match="projection leading dimension"):
+        g._check(g.lib.chebfi_rayleigh_ritz_proj(g.h, y, ctypes.c_void_p(ev.data_ptr()), None, pp, cell.nproj - 1,
+                                                 nb, ld, None))
+    with pytest.raises(ValueError):
+        g.cheb_filter(Y, 2, 0.0, 10.0, proj=_proj_buf(cell.nproj + 1, cell.nbands))
+    # norm-conserving projectors (S = I): the handed projections give the filter computed
+    # from scratch
+    nc = make_cell(8.0, 16, 3.0, 2, 1, 3, False, 5)
+    h = _ctx(nc)
+    Yn = _F(nc.Y0)
+    pn = _proj_buf(nc.nproj, nc.nbands)
+    h.rayleigh_ritz(Yn, proj=pn)
+    Yn2 = Yn.clone()
+    h.cheb_filter(Yn, 3, 0.0, 30.0, proj=pn)
+    h.cheb_filter(Yn2, 3, 0.0, 30.0)
+    _close(_np(Yn), _np(Yn2), TOL64)
