@@ -24,6 +24,7 @@ namespace fk {
 
 constexpr int kThreadsF = 256;
 constexpr int kCBF = 32;  // columns per z-pass block
+static_assert(kThreadsF % kCBF == 0, "z-pass blocks are whole groups of kCBF threads");
 
 struct FastArgs {
   int ncol, nxa, pitch, zpitch, ncolp;
@@ -118,12 +119,15 @@ __device__ __forceinline__ void zinv_body(const cplx<typename SphT<R>::type>* __
   __syncthreads();
   LineMap lm;
   lm.stride = fa.zpitch;
-  fast::lines_F<N3, +1>(lines, nc, lm, 1, tw);
+  // a full block's line count is the compile-time kCBF (the passes' item decode divides by it)
+  if (nc == kCBF) fast::lines_F<N3, +1>(lines, kCBF, lm, 1, tw);
+  else fast::lines_F<N3, +1>(lines, nc, lm, 1, tw);
   cplx<R>* t = T + b * fa.ldt + c0;
-  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
-    const int z = i / nc, l = i - z * nc;
-    t[(int64_t)z * fa.ncolp + l] = lines[l * fa.zpitch + z];
-  }
+  // lane l of each group of kCBF threads writes column l (blockDim.x is a multiple of kCBF)
+  const int l = threadIdx.x % kCBF;
+  if (l < nc)
+    for (int z = threadIdx.x / kCBF; z < N3; z += blockDim.x / kCBF)
+      t[(int64_t)z * fa.ncolp + l] = lines[l * fa.zpitch + z];
 }
 
 // plane z of block b: inverse y and x transforms, multiply by V_loc, forward x and y
@@ -363,14 +367,17 @@ __device__ __forceinline__ void zfwd_body(const cplx<R>* __restrict__ T, const F
   cplx<R>* lines = reinterpret_cast<cplx<R>*>(smem_raw) + N3;
   const int nc = min(kCBF, fa.ncol - c0);
   const cplx<R>* t = T + b * fa.ldt + c0;
-  for (int i = threadIdx.x; i < N3 * nc; i += blockDim.x) {
-    const int z = i / nc, l = i - z * nc;
-    lines[l * fa.zpitch + z] = t[(int64_t)z * fa.ncolp + l];
+  {
+    const int l = threadIdx.x % kCBF;  // as in the inverse pass
+    if (l < nc)
+      for (int z = threadIdx.x / kCBF; z < N3; z += blockDim.x / kCBF)
+        lines[l * fa.zpitch + z] = t[(int64_t)z * fa.ncolp + l];
   }
   __syncthreads();
   LineMap lm;
   lm.stride = fa.zpitch;
-  fast::lines_G<N3, -1>(lines, nc, lm, 1, tw);
+  if (nc == kCBF) fast::lines_G<N3, -1>(lines, kCBF, lm, 1, tw);
+  else fast::lines_G<N3, -1>(lines, nc, lm, 1, tw);
   const int j0 = fa.col_start[c0], j1 = fa.col_start[c0 + nc];
   const CS* y = ep.Y + b * ep.ldy;
   const R inv_n3 = to_compute<R>(ep.inv_n3), ea = to_compute<R>(ep.a), ec = to_compute<R>(ep.c),
