@@ -5,7 +5,9 @@ Workload ("paw96"): cubic 40-bohr PAW cell, FFT grid 96^3, G-sphere of 60005 pla
 2048 bands, 256 atoms x 8 projectors (N_proj = 2048), seeded synthetic inputs, Chebyshev
 degree 4.  One step is one pass of Algorithm 2 through the public API: the filter of
 degree 4 on all 2048 bands (cheb_filter) followed by Rayleigh-Ritz in FP64
-(rayleigh_ritz); lambda_- of the next step is the largest Ritz value.
+(rayleigh_ritz); lambda_- of the next step is the largest Ritz value, and the next filter
+starts from the projections P^H Y that Rayleigh-Ritz formed for the rotated block (as
+Algorithm 2's loop in chebfi_solve does; the first warm-up filter forms its own).
 
 Metric: filter band-H-applications per second = bands x degree / time inside the filter,
 for the filter form given by --prec (default: the mixed form).  The FP64 form is timed on
@@ -407,10 +409,14 @@ def run_extra(args):
             lo = float(g.rayleigh_quotients(Y).max().item())
             hist = []
             ev = rs = None
+            # each filter starts from the projections its Rayleigh-Ritz handed over
+            pbuf = torch.empty((nb, cell.nproj), dtype=torch.complex128, device="cuda").T
+            proj = None
             t0 = time.perf_counter()
             for s_ in range(sweeps_max):
-                g.cheb_filter(Y, DEGREE, lo, hi, prec=prec)
-                ev, rs = g.rayleigh_ritz(Y)
+                g.cheb_filter(Y, DEGREE, lo, hi, prec=prec, proj=proj)
+                ev, rs = g.rayleigh_ritz(Y, proj=pbuf)
+                proj = pbuf
                 lo = float(ev.max().item())
                 cert = float(rs[:k75].max().item()) / np.sqrt(smin)
                 hist.append(cert)

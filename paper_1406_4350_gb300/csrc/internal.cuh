@@ -30,14 +30,14 @@ __host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { ret
 // On the device a complex sum or difference is one packed FP32x2 instruction (sm_100 and up);
 // the difference as b (-1) + a, exact in the product and rounded once like a subtraction.
 __host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
   return __fadd2_rn(a, b);
 #else
   return make_float2(a.x + b.x, a.y + b.y);
 #endif
 }
 __host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
   return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 #else
   return make_float2(a.x - b.x, a.y - b.y);
