@@ -39,8 +39,9 @@ DEGREE = 4
 
 def _traffic(tag: str):
     """DRAM bytes per launch of a kernel at the benchmark workload, from the ncu capture
-    recorded in profiles/traffic_paw96.md, or None when the kernel's source has changed
-    since (the record names the file and its SHA-1) or there is no record."""
+    recorded in profiles/traffic_paw96.md, or None when the kernel's sources have changed
+    since (the record names the files and the SHA-1 of their concatenation) or there is no
+    record."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic_paw96.md")
     if not os.path.exists(path):
@@ -51,8 +52,13 @@ def _traffic(tag: str):
         f = dict(kv.split("=", 1) for kv in line.split()[1:])
         if f.get("tag") != tag:
             continue
-        src = os.path.join(ROOT, f["file"])
-        if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != f["sha1"]:
+        h = hashlib.sha1()
+        for name in f["files"].split(","):
+            src = os.path.join(ROOT, name)
+            if not os.path.exists(src):
+                return None
+            h.update(open(src, "rb").read())
+        if h.hexdigest() != f["sha1"]:
             return None
         return float(f["bytes_per_launch"])
     return None
