@@ -52,6 +52,8 @@ def _traffic(tag: str):
         f = dict(kv.split("=", 1) for kv in line.split()[1:])
         if f.get("tag") != tag:
             continue
+        if "files" not in f or "sha1" not in f or "bytes_per_launch" not in f:
+            return None
         h = hashlib.sha1()
         for name in f["files"].split(","):
             src = os.path.join(ROOT, name)
