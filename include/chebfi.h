@@ -212,9 +212,11 @@ int chebfi_solve_stats(const chebfi_ctx* ctx, int* sweeps_done, int64_t* band_ap
 
 /* chebfi_cheb_filter on a block in HOST memory (complex128, npw x nb column-major, leading
  * dimension ld, caller's row order; page-locked memory for full copy bandwidth), in place.
- * Bands are filtered independently, so the block goes through the GPU in nchunks band chunks
- * (0: 4 chunks from 2048 bands up, 2 from 1024, else 1): the copy in of chunk c, the filter of chunk c-1
- * and the copy out of chunk c-2 overlap (two device staging buffers, two copy streams).
+ * Bands are filtered independently, so the block goes through the GPU in nchunks equal band
+ * chunks (0: from 2048 bands up five chunks of nb/8, nb/4, nb/4, nb/4 and the rest, so that
+ * the two copies that overlap no filter are short; 2 from 1024; else 1): the copy in of chunk
+ * c, the filter of chunk c-1 and the copy out of chunk c-2 overlap (two device staging
+ * buffers, two copy streams).
  * Stream-ordered on `stream`: the host block is final once `stream` completes.  The host
  * block must not be touched until then. */
 int chebfi_cheb_filter_host(chebfi_ctx* ctx, void* Y, int64_t nb, int64_t ld, int degree, double lambda_lo,

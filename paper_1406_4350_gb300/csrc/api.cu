@@ -1715,10 +1715,24 @@ static int filter_host(chebfi_ctx* ctx, void* Y, const void* proj, int64_t ldp, 
   const int64_t npw = ctx->npw;
   const bool with_p = proj && nq > 0;
   // bands are filtered independently, so the block is processed in band chunks: chunk c is
-  // copied in while chunk c-1 is filtered and chunk c-2 is copied out (two staging buffers)
-  int nc = nchunks > 0 ? nchunks : (nb >= 2048 ? 4 : (nb >= 1024 ? 2 : 1));
-  nc = (int)std::min<int64_t>(nc, nb);
-  const int64_t per = (nb + nc - 1) / nc;
+  // copied in while chunk c-1 is filtered and chunk c-2 is copied out (two staging buffers).
+  // Only the first chunk's copy in and the last chunk's copy out overlap no filter, so the
+  // automatic split from 2048 bands up makes those two chunks half as wide as the three
+  // between them; below that, or with nchunks given, the chunks are equal.
+  std::vector<int64_t> start;
+  if (nchunks == 0 && nb >= 2048) {
+    const int64_t half = (nb + 7) / 8;
+    start = {0, half, 3 * half, 5 * half, 7 * half, nb};
+  } else {
+    int nc = nchunks > 0 ? nchunks : (nb >= 1024 ? 2 : 1);
+    nc = (int)std::min<int64_t>(nc, nb);
+    const int64_t per = (nb + nc - 1) / nc;
+    for (int64_t b0 = 0; b0 < nb; b0 += per) start.push_back(b0);
+    start.push_back(nb);
+  }
+  const int nc = (int)start.size() - 1;
+  int64_t per = 0;
+  for (int c = 0; c < nc; ++c) per = std::max<int64_t>(per, start[c + 1] - start[c]);
   if (!ctx->copy_in) {
     CHEBFI_CUDA(cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
     CHEBFI_CUDA(cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
@@ -1740,8 +1754,8 @@ static int filter_host(chebfi_ctx* ctx, void* Y, const void* proj, int64_t ldp, 
   char* host = static_cast<char*>(Y);
   const char* hproj = static_cast<const char*>(proj);
   for (int c = 0; c < nc; ++c) {
-    const int64_t b0 = c * per, nbc = std::min<int64_t>(per, nb - b0);
-    if (nbc <= 0) break;
+    const int64_t b0 = start[c], nbc = start[c + 1] - b0;
+    if (nbc <= 0) continue;
     const int k = c % nbuf;
     double2* dev = ctx->stage[k].p;
     // chunk c-2 copied out and filtered (its projections read)

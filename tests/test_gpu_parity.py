@@ -456,6 +456,21 @@ def test_cheb_filter_host_block_in_chunks(prec, tol, nchunks):
     _close(host.numpy(), ref, tol * 5)
 
 
+def test_cheb_filter_host_block_tapered_chunks():
+    """From 2048 bands up the automatic split of the host-block filter makes the first and the
+    last chunk half as wide (nb/8, nb/4, nb/4, nb/4, rest): every band against the oracle."""
+    cell = make_cell(8.0, 16, 3.0, 3, 8, 2049, True, 33)
+    op = PWOperator.from_cell(cell)
+    hi = ch.upper_bound(op, "rigorous")
+    lo = float(ch.rayleigh_quotients(op, cell.Y0).max())
+    g = _ctx(cell)
+    host = torch.empty((cell.nbands, cell.npw), dtype=torch.complex128, pin_memory=True).T
+    host.copy_(torch.from_numpy(cell.Y0))
+    g.cheb_filter_host(host, 3, lo, hi, nchunks=0)
+    torch.cuda.synchronize()
+    _close(host.numpy(), ch.filter_reuse(op, cell.Y0, 3, lo, hi), TOL64 * 3)
+
+
 # ----------------------------------------------------------------------------- projections handed over
 def _proj_buf(nq, nb):
     return torch.empty((nb, nq), dtype=torch.complex128, device="cuda").T
