@@ -72,9 +72,62 @@ __device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 // exact scaling by 1/2
 __device__ __forceinline__ dfl df_half(dfl a) { return dfl(0.5f * a.h, 0.5f * a.l); }
 
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// The complex operations with the (Re, Im) pair of each part in one packed FP32x2 register
+// pair: the same error-free transformations, in the same order, with one packed instruction
+// for the two components (a difference is b (-1) + a, exact product, one rounding).
+struct dfl2 {
+  float2 h, l;  // (Re.h, Im.h), (Re.l, Im.l)
+};
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ dfl2 pk(cdf a) { return dfl2{make_float2(a.x.h, a.y.h), make_float2(a.x.l, a.y.l)}; }
+__device__ __forceinline__ cdf upk(dfl2 a) { return cdf{dfl(a.h.x, a.l.x), dfl(a.h.y, a.l.y)}; }
+__device__ __forceinline__ dfl2 fast2sum2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  return dfl2{s, f2sub(b, f2sub(s, a))};
+}
+__device__ __forceinline__ dfl2 add2(dfl2 a, dfl2 b) {
+  const float2 s = __fadd2_rn(a.h, b.h);
+  const float2 bb = f2sub(s, a.h);
+  const float2 e = __fadd2_rn(f2sub(a.h, f2sub(s, bb)), f2sub(b.h, bb));
+  return fast2sum2(s, __fadd2_rn(e, __fadd2_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfl2 mul2(dfl2 a, dfl2 b) {
+  const float2 p = __fmul2_rn(a.h, b.h);
+  float2 e = __ffma2_rn(a.h, b.h, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(a.h, b.l, e);
+  e = __ffma2_rn(a.l, b.h, e);
+  return fast2sum2(p, e);
+}
+__device__ __forceinline__ cdf operator+(cdf a, cdf b) { return upk(add2(pk(a), pk(b))); }
+__device__ __forceinline__ cdf operator-(cdf a, cdf b) { return upk(add2(pk(a), pk(cdf{-b.x, -b.y}))); }
+// (a.x b.x - a.y b.y, a.x b.y + a.y b.x): the products (a.x b.x, a.x b.y) and (a.y b.y, a.y b.x)
+// as two packed products, then one packed sum with the first lane's sign flipped
+__device__ __forceinline__ cdf operator*(cdf a, cdf b) {
+  const dfl2 p1 = mul2(dfl2{make_float2(a.x.h, a.x.h), make_float2(a.x.l, a.x.l)}, pk(b));
+  const dfl2 p2 = mul2(dfl2{make_float2(a.y.h, a.y.h), make_float2(a.y.l, a.y.l)},
+                       dfl2{make_float2(b.y.h, b.x.h), make_float2(b.y.l, b.x.l)});
+  return upk(add2(p1, dfl2{make_float2(-p2.h.x, p2.h.y), make_float2(-p2.l.x, p2.l.y)}));
+}
+// the codelets' helpers (fft_core.cuh): a / 2 (exact), SIGN i h d, s a
+__device__ __forceinline__ cdf chalf(cdf a) {
+  const dfl2 v = pk(a);
+  return upk(dfl2{__fmul2_rn(v.h, make_float2(0.5f, 0.5f)), __fmul2_rn(v.l, make_float2(0.5f, 0.5f))});
+}
+template <int SIGN> __device__ __forceinline__ cdf cmul_i(cdf d, dfl h) {
+  // (h d.y, h d.x), then the sign of one lane: (-h d.y, h d.x) = i h d, (h d.y, -h d.x) = -i h d
+  const dfl2 q = mul2(dfl2{make_float2(h.h, h.h), make_float2(h.l, h.l)},
+                      dfl2{make_float2(d.y.h, d.x.h), make_float2(d.y.l, d.x.l)});
+  return SIGN > 0 ? cdf{dfl(-q.h.x, -q.l.x), dfl(q.h.y, q.l.y)} : cdf{dfl(q.h.x, q.l.x), dfl(-q.h.y, -q.l.y)};
+}
+__device__ __forceinline__ cdf cscale(cdf a, dfl s) {
+  return upk(mul2(pk(a), dfl2{make_float2(s.h, s.h), make_float2(s.l, s.l)}));  // a.x s, a.y s
+}
+#else
 __device__ __forceinline__ cdf operator+(cdf a, cdf b) { return cdf{a.x + b.x, a.y + b.y}; }
 __device__ __forceinline__ cdf operator-(cdf a, cdf b) { return cdf{a.x - b.x, a.y - b.y}; }
 __device__ __forceinline__ cdf operator*(cdf a, cdf b) { return cdf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+#endif
 __device__ __forceinline__ cdf conjg(cdf a) { return cdf{a.x, -a.y}; }
 
 // conversions at the FP64 storage boundary (one FP64 add each way)

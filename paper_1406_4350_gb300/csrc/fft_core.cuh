@@ -22,6 +22,28 @@ namespace chebfi {
 __host__ __device__ __forceinline__ float half_of(float v) { return 0.5f * v; }
 __host__ __device__ __forceinline__ double half_of(double v) { return 0.5 * v; }
 
+// Component-wise helpers of the codelets; the double-float complex type overloads them
+// (dfloat.cuh) with packed FP32x2 arithmetic on its (Re, Im) pairs.
+template <typename C> __host__ __device__ __forceinline__ C chalf(C a) {  // a / 2, exact
+  C r;
+  r.x = half_of(a.x);
+  r.y = half_of(a.y);
+  return r;
+}
+template <int SIGN, typename C, typename R> __host__ __device__ __forceinline__ C cmul_i(C d, R h) {  // SIGN i h d
+  C u;
+  u.x = h * d.y;
+  u.y = h * d.x;
+  if (SIGN > 0) u.x = -u.x;
+  else u.y = -u.y;
+  return u;
+}
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) {  // s a, s real
+  a.x *= s;
+  a.y *= s;
+  return a;
+}
+
 // r-point DFT out_p = sum_q x_q w^{pq}, w = exp(SIGN 2 pi i / r), in place.
 template <int SIGN, typename C>
 __host__ __device__ __forceinline__ void small_dft(C* x, int r) {
@@ -48,14 +70,8 @@ __host__ __device__ __forceinline__ void small_dft(C* x, int r) {
   } else if (r == 3) {
     const R h = (R)0.86602540378443864676;  // sqrt(3)/2
     C s = x[1] + x[2], d = x[1] - x[2];
-    C t;
-    t.x = x[0].x - half_of(s.x);
-    t.y = x[0].y - half_of(s.y);
-    C u;  // SIGN i sqrt(3)/2 d
-    u.x = h * d.y;
-    u.y = h * d.x;
-    if (SIGN > 0) u.x = -u.x;
-    else u.y = -u.y;
+    const C t = x[0] - chalf(s);
+    const C u = cmul_i<SIGN>(d, h);  // SIGN i sqrt(3)/2 d
     x[0] = x[0] + s;
     x[1] = t + u;
     x[2] = t - u;

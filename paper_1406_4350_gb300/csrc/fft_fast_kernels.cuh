@@ -167,8 +167,7 @@ __device__ __forceinline__ void plane_body(cplx<R>* __restrict__ T, const R* __r
 #pragma unroll
       for (int kb = 0; kb < NB; ++kb) {
         const R s = vv[kb * N];
-        u[kb].x *= s;
-        u[kb].y *= s;
+        u[kb] = cscale(u[kb], s);
       }
       fast::dft<NB, -1>(u);
 #pragma unroll
@@ -287,8 +286,7 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
 #pragma unroll
       for (int kb = 0; kb < NB; ++kb) {
         const R s = vv[kb * N];
-        u[kb].x *= s;
-        u[kb].y *= s;
+        u[kb] = cscale(u[kb], s);
       }
       fast::dft<NB, -1>(u);
 #pragma unroll
