@@ -205,8 +205,8 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
   C* rows = plane + lo * P;  // row a of the active range
   // y, inverse: F's pass A on the active rows, its inputs read from the column buffer;
   // consecutive threads take consecutive y of one row, so they read consecutive columns
-  {
-    // blockDim.x is a multiple of NB, so every item of this thread has the same nb: its
+  if constexpr (NT % NB == 0) {
+    // blockDim.x (NT) is a multiple of NB, so every item of this thread has the same nb: its
     // twiddles are read once (a warp's threads hold NB different nb)
     const int nb = threadIdx.x % NB;
     C w[NA];
@@ -226,6 +226,23 @@ __device__ __forceinline__ void plane_body_pruned(cplx<R>* __restrict__ T, const
       row[0] = v[0];
 #pragma unroll
       for (int ka = 1; ka < NA; ++ka) row[NB * ka] = v[ka] * w[ka];
+    }
+  } else {
+    // NB = 6 with a 256-thread block: an item's nb and twiddles are its own
+    for (int it = threadIdx.x; it < nl * NB; it += blockDim.x) {
+      const int a = it / NB, nb = it - a * NB;
+      C* row = rows + a * P + nb;
+      const int32_t* rc = fa.row_col + a * N + nb;
+      C v[NA];
+#pragma unroll
+      for (int na = 0; na < NA; ++na) {
+        const int c = __ldg(rc + NB * na);
+        v[na] = c >= 0 ? t[c] : zero;
+      }
+      fast::dft<NA, +1>(v);
+      row[0] = v[0];
+#pragma unroll
+      for (int ka = 1; ka < NA; ++ka) row[NB * ka] = v[ka] * fast::twN<+1>(tw, nb * ka);
     }
   }
   __syncthreads();

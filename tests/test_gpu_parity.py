@@ -108,6 +108,27 @@ def test_fp64_fft_double_float_and_native(name):
         g.set_fft64(7)
 
 
+def test_plane_pass_with_a_wide_sphere():
+    """A sphere spanning 43 of the 48 x rows: the first y pass of the plane kernel has
+    43 x 6 items, more than a 256-thread block (NB = 6 does not divide 256, so each item takes
+    its own twiddles); apply_H in the FP64 form (double-float and FP64-unit FFTs), FP32 and
+    mixed against the oracle."""
+    from paper_1406_4350_gb300 import F32, MIXED
+    from paper_1406_4350_gb300._lib import FFT64_DOUBLE_FLOAT, FFT64_NATIVE
+    cell = make_cell(8.0, 48, 140.0, 2, 8, 3, True, 7)
+    xs = (cell.miller[:, 0] + 24) % 48
+    assert xs.max() - xs.min() + 1 == 43
+    op = PWOperator.from_cell(cell)
+    ref = op.apply_H(cell.Y0)
+    g = _ctx(cell)
+    for mode in (FFT64_DOUBLE_FLOAT, FFT64_NATIVE):
+        g.set_fft64(mode)
+        _close(_np(g.apply_H(_F(cell.Y0))), ref, TOL64)
+    _close(_np(g.apply_H(_F(cell.Y0), prec=F32)), ref, TOL32)
+    _close(_np(g.apply_H(_F(cell.Y0), prec=MIXED)), ref, TOLMIX)
+    g.sync_status()
+
+
 @pytest.mark.parametrize("name", ["tiny_paw", "nc24", "paw48_37"])
 def test_apply_H_fp32(name):
     from paper_1406_4350_gb300 import F32
